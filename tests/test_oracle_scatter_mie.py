@@ -1,0 +1,200 @@
+"""Pins for the oracle's observables (O10), Mie series (O11) and the
+DDA-versus-Mie accuracy the paper reports (Secs. 3.2, 4)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dda, errors, lattice, mie, observables, polarizability, system
+from paper_0704_0037_gb300 import inputs
+
+
+# ------------------------------------------------------------------ Mie
+
+def _mie_mpmath(x, m, nterms):
+    """Independent evaluation with mpmath spherical Bessel functions (50 digits)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    x = mpmath.mpf(x)
+    m = mpmath.mpc(m)
+    mx = m * x
+
+    def psi(n, z):
+        return z * mpmath.sqrt(mpmath.pi / (2 * z)) * mpmath.besselj(n + 0.5, z)
+
+    def xi(n, z):
+        return z * mpmath.sqrt(mpmath.pi / (2 * z)) * (mpmath.besselj(n + 0.5, z)
+                                                       + 1j * mpmath.bessely(n + 0.5, z))
+
+    def dpsi(n, z):
+        return mpmath.diff(lambda t: psi(n, t), z)
+
+    def dxi(n, z):
+        return mpmath.diff(lambda t: xi(n, t), z)
+
+    a, b = [], []
+    for n in range(1, nterms + 1):
+        p_mx, dp_mx = psi(n, mx), dpsi(n, mx)
+        p_x, dp_x = psi(n, x), dpsi(n, x)
+        x_x, dx_x = xi(n, x), dxi(n, x)
+        a.append(complex((m * p_mx * dp_x - p_x * dp_mx) / (m * p_mx * dx_x - x_x * dp_mx)))
+        b.append(complex((p_mx * dp_x - m * p_x * dp_mx) / (p_mx * dx_x - m * x_x * dp_mx)))
+    return np.array(a), np.array(b)
+
+
+@pytest.mark.parametrize("x,m", [(3.0, 1.5), (3.0, 1.33 + 0.1j), (20.0, 2.0)])
+def test_mie_coefficients_against_mpmath(x, m):
+    a, b = mie.coefficients(x, m)
+    k = min(a.size, 12)
+    ar, br = _mie_mpmath(x, m, k)
+    assert np.allclose(a[:k], ar, rtol=1e-10, atol=1e-13)
+    assert np.allclose(b[:k], br, rtol=1e-10, atol=1e-13)
+
+
+def test_mie_against_scipy_spherical_bessel():
+    from scipy.special import spherical_jn, spherical_yn
+    x, m = 5.0, 1.4
+    a, b = mie.coefficients(x, m)
+    n = np.arange(1, a.size + 1)
+    mx = m * x
+    psi_x = x * spherical_jn(n, x)
+    dpsi_x = spherical_jn(n, x) + x * spherical_jn(n, x, derivative=True)
+    xi_x = x * (spherical_jn(n, x) + 1j * spherical_yn(n, x))
+    dxi_x = dpsi_x + 1j * (spherical_yn(n, x) + x * spherical_yn(n, x, derivative=True))
+    psi_m = mx * spherical_jn(n, mx)
+    dpsi_m = spherical_jn(n, mx) + mx * spherical_jn(n, mx, derivative=True)
+    ar = (m * psi_m * dpsi_x - psi_x * dpsi_m) / (m * psi_m * dxi_x - xi_x * dpsi_m)
+    br = (psi_m * dpsi_x - m * psi_x * dpsi_m) / (psi_m * dxi_x - m * xi_x * dpsi_m)
+    assert np.allclose(a, ar, rtol=1e-9, atol=1e-14)
+    assert np.allclose(b, br, rtol=1e-9, atol=1e-14)
+
+
+def test_mie_energy_conservation_and_limits():
+    for x, m in [(3.0, 1.5), (40.0, 1.05), (20.0, 2.0)]:
+        qe, qs, qa, _ = mie.efficiencies(x, m)
+        assert abs(qe - qs) < 1e-10 * qe            # real m: no absorption
+    # Rayleigh limit
+    x, m = 0.01, 1.5
+    qe, qs, _, _ = mie.efficiencies(x, m)
+    ray = 8.0 / 3.0 * x ** 4 * abs((m * m - 1) / (m * m + 2)) ** 2
+    assert abs(qs / ray - 1) < 1e-3
+    # m = 1: no scattering
+    a, b = mie.coefficients(3.0, 1.0)
+    assert np.abs(a).max() < 1e-14 and np.abs(b).max() < 1e-14
+    # absorbing sphere: Q_abs > 0
+    assert mie.efficiencies(3.0, 1.5 + 0.1j)[2] > 0
+
+
+def test_mie_angular_integrals():
+    """Q_sca = (1/x^2) int (|S1|^2+|S2|^2) sin t dt; Q_ext = (4/x^2) Re S(0);
+    g from the same integral weighted by cos t."""
+    x, m = 7.0, 1.33 + 0.01j
+    qe, qs, _, g = mie.efficiencies(x, m)
+    mu, w = np.polynomial.legendre.leggauss(200)
+    S1, S2 = mie.amplitudes(x, m, np.rad2deg(np.arccos(mu)))
+    s = np.abs(S1) ** 2 + np.abs(S2) ** 2
+    assert abs(np.sum(w * s) / x ** 2 / qs - 1) < 1e-10
+    assert abs(np.sum(w * s * mu) / x ** 2 / qs / g - 1) < 1e-9
+    S1_0, S2_0 = mie.amplitudes(x, m, [0.0])
+    assert abs(S1_0[0] - S2_0[0]) < 1e-12 * abs(S1_0[0])
+    assert abs(4 / x ** 2 * S1_0[0].real / qe - 1) < 1e-12
+
+
+# ------------------------------------------------------------------ observables
+
+def test_quadrature_weights():
+    dirs, w = observables.sphere_quadrature(16, 32)
+    assert abs(w.sum() - 4 * math.pi) < 1e-12
+    assert np.allclose(np.linalg.norm(dirs, axis=1), 1.0)
+    e = np.array([1.0, 0.0, 0.0])
+    assert abs(np.sum(w * (1 - (dirs @ e) ** 2)) - 8 * math.pi / 3) < 1e-12
+
+
+def test_qabs_vanishes_for_real_m_any_P():
+    rng = np.random.default_rng(0)
+    P = rng.standard_normal((3, 40)) + 1j * rng.standard_normal((3, 40))
+    for presc in ("rr", "ldr", "cldr"):
+        a = polarizability.alpha_diag(1.6, 0.5, presc, (0, 0, 1), (1, 0, 0))
+        alpha = np.repeat(a[:, None], 40, axis=1)
+        assert abs(observables.q_abs(P, alpha, 0.5, 2.0)) < 1e-14
+    a = polarizability.alpha_diag(1.6, 0.5, "cm")
+    alpha = np.repeat(a[:, None], 40, axis=1)
+    assert observables.q_abs(P, alpha, 0.5, 2.0) < 0        # CM is not energy consistent
+
+
+def test_optical_theorem_identity_any_P():
+    rng = np.random.default_rng(1)
+    pos = rng.standard_normal((30, 3)) * 3
+    P = rng.standard_normal((3, 30)) + 1j * rng.standard_normal((3, 30))
+    kd, xs = 0.4, 2.5
+    prop, pol = np.array([0.0, 0.6, 0.8]), np.array([1.0, 0.0, 0.0])
+    e = system.incident_field(pos, kd, prop, pol)
+    q1 = observables.q_ext(P, e, kd, xs)
+    F = observables.farfield(P, pos, kd, prop[None, :])[0]
+    q2 = observables.q_ext_forward(F, pol, kd, xs)
+    assert abs(q1 - q2) < 1e-12 * abs(q1)
+
+
+def test_single_dipole_efficiencies():
+    kd, xs = 0.3, 0.3 * (3 / (4 * math.pi)) ** (1 / 3)
+    alpha = polarizability.alpha_diag(1.5, kd, "ldr")
+    P = alpha[:, None] * np.array([[1.0], [0.0], [0.0]])
+    pos = np.zeros((1, 3))
+    e = system.incident_field(pos, kd, (0, 0, 1), (1, 0, 0))
+    qe = observables.q_ext(P, e, kd, xs)
+    assert abs(qe - 4 * kd ** 3 * alpha[0].imag / xs ** 2) < 1e-15
+    qs = observables.q_sca_quadrature(P, pos, kd, xs, 12, 24)
+    assert abs(qs - 8 / 3 * kd ** 6 * abs(alpha[0]) ** 2 / xs ** 2) < 1e-12 * qs
+    assert abs(qe - qs) < 1e-12 * qe                     # RR/LDR single dipole conserves energy
+
+
+@pytest.mark.parametrize("m,presc", [(1.5, "ldr"), (1.5 + 0.2j, "ldr"), (2.0, "rr")])
+def test_energy_balance_exact_solution(m, presc):
+    """The exact DDA solution (dense LU) satisfies Q_ext = Q_abs + Q_sca."""
+    occ = inputs.sphere(6)
+    n_occ = int((occ > 0).sum())
+    xs = 1.2
+    prob = dda.Problem(occ, [m], lattice.kd_volume_corrected(xs, n_occ))
+    res = dda.simulate(prob, xs, presc, pols=((1, 0, 0),), method="dense")
+    P = res["P"][0]
+    qs = observables.q_sca_quadrature(P, prob.pos, prob.kd, xs, 24, 48)
+    assert abs(res["qext"][0] - res["qabs"][0] - qs) < 1e-9 * res["qext"][0]
+
+
+def test_plane_amplitudes_cross_terms_vanish_for_sphere():
+    """The xz plane is a symmetry plane of the discretised sphere: S3 = S4 = 0."""
+    occ = inputs.sphere(8)
+    n_occ = int((occ > 0).sum())
+    xs = 2.0
+    prob = dda.Problem(occ, [1.5], lattice.kd_volume_corrected(xs, n_occ))
+    th = inputs.angles_deg(19)
+    res = dda.simulate(prob, xs, "ldr", method="dense", thetas=th)
+    S1, S2, S3, S4 = observables.amplitude_plane(res["F"][0], res["F"][1], th)
+    scale = np.abs(S1).max()
+    assert np.abs(S3).max() < 1e-12 * scale and np.abs(S4).max() < 1e-12 * scale
+    # forward direction: S1(0) = S2(0)
+    assert abs(S1[0] - S2[0]) < 1e-12 * abs(S1[0])
+
+
+@pytest.mark.slow
+def test_dda_converges_to_mie_config_sphere16():
+    """x = 3, m = 1.5, LDR, 16^3 box (about 11 dipoles per wavelength): the DDA
+    errors are of the size the paper quotes for this regime (Sec. 4: a few per
+    cent for cross sections, max S11 errors < 0.4 for x < 10), and they shrink
+    as the lattice is refined."""
+    xs, m = 3.0, 1.5
+    th = inputs.angles_deg(181)
+    s11_mie = mie.s11(xs, m, th)
+    qext_mie = mie.efficiencies(xs, m)[0]
+    errs = []
+    for n in (16, 24):
+        occ = inputs.sphere(n)
+        prob = dda.Problem(occ, [m], lattice.kd_volume_corrected(xs, int((occ > 0).sum())))
+        res = dda.simulate(prob, xs, "ldr", tol=1e-8, thetas=th)
+        qext = 0.5 * (res["qext"][0] + res["qext"][1])
+        e_q = errors.rel_error(qext, qext_mie)
+        e_max, e_rms = errors.s11_errors(res["s11"], s11_mie)
+        errs.append((e_q, e_max, e_rms))
+        assert abs(res["qabs"][0]) < 1e-10
+    assert errs[0][0] < 0.03 and errs[0][1] < 0.4
+    assert errs[1][0] < errs[0][0] and errs[1][2] < errs[0][2]
