@@ -1,0 +1,459 @@
+#!/usr/bin/env python
+"""Benchmark of the DDA hot path on one GB300 (or N replicas under torchrun).
+
+Workload: sphere x = 40, m = 1.05 (LDR polarizability) on a 134^3 box
+(1,260,552 dipoles, about 10 dipoles per wavelength, the paper's rule of
+Sec. 3.1), padded FFT grid 270^3, incidence along z with x polarisation.
+
+One step = one whole pass of the path for that particle: beta and the
+right-hand side, the D-matrix (FFT of G, FP64, plus its complex64 copy),
+QMR-CS in the FP32-refined form to a true relative residual of 1e-5, and the
+scattering quantities (F at 181 angles in the xz plane, Q_ext, Q_abs).
+
+value = products with A (complex64 and complex128) per second over the timed
+steps, whole job.  Beside it: the time to residual 1e-5 of the same solve and
+of the plain FP64 form on the same GPU, per-kernel roofline data, the CPU
+oracle baseline and an end-to-end run through the C-ABI with host buffers.
+
+--impl reference times the CPU oracle (the plain complex128 restatement of
+the method) on bounded samples of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DDA matvecs/s & time-to-residual-1e-5 vs plain FP64 form on same GB300"
+UNIT = "matvec/s"
+N_SPHERE, X_SIZE, M_INDEX = 134, 40.0, 1.05
+TOL = 1e-5
+INNER_TOL = 3e-3
+N_ANGLES = 181
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=INNER_TOL)
+    ap.add_argument("--n", type=int, default=N_SPHERE, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload_config(n, note):
+    return {"workload": f"sphere x={X_SIZE:g} m={M_INDEX:g} LDR, {n}^3 box, QMR-CS to 1e-5 "
+                        "(FP32-refined), F at 181 xz-plane angles",
+            "n_box": n, "x": X_SIZE, "m": M_INDEX, "polarizability": "LDR",
+            "solver": "qmr_cs", "precision": "fp32_refined", "tol": TOL,
+            "l2": note, "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+# ---------------------------------------------------------------- roofline models
+def kernel_models(n, M, n_occ):
+    """Algorithmic bytes (complex64 kernels, HBM-bound) and flops (complex128
+    kernels, FP64-ALU-bound) per launch of each traced kernel, from the pass
+    structure of the product (Sec. 2): padded M, lattice n, N_occ dipoles.
+    FFT flops use 5 L log2 L per complex transform of length L."""
+    lg = math.log2(M)
+    out = {}
+    for s, suf in ((8, "c64"), (16, "c128")):
+        b1 = 3 * M * n * n * s          # [3][nz][ny][Mx]
+        b2 = 3 * M * M * n * s          # [3][nz][My][Mx]
+        oct_ = 6 * (M // 2 + 1) ** 3 * s
+        vec = 3 * n_occ * s
+        idx = n_occ * 3 + (n * n + 1) * 8   # x index (2 B) + material (1 B) per dipole + row offsets
+        out[f"p1_xfft_{suf}"] = dict(bytes=vec + idx + b1, flops=3 * n * n * 5 * M * lg)
+        out[f"p2_yfft_{suf}"] = dict(bytes=b1 + b2, flops=3 * n * M * 5 * M * lg)
+        out[f"p3_zconv_{suf}"] = dict(bytes=2 * b2 + oct_, flops=3 * M * M * 2 * 5 * M * lg + 66 * M ** 3)
+        out[f"p4_yifft_{suf}"] = dict(bytes=b2 + b1, flops=3 * n * M * 5 * M * lg)
+        out[f"p5_xifft_{suf}"] = dict(bytes=b1 + 2 * vec + idx, flops=3 * n * n * 5 * M * lg)
+    out["dbuild_lines"] = dict(bytes=3 * 2 * M ** 3 * 16, flops=5 * M ** 3 * math.log2(M ** 3))
+    return out
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "of measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe's nominal 1.25 TFLOP/s)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_0704_0037_gb300 import build, dda, inputs
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    occ = inputs.sphere(n)
+    prop = np.array([[0.0, 0.0, 1.0]])
+    pol = np.array([[1.0, 0.0, 0.0]])
+    th = inputs.angles_deg(N_ANGLES)
+    t = np.deg2rad(th)
+    dirs = np.stack([np.sin(t), np.zeros_like(t), np.cos(t)], axis=1)
+    opts = dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_LDR, prec=dda.DDA_FP32_REFINED, tol=TOL,
+                maxiter=10000, inner_tol=args.inner_tol)
+    p = dda.Particle(occ, [M_INDEX], X_SIZE, volume_corrected=True)
+    P = torch.zeros((1, 3, p.n_occ), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
+
+    solve_ms = []
+
+    def step(record=False):
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, info, _ = dda.dda_solve(p.h, opts, prop, pol, P)
+        e1.record(stream)
+        F, q = dda.dda_scatter(p.h, dda.DDA_LDR, P, prop, pol, dirs)
+        if record:
+            e1.synchronize()
+            solve_ms.append(e0.elapsed_time(e1))
+        return st, info[0], q
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0)
+    if rank == 0:
+        clocks.start()
+    dda.dda_trace(p.h, True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    mv = mv64 = iters = 0
+    last = None
+    for _ in range(args.steps):
+        st, info, q = step(record=True)
+        mv += info["matvecs"]
+        mv64 += info["matvecs_fp64"]
+        iters += info["iters"]
+        last = (st, info, q)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    trace = dda.dda_trace_read(p.h)
+    dda.dda_trace(p.h, False)
+    clk = clocks.stop() if rank == 0 else None
+    t_max = ms
+    mv_all = mv
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+        mm = torch.tensor([mv], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(mm, op=torch.distributed.ReduceOp.SUM)
+        mv_all = int(mm.item())
+    value = mv_all / (t_max / 1e3)
+
+    # plain FP64 form on the same GPU (the comparison base of the metric)
+    opts64 = dict(opts, prec=dda.DDA_FP64)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st64, info64, _ = dda.dda_solve(p.h, opts64, prop, pol, P)
+    e1.record(stream)
+    e1.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    F64, q64 = dda.dda_scatter(p.h, dda.DDA_LDR, P, prop, pol, dirs[:1])
+
+    # matvec-only rates (CUDA events, 10 products each, inputs > L2)
+    rates = {}
+    for prec, dt, nm in ((dda.DDA_FP32_REFINED, torch.complex64, "c64"),
+                         (dda.DDA_FP64, torch.complex128, "c128")):
+        x = torch.randn((1, 3, p.n_occ), dtype=dt, device=dev)
+        y = torch.empty_like(x)
+        dda.dda_matvec(p.h, prec, x, y)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        reps = 10 if nm == "c64" else 3
+        a.record(stream)
+        for _ in range(reps):
+            dda.dda_matvec(p.h, prec, x, y)
+        b.record(stream)
+        b.synchronize()
+        rates[nm] = reps / (a.elapsed_time(b) / 1e3)
+        del x, y
+
+    result = None
+    if rank == 0:
+        st, info, q = last
+        M = p.grid[0]
+        models = kernel_models(n, M, p.n_occ)
+        peaks, peak_note = load_peaks()
+        ker = {k: v for k, v in trace.items() if k != "all_launches"}
+        tot = sum(v[0] for v in ker.values())
+        dom = max(ker, key=lambda k: ker[k][0])
+        dms, dcnt = ker[dom]
+        avg_s = dms / dcnt / 1e3
+        md = models.get(dom)
+        if dom.endswith("c64"):
+            achieved = md["bytes"] / avg_s / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "peak_note": f"hbm_gbs {peak_note}"}
+        else:
+            achieved = md["flops"] / avg_s / 1e12 if md else None
+            roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                    "traffic": None, "peak_note": "FP64 ALU peak derived from unit counts and clock"}
+        roof["share"] = dms / tot
+        roof["avg_launch_ms"] = dms / dcnt
+        per_kernel = {}
+        for k, (kms, kc) in sorted(ker.items(), key=lambda kv: -kv[1][0]):
+            e = {"ms": round(kms, 3), "launches": kc, "share": round(kms / tot, 4),
+                 "avg_ms": round(kms / kc, 4)}
+            md = models.get(k)
+            if md and k.endswith("c64"):
+                e["hbm_gbs"] = round(md["bytes"] / (kms / kc / 1e3) / 1e9, 1)
+                e["hbm_frac"] = round(e["hbm_gbs"] / peaks["hbm_gbs"], 3)
+            elif md:
+                e["fp64_tflops"] = round(md["flops"] / (kms / kc / 1e3) / 1e12, 3)
+            per_kernel[k] = e
+        c64_matvec_bytes = sum(models[f"p{i}_{nm}_c64"]["bytes"] for i, nm in
+                               ((1, "xfft"), (2, "yfft"), (3, "zconv"), (4, "yifft"), (5, "xifft")))
+        t2r = statistics.median(solve_ms) / 1e3
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "data": "synthetic (sphere occupancy computed from the lattice; no dataset)",
+            "config": workload_config(n, "inputs larger than L2: 234 MB complex64 y-pass buffer, "
+                                         "315 MB FP64 G grid, 121 MB D octant, per step"),
+            "time_to_residual_s": t2r,
+            "fp64_form": {"time_to_residual_s": fp64_ms / 1e3, "status": info64[0]["status_name"],
+                          "iters": info64[0]["iters"], "matvecs": info64[0]["matvecs"],
+                          "rel_res_true": info64[0]["rel_res_true"], "qext": float(q64[0, 0])},
+            "speedup_vs_fp64_form": (fp64_ms / 1e3) / t2r,
+            "solve": {"status": info["status_name"], "iters_inner": info["iters"],
+                      "outer": info["outer"], "matvecs": info["matvecs"],
+                      "matvecs_fp64": info["matvecs_fp64"], "rel_res_true": info["rel_res_true"],
+                      "qext": float(q[0, 0]), "qabs": float(q[0, 1])},
+            "matvec_only": {"c64_per_s": rates["c64"], "c128_per_s": rates["c128"],
+                            "c64_effective_hbm_frac": c64_matvec_bytes * rates["c64"] / 1e9 / peaks["hbm_gbs"]},
+            "roofline": roof,
+            "kernels": per_kernel,
+            "gpu_launches": int(trace.get("all_launches", (0, 0))[1]),
+            "clocks": clk,
+        }
+    if not args.no_e2e:
+        e2e = run_e2e(args, occ, opts, prop, pol, dirs, world, dev)
+        if result is not None:
+            result["e2e"] = e2e
+    p.close()
+    return result
+
+
+def run_e2e(args, occ, opts, prop, pol, dirs, world, dev):
+    """The same metric through the C-ABI from host memory: lattice upload,
+    D-matrix, solve, P copied back to pinned host memory, scattering results
+    on the host, handle freed -- all inside the timed region."""
+    import torch
+    from paper_0704_0037_gb300 import dda
+    steps = max(2, args.steps // 2)
+    P_host = None
+    mv = 0
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        p = dda.Particle(occ, [M_INDEX], X_SIZE, volume_corrected=True)
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+        P = torch.empty((1, 3, p.n_occ), dtype=torch.complex128, device=dev)
+        st, info, _ = dda.dda_solve(p.h, opts, prop, pol, P)
+        if P_host is None:
+            P_host = torch.empty(P.shape, dtype=P.dtype, pin_memory=True)
+        P_host.copy_(P)
+        F, q = dda.dda_scatter(p.h, dda.DDA_LDR, P, prop, pol, dirs)
+        torch.cuda.synchronize()
+        mv += info[0]["matvecs"]
+        h2d = occ.nbytes + 16 + 6 * 8 * 2
+        d2h = P_host.numel() * 16 + F.size * 16 + q.size * 8
+        p.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([dt], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        dt = float(tt.item())
+        mm = torch.tensor([mv], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(mm, op=torch.distributed.ReduceOp.SUM)
+        mv = int(mm.item())
+    return {"value": mv / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps, "s_per_step": dt / steps}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(n, n_products):
+    """Oracle (CPU, complex128, full unsymmetrised D, scipy.fft) on the
+    workload: D build once, then n_products FFT products.  Returns
+    (products/s over the products, D build seconds, cores)."""
+    from oracle import dda as odda
+    from oracle.fft_matvec import _WORKERS
+    from paper_0704_0037_gb300 import inputs
+    occ = inputs.sphere(n)
+    n_occ = int((occ > 0).sum())
+    from oracle import lattice
+    prob = odda.Problem(occ, [M_INDEX], lattice.kd_volume_corrected(X_SIZE, n_occ))
+    t0 = time.perf_counter()
+    prob.dmat()
+    t_d = time.perf_counter() - t0
+    beta = prob.beta("ldr", (0, 0, 1), (1, 0, 0))
+    mv = prob.matvec(beta, "fft")
+    x = inputs.random_vectors(3, 1, n_occ)[0]
+    t0 = time.perf_counter()
+    for _ in range(n_products):
+        x = mv(x)
+    t_p = time.perf_counter() - t0
+    return n_products / t_p, t_d, _WORKERS
+
+
+def cpu_baseline(n):
+    rate, t_d, cores = oracle_sample(n, 2)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"2 FFT products of the CPU oracle (complex128, full unsymmetrised D, scipy.fft) "
+                      f"on the {n}^3 sphere after one D build ({t_d:.1f} s, not in the rate)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    n = args.n
+    from oracle import dda as odda
+    from oracle import lattice
+    from oracle.fft_matvec import _WORKERS
+    from paper_0704_0037_gb300 import inputs
+    occ = inputs.sphere(n)
+    n_occ = int((occ > 0).sum())
+    prob = odda.Problem(occ, [M_INDEX], lattice.kd_volume_corrected(X_SIZE, n_occ))
+    prob.dmat()
+    beta = prob.beta("ldr", (0, 0, 1), (1, 0, 0))
+    mv = prob.matvec(beta, "fft")
+    x = inputs.random_vectors(3, 1, n_occ)[0]
+    for _ in range(args.warmup):
+        mv(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = mv(x)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = (f"each step one FFT product of the CPU oracle (complex128, full unsymmetrised D, "
+              f"scipy.fft, {_WORKERS} threads) on the {n}^3 sphere; D built once before warm-up")
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(n, "CPU run"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _WORKERS, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group(backend="nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(args.n)
+        print(json.dumps(res))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * dda.h -- C-ABI of the GB300 (sm_103a) discrete dipole approximation library.
+ *
+ * The library computes the DDA of Yurkin, Maltsev & Hoekstra
+ * (arXiv:0704.0037): the dipole polarizations P of Eq. (1), obtained by
+ * solving the Jacobi-symmetrised system of Eqs. (2)-(3),
+ *
+ *     x_i - sum_{j != i} beta_i G_ij beta_j x_j = beta_i E_inc,i ,   P_i = beta_i x_i,
+ *
+ * with the interaction-matrix product done by zero-padded FFT convolution
+ * split into 1D transforms with pruning (Sec. 2, performance paragraph),
+ * inside the complex-symmetric Krylov solvers of Sec. 2 (QMR, Bi-CG,
+ * Bi-CGSTAB, CGNR), stopped on the relative residual norm (default 1e-5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an int status (enum dda_status); no exception, abort
+ *   or longjmp crosses the ABI.  A negative status sets a per-handle message
+ *   readable with dda_last_error().  Nothing is silently downgraded: there is
+ *   no CPU fallback, and a missing or failing GPU gives DDA_ERR_CUDA.
+ * - Units: lengths in dipole sizes d; kd = k d; |E0| = 1; the polarizations
+ *   are dimensionless (alpha in units of d^3), Gaussian units.
+ * - Lattice: a box of nx*ny*nz cells, host arrays with x fastest
+ *   (index = (iz*ny + iy)*nx + ix); cell centres r = ((2i+1-n)/2) per axis, so
+ *   the origin (and the phase origin of E_inc) is the box centre.
+ * - Occupied ("real") dipoles are numbered 0..N_occ-1 in that x-fastest scan
+ *   order.  A complex vector on the dipoles is laid out [nrhs][3][N_occ],
+ *   interleaved (re, im): complex128 (16 B) or complex64 (8 B) per element.
+ * - The handle owns all its device workspace (FFT of G, padded FFT buffers,
+ *   Krylov vectors).  Buffers passed as *_dev are caller-owned device memory
+ *   (e.g. torch tensors); *_host pointers are caller-owned host memory.
+ * - All device work is enqueued on the stream given at dda_init_lattice
+ *   (NULL = legacy default stream).  Calls that return host results
+ *   (dda_solve, dda_scatter) synchronise that stream before returning.
+ * - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef DDA_H
+#define DDA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dda_ctx* dda_t;                 /* opaque handle */
+
+enum dda_status {
+  DDA_OK = 0,
+  DDA_NOT_CONVERGED = 1,   /* maxiter reached; results are those of the last iterate   */
+  DDA_BREAKDOWN = 2,       /* Lanczos/Bi-CG breakdown (a zero pivot), no look-ahead       */
+  DDA_ERR_ARG = -1,        /* invalid argument (NULL pointer, size, enum value)          */
+  DDA_ERR_CUDA = -2,       /* a CUDA call failed (message holds cudaGetErrorString)      */
+  DDA_ERR_OOM = -3,        /* device allocation failed                                   */
+  DDA_ERR_STATE = -4,      /* call out of order (e.g. product before dda_build_Dmatrix)  */
+  DDA_ERR_NONFINITE = -5,  /* a NaN/Inf appeared in a solver reduction                   */
+  DDA_ERR_TIMEOUT = -6     /* reserved: a bounded device wait gave up                    */
+};
+
+/* Polarizability prescriptions of Sec. 2: Clausius-Mossotti, radiative
+ * reaction, lattice dispersion relation, corrected LDR.  All are diagonal. */
+enum dda_pol { DDA_CM = 0, DDA_RR = 1, DDA_LDR = 2, DDA_CLDR = 3 };
+
+/* Iterative solvers of Sec. 2; QMR and Bi-CG use the complex symmetry of A. */
+enum dda_solver { DDA_QMR_CS = 0, DDA_BICG_CS = 1, DDA_BICGSTAB = 2, DDA_CGNR = 3 };
+
+/* Arithmetic of the product / solve.  DDA_FP64: complex128 everywhere (the
+ * paper's choice, Sec. 2).  DDA_FP32_REFINED: complex64 vectors and FFTs with
+ * FP64 D-matrix build, Krylov scalars, inner products and an FP64 outer
+ * iterative refinement on the true residual. */
+enum dda_prec { DDA_FP64 = 0, DDA_FP32_REFINED = 1 };
+
+/*
+ * dda_init_lattice -- create a handle for one particle (Sec. 2 Eq. (1); the
+ * lattice and the volume correction of Sec. 3.1).
+ *   out        : receives the new handle (set to NULL on failure).
+ *   nx,ny,nz   : box size in cells, each >= 1.
+ *   occ_host   : nx*ny*nz bytes, x fastest; 0 = void, k in 1..n_mat = material k.
+ *   n_mat      : number of materials, 1..255.
+ *   m_host     : 2*n_mat doubles, refractive index of material k as (re, im).
+ *   kd         : k*d if volume_corrected == 0; otherwise the size parameter
+ *                x = k a_eq and the library sets kd = x (4 pi / (3 N_occ))^(1/3)
+ *                so that N_occ d^3 equals the sphere volume (Sec. 3.1).
+ *   cuda_stream: cudaStream_t on which all device work is enqueued.
+ * Errors: DDA_ERR_ARG (bad sizes, no occupied cell, material index > n_mat),
+ *   DDA_ERR_CUDA / DDA_ERR_OOM.  Copies what it needs from the host arrays.
+ */
+int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_t* occ_host,
+                     int n_mat, const double* m_host, double kd, int volume_corrected,
+                     void* cuda_stream);
+
+/*
+ * dda_build_Dmatrix -- FFT of the Green's tensor on the padded grid (Sec. 2:
+ * the product is an FFT convolution and the symmetry of the interaction
+ * matrix reduces the memory of its Fourier transform).
+ * Builds G (FP64) on an M_x*M_y*M_z grid with M >= 2n - 1 (7-smooth), takes
+ * its 3D FFT in FP64 and keeps the 6 components on the octant
+ * k_mu in [0, M_mu/2] (the rest follows from parity), pre-scaled by
+ * 1/(M_x M_y M_z).  prec = DDA_FP32_REFINED also keeps a complex64 copy.
+ * Errors: DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM.
+ */
+int dda_build_Dmatrix(dda_t h, int prec);
+
+/*
+ * dda_set_beta -- polarizability and beta = sqrt(alpha) (Eq. (2), principal
+ * branch) used by dda_matvec for each right-hand side.
+ *   pol_prescription : enum dda_pol.
+ *   nrhs             : number of right-hand sides, >= 1.
+ *   prop_host        : 3*nrhs doubles, unit propagation vectors a (LDR's S term
+ *                      and CLDR's a_mu^2 depend on them).
+ *   polvec_host      : 6*nrhs doubles, polarisation e of each RHS as 3 complex
+ *                      (re, im) -- LDR's S = sum_mu (a_mu e_mu)^2.
+ * Errors: DDA_ERR_ARG.  The beta table is computed on the device in FP64.
+ */
+int dda_set_beta(dda_t h, int pol_prescription, int nrhs, const double* prop_host,
+                 const double* polvec_host);
+
+/*
+ * dda_matvec -- y = A x with A of Eq. (2), for nrhs right-hand sides:
+ *   y_i = x_i - beta_i sum_{j != i} G_ij beta_j x_j.
+ *   prec  : DDA_FP64 -> x, y are complex128; DDA_FP32_REFINED -> complex64.
+ *   x_dev : caller-owned device buffer [nrhs][3][N_occ] (read only).
+ *   y_dev : caller-owned device buffer [nrhs][3][N_occ] (written); must not
+ *           alias x_dev.
+ *   nrhs  : must not exceed the nrhs of the last dda_set_beta; RHS r uses
+ *           beta table r.
+ * Errors: DDA_ERR_STATE (no D-matrix of that precision, no beta),
+ *   DDA_ERR_ARG, DDA_ERR_CUDA.  Asynchronous on the handle's stream.
+ */
+int dda_matvec(dda_t h, int prec, const void* x_dev, void* y_dev, int nrhs);
+
+/*
+ * dda_matvec_adjoint -- y = A^H x = conj(A conj(x)) (A is complex symmetric,
+ * Eq. (2)); the product CGNR needs.  Same arguments as dda_matvec.
+ */
+int dda_matvec_adjoint(dda_t h, int prec, const void* x_dev, void* y_dev, int nrhs);
+
+typedef struct {
+  int solver;           /* enum dda_solver                                       */
+  int pol;              /* enum dda_pol: polarizability prescription             */
+  int prec;             /* enum dda_prec                                         */
+  double tol;           /* stop when ||b - A x||_2 / ||b||_2 < tol (Sec. 2: 1e-5) */
+  int maxiter;          /* iterations per RHS (inner iterations summed for FP32)  */
+  double inner_tol;     /* FP32_REFINED: relative tolerance of each inner solve   */
+  int checkpoint_every; /* reserved, 0                                            */
+} dda_solve_opts;
+
+typedef struct {
+  int status;           /* enum dda_status of this RHS                           */
+  int iters;            /* solver iterations (all inner iterations for FP32)      */
+  int matvecs;          /* products with A or A^H (any precision)                 */
+  int matvecs_fp64;     /* of which in FP64                                       */
+  int outer;            /* FP32_REFINED: refinement steps; FP64: 0                */
+  double rel_res_true;  /* ||b - A x|| / ||b|| recomputed in FP64 at exit         */
+  double rel_res_recur; /* the solver's own residual estimate at exit             */
+  double seconds;       /* wall time of this RHS                                  */
+} dda_solve_info;
+
+/*
+ * dda_solve -- solve Eq. (3) for nrhs incident plane waves and return
+ * P = beta x (Eq. (3)).  Starts from x0 = 0.
+ *   opts      : solver options (host).
+ *   prop_host : 3*nrhs doubles, unit propagation vectors.
+ *   pol_host  : 6*nrhs doubles, unit polarisations (complex, re/im pairs).
+ *   P_dev     : caller-owned device buffer [nrhs][3][N_occ] complex128 (out).
+ *   res_hist  : optional host [nrhs][hist_len] relative residual per iteration
+ *               (index 0 = 1.0 before the first iteration); unused tail = -1.
+ *   info      : host array of nrhs dda_solve_info.
+ * Also leaves beta set for these RHS (as dda_set_beta).  Requires
+ * dda_build_Dmatrix for DDA_FP64, and with DDA_FP32_REFINED for that mode.
+ * Returns the worst per-RHS status (errors first, then BREAKDOWN,
+ * NOT_CONVERGED).  Synchronises the stream.
+ */
+int dda_solve(dda_t h, const dda_solve_opts* opts, int nrhs, const double* prop_host,
+              const double* pol_host, void* P_dev, double* res_hist, int hist_len,
+              dda_solve_info* info);
+
+/*
+ * dda_scatter -- scattering quantities of Sec. 3.1 from P (FP64 sums).
+ *   pol_prescription : the prescription P was computed with (Q_abs needs alpha).
+ *   P_dev     : device [nrhs][3][N_occ] complex128.
+ *   prop_host, pol_host : as in dda_solve (E_inc for Q_ext, alpha for Q_abs).
+ *   n_dir, dirs_host : n_dir unit directions n (3 doubles each), may be 0.
+ *   weights_host     : optional n_dir quadrature weights (sum 4 pi); when given,
+ *                      Q_sca = (1/(pi x^2)) sum_k w_k |F(n_k)|^2.
+ *   F_out_host : host [nrhs][n_dir][3] complex (re, im): the amplitude
+ *                F(n) = -i kd^3 (I - n n) sum_j P_j exp(-i kd n.r_j).
+ *   q_out_host : host [nrhs][3] = (Q_ext, Q_abs, Q_sca); Q_sca is NaN without
+ *                weights.  x = kd (3 N_occ / (4 pi))^(1/3) normalises Q.
+ * Synchronises the stream.
+ */
+int dda_scatter(dda_t h, int pol_prescription, const void* P_dev, int nrhs,
+                const double* prop_host, const double* pol_host, int n_dir,
+                const double* dirs_host, const double* weights_host, double* F_out_host,
+                double* q_out_host);
+
+/*
+ * dda_mueller_plane -- S11(theta) in the xz scattering plane (Sec. 3.1: all
+ * Mueller elements in one scattering plane; S11 is the one the paper plots)
+ * from the amplitudes of x- and y-polarised incidence along +z evaluated at
+ * n = (sin t, 0, cos t): S2 = theta.F_x, S4 = -y.F_x, S3 = -theta.F_y,
+ * S1 = y.F_y (Bohren-Huffman amplitude matrix), S11 = (|S1|^2+...+|S4|^2)/2.
+ *   F_xpol_host, F_ypol_host : [n_theta][3] complex (as dda_scatter returns).
+ *   theta_deg_host : n_theta angles in degrees.   s11_out_host : n_theta doubles.
+ * Host-only arithmetic; no device work.
+ */
+int dda_mueller_plane(int n_theta, const double* theta_deg_host, const double* F_xpol_host,
+                      const double* F_ypol_host, double* s11_out_host);
+
+/*
+ * dda_trace -- per-kernel timing (the paper reports only whole-run times,
+ * Fig. 3; this is the library's own tracing).  enable != 0 starts recording a
+ * CUDA event pair around each launch of the product passes P1..P5, the
+ * D-matrix build and the far-field kernels on the handle's stream, and
+ * resets the totals; 0 stops.  Adds two event records per traced launch.
+ */
+int dda_trace(dda_t h, int enable);
+
+/*
+ * dda_trace_read -- totals since dda_trace(h, 1), after waiting for the
+ * recorded events.  For k < min(max_n, *n_out): names_out + 32*k receives the
+ * kernel name (NUL-terminated), ms_out[k] the summed duration in ms and
+ * count_out[k] the number of launches.  *n_out = number of entries.  Entry 0
+ * is "all_launches": ms 0, count = every kernel launch this library made (in
+ * any handle) since dda_trace(h, 1).
+ */
+int dda_trace_read(dda_t h, int max_n, char* names_out, double* ms_out, long long* count_out,
+                   int* n_out);
+
+/* Queries. */
+int dda_n_occ(dda_t h, long long* n_occ);
+int dda_kd(dda_t h, double* kd);
+int dda_grid(dda_t h, int* grid3);              /* padded (M_x, M_y, M_z)            */
+int dda_positions(dda_t h, int* ijk_host);      /* [N_occ][3] lattice indices (ix,iy,iz) */
+const char* dda_last_error(dda_t h);            /* never NULL; "" if no error        */
+int dda_free(dda_t h);                          /* releases all handle memory; NULL ok */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDA_H */

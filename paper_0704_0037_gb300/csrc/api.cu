@@ -1,0 +1,391 @@
+// C-ABI entry points: handle, lattice, beta tables, products, queries.
+// Equation and section references are to Yurkin, Maltsev & Hoekstra,
+// arXiv:0704.0037.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace dda;
+
+int dda_fail(dda_t h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int dda_cuda_fail(dda_t h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a non-sticky error so the handle stays usable
+  return dda_fail(h, e == cudaErrorMemoryAllocation ? DDA_ERR_OOM : DDA_ERR_CUDA, m);
+}
+
+namespace {
+
+// exp(-2 pi i m / M) for m < M, in long double, for the three axes.
+template <typename R>
+std::vector<cpx<R>> twiddles(const Geom& g) {
+  std::vector<cpx<R>> t;
+  const long double twopi = 6.283185307179586476925286766559L;
+  for (int M : {g.Mx, g.My, g.Mz})
+    for (int m = 0; m < M; ++m) {
+      long double a = twopi * (long double)m / (long double)M;
+      t.push_back(mk<R>((R)cosl(a), (R)(-sinl(a))));
+    }
+  return t;
+}
+
+template <typename R>
+int ensure_work(dda_t h, Work<R>& w) {
+  const Geom& g = h->g;
+  if (!w.tw) {
+    std::vector<cpx<R>> t = twiddles<R>(g);
+    if (cudaMalloc(&w.tw, t.size() * sizeof(cpx<R>)) != cudaSuccess) {
+      w.tw = nullptr;
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "cannot allocate twiddle tables");
+    }
+    DDA_CK(h, cudaMemcpy(w.tw, t.data(), t.size() * sizeof(cpx<R>), cudaMemcpyHostToDevice));
+  }
+  if (!w.B1) {
+    if (cudaMalloc(&w.B1, g.b1() * sizeof(cpx<R>)) != cudaSuccess) {
+      w.B1 = nullptr;
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "cannot allocate FFT work buffer B1");
+    }
+  }
+  if (!w.B2) {
+    if (cudaMalloc(&w.B2, g.b2() * sizeof(cpx<R>)) != cudaSuccess) {
+      w.B2 = nullptr;
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "cannot allocate FFT work buffer B2");
+    }
+  }
+  return DDA_OK;
+}
+
+template <typename R>
+void free_work(Work<R>& w) {
+  cudaFree(w.B1); cudaFree(w.B2); cudaFree(w.tw); cudaFree(w.D); cudaFree(w.beta);
+  w = Work<R>();
+}
+
+// ---------------------------------------------------------------- beta (O3)
+__device__ c128 csqrt_principal(c128 z) {
+  const double r = hypot(z.x, z.y);
+  if (r == 0.0) return mk<double>(0.0, 0.0);
+  if (z.x >= 0.0) {
+    const double t = sqrt(0.5 * (r + z.x));
+    return mk<double>(t, z.y / (2.0 * t));
+  }
+  const double t = sqrt(0.5 * (r - z.x));
+  return mk<double>(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+
+__device__ c128 cdiv(c128 a, c128 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return mk<double>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// Polarizability prescriptions of Sec. 2 (formulas of the cited works):
+//   1/alpha = 1/alpha_CM + c_corr kd^2 - (2/3) i kd^3   (RR: c_corr = 0),
+//   LDR: c_corr = b1 + b2 m^2 + b3 S m^2, S = sum (a_mu e_mu)^2;
+//   CLDR: component mu uses b3 m^2 a_mu^2;  CM: 1/alpha = 1/alpha_CM.
+// beta = sqrt(alpha) (Eq. (2)), principal branch.
+__global__ void k_beta(int nrhs, int n_mat, const double* __restrict__ m, int presc,
+                       const double* __restrict__ prop, const double* __restrict__ pol, double kd,
+                       c128* __restrict__ b64, c64* __restrict__ b32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrhs * n_mat * 3) return;
+  const int mu = i % 3;
+  const int k = (i / 3) % n_mat;
+  const int r = i / (3 * n_mat);
+  const double b1 = -1.8915316, b2 = 0.1648469, b3 = -1.7700004;
+  const c128 mm = mk<double>(m[2 * k], m[2 * k + 1]);
+  const c128 eps = mm * mm;
+  const double pi = 3.141592653589793238462643;
+  // alpha_CM = (3/4pi)(eps-1)/(eps+2)  ->  1/alpha_CM = (4pi/3)(eps+2)/(eps-1)
+  c128 inv = cdiv(eps + mk<double>(2.0, 0.0), eps - mk<double>(1.0, 0.0));
+  inv = mk<double>(inv.x * (4.0 * pi / 3.0), inv.y * (4.0 * pi / 3.0));
+  const double k2 = kd * kd, k3 = kd * kd * kd;
+  const c128 m2 = eps;
+  if (presc != DDA_CM) inv = inv + mk<double>(0.0, -(2.0 / 3.0) * k3);
+  if (presc == DDA_LDR) {
+    const double* a = prop + 3 * r;
+    const double* e = pol + 6 * r;
+    c128 S = mk<double>(0.0, 0.0);
+    for (int q = 0; q < 3; ++q) {
+      const c128 ae = mk<double>(a[q] * e[2 * q], a[q] * e[2 * q + 1]);
+      S = S + ae * ae;
+    }
+    const c128 corr = mk<double>(b1, 0.0) + mk<double>(b2, 0.0) * m2 + mk<double>(b3, 0.0) * S * m2;
+    inv = inv + mk<double>(corr.x * k2, corr.y * k2);
+  } else if (presc == DDA_CLDR) {
+    const double am = prop[3 * r + mu];
+    const c128 corr = mk<double>(b1, 0.0) + mk<double>(b2, 0.0) * m2 + mk<double>(b3 * am * am, 0.0) * m2;
+    inv = inv + mk<double>(corr.x * k2, corr.y * k2);
+  }
+  const c128 alpha = cdiv(mk<double>(1.0, 0.0), inv);
+  const c128 beta = csqrt_principal(alpha);
+  b64[i] = beta;
+  b32[i] = mk<float>((float)beta.x, (float)beta.y);
+}
+
+bool finite_all(const double* p, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+int dda_beta_internal(dda_t h, int presc, int nrhs, const double* prop, const double* pol) {
+  if (presc < DDA_CM || presc > DDA_CLDR) return dda_fail(h, DDA_ERR_ARG, "unknown polarizability prescription");
+  if (nrhs < 1) return dda_fail(h, DDA_ERR_ARG, "nrhs must be >= 1");
+  if (!prop || !pol) return dda_fail(h, DDA_ERR_ARG, "prop and pol must not be NULL");
+  if (!finite_all(prop, 3 * nrhs) || !finite_all(pol, 6 * nrhs))
+    return dda_fail(h, DDA_ERR_ARG, "non-finite propagation or polarisation vector");
+  const int nb = nrhs * h->n_mat * 3;
+  if (h->beta_cap < nrhs) {
+    cudaFree(h->w64.beta); cudaFree(h->w32.beta);
+    h->w64.beta = nullptr; h->w32.beta = nullptr; h->beta_cap = 0; h->beta_nrhs = 0;
+    if (cudaMalloc(&h->w64.beta, nb * sizeof(c128)) != cudaSuccess ||
+        cudaMalloc(&h->w32.beta, nb * sizeof(c64)) != cudaSuccess) {
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "cannot allocate beta tables");
+    }
+  }
+  double* dbuf = nullptr;
+  const size_t nd = 2 * h->n_mat + 3 * nrhs + 6 * nrhs;
+  DDA_CK(h, cudaMalloc(&dbuf, nd * sizeof(double)));
+  std::vector<double> hb(nd);
+  std::memcpy(hb.data(), h->m.data(), 2 * h->n_mat * sizeof(double));
+  std::memcpy(hb.data() + 2 * h->n_mat, prop, 3 * nrhs * sizeof(double));
+  std::memcpy(hb.data() + 2 * h->n_mat + 3 * nrhs, pol, 6 * nrhs * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(dbuf, hb.data(), nd * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    k_beta<<<(nb + 127) / 128, 128, 0, h->stream>>>(nrhs, h->n_mat, dbuf, presc, dbuf + 2 * h->n_mat,
+                                                    dbuf + 2 * h->n_mat + 3 * nrhs, h->kd,
+                                                    h->w64.beta, h->w32.beta); count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(dbuf);
+  if (e != cudaSuccess) return dda_cuda_fail(h, e, "beta build");
+  if (nrhs > h->beta_cap) h->beta_cap = nrhs;
+  h->beta_nrhs = nrhs;
+  h->beta_presc = presc;
+  return DDA_OK;
+}
+
+// ---------------------------------------------------------------- C-ABI
+
+extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_t* occ,
+                                int n_mat, const double* m, double kd, int volume_corrected,
+                                void* cuda_stream) {
+  if (!out) return DDA_ERR_ARG;
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 65535 || ny > 65535 || nz > 65535 || !occ || !m ||
+      n_mat < 1 || n_mat > 255 || !(kd > 0.0) || !std::isfinite(kd))
+    return DDA_ERR_ARG;
+  if (!finite_all(m, 2 * n_mat)) return DDA_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return DDA_ERR_CUDA;
+  }
+  dda_ctx* h = new (std::nothrow) dda_ctx();
+  if (!h) return DDA_ERR_OOM;
+  Geom& g = h->g;
+  g.nx = nx; g.ny = ny; g.nz = nz;
+  g.nrows = ny * nz;
+  h->row_off_h.assign((size_t)g.nrows + 1, 0);
+  std::vector<uint8_t> mat;
+  for (int r = 0; r < g.nrows; ++r) {
+    const uint8_t* row = occ + (size_t)r * nx;
+    for (int ix = 0; ix < nx; ++ix) {
+      if (row[ix]) {
+        if (row[ix] > n_mat) { delete h; return DDA_ERR_ARG; }
+        h->xi_h.push_back((uint16_t)ix);
+        mat.push_back((uint8_t)(row[ix] - 1));
+      }
+    }
+    h->row_off_h[r + 1] = (long long)h->xi_h.size();
+  }
+  g.n_occ = (long long)h->xi_h.size();
+  if (g.n_occ == 0) { delete h; return DDA_ERR_ARG; }
+  g.Mx = smooth_size(2 * nx - 1);
+  g.My = smooth_size(2 * ny - 1);
+  g.Mz = smooth_size(2 * nz - 1);
+  g.px = make_plan(g.Mx); g.py = make_plan(g.My); g.pz = make_plan(g.Mz);
+  g.tr = &h->tracer;
+  h->n_mat = n_mat;
+  h->m.assign(m, m + 2 * n_mat);
+  // Sec. 3.1 volume correction: N_occ d^3 = (4/3) pi a^3  =>  kd = x (4 pi / (3 N_occ))^(1/3)
+  h->kd = volume_corrected ? kd * std::cbrt(4.0 * M_PI / (3.0 * (double)g.n_occ)) : kd;
+  h->stream = (cudaStream_t)cuda_stream;
+  int rc = DDA_OK;
+  if (cudaMalloc(&h->d_row_off, h->row_off_h.size() * sizeof(long long)) != cudaSuccess ||
+      cudaMalloc(&h->d_xi, h->xi_h.size() * sizeof(uint16_t)) != cudaSuccess ||
+      cudaMalloc(&h->d_mat, mat.size()) != cudaSuccess) {
+    cudaGetLastError();
+    rc = DDA_ERR_OOM;
+  } else if (cudaMemcpy(h->d_row_off, h->row_off_h.data(), h->row_off_h.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(h->d_xi, h->xi_h.data(), h->xi_h.size() * sizeof(uint16_t),
+                        cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(h->d_mat, mat.data(), mat.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    rc = DDA_ERR_CUDA;
+  }
+  if (rc != DDA_OK) { dda_free(h); return rc; }
+  *out = h;
+  return DDA_OK;
+}
+
+extern "C" int dda_build_Dmatrix(dda_t h, int prec) {
+  if (!h) return DDA_ERR_ARG;
+  if (prec != DDA_FP64 && prec != DDA_FP32_REFINED) return dda_fail(h, DDA_ERR_ARG, "unknown precision");
+  if (h->g.px.nst < 0 || h->g.py.nst < 0 || h->g.pz.nst < 0)
+    return dda_fail(h, DDA_ERR_ARG, "padded grid is not 7-smooth");
+  int rc = ensure_work<double>(h, h->w64);
+  if (rc != DDA_OK) return rc;
+  if (prec == DDA_FP32_REFINED) {
+    rc = ensure_work<float>(h, h->w32);
+    if (rc != DDA_OK) return rc;
+  }
+  return dda_build_D_internal(h, prec == DDA_FP32_REFINED);
+}
+
+extern "C" int dda_set_beta(dda_t h, int presc, int nrhs, const double* prop, const double* pol) {
+  if (!h) return DDA_ERR_ARG;
+  return dda_beta_internal(h, presc, nrhs, prop, pol);
+}
+
+static int matvec_common(dda_t h, int prec, const void* x, void* y, int nrhs, bool adjoint) {
+  if (!h) return DDA_ERR_ARG;
+  if (!x || !y) return dda_fail(h, DDA_ERR_ARG, "x and y must not be NULL");
+  if (x == y) return dda_fail(h, DDA_ERR_ARG, "x and y must not alias");
+  if (nrhs < 1) return dda_fail(h, DDA_ERR_ARG, "nrhs must be >= 1");
+  if (nrhs > h->beta_nrhs) return dda_fail(h, DDA_ERR_STATE, "beta not set for that many RHS (dda_set_beta)");
+  cudaError_t e;
+  if (prec == DDA_FP64) {
+    if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "FP64 D-matrix not built");
+    e = launch_matvec<double>(h->g, h->lat(), h->w64, h->w64.beta, h->n_mat, (const c128*)x,
+                              (c128*)y, nrhs, adjoint, h->stream);
+  } else if (prec == DDA_FP32_REFINED) {
+    if (!h->w32.have_D) return dda_fail(h, DDA_ERR_STATE, "FP32 D-matrix not built");
+    e = launch_matvec<float>(h->g, h->lat(), h->w32, h->w32.beta, h->n_mat, (const c64*)x,
+                             (c64*)y, nrhs, adjoint, h->stream);
+  } else {
+    return dda_fail(h, DDA_ERR_ARG, "unknown precision");
+  }
+  if (e != cudaSuccess) return dda_cuda_fail(h, e, "matvec launch");
+  return DDA_OK;
+}
+
+extern "C" int dda_matvec(dda_t h, int prec, const void* x, void* y, int nrhs) {
+  return matvec_common(h, prec, x, y, nrhs, false);
+}
+
+extern "C" int dda_matvec_adjoint(dda_t h, int prec, const void* x, void* y, int nrhs) {
+  return matvec_common(h, prec, x, y, nrhs, true);
+}
+
+extern "C" int dda_solve(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
+                         const double* pol, void* P_dev, double* hist, int hist_len,
+                         dda_solve_info* info) {
+  if (!h) return DDA_ERR_ARG;
+  if (!o || !prop || !pol || !P_dev || !info || nrhs < 1 || (hist && hist_len < 1))
+    return dda_fail(h, DDA_ERR_ARG, "bad dda_solve arguments");
+  if (o->solver < DDA_QMR_CS || o->solver > DDA_CGNR) return dda_fail(h, DDA_ERR_ARG, "unknown solver");
+  if (o->prec != DDA_FP64 && o->prec != DDA_FP32_REFINED) return dda_fail(h, DDA_ERR_ARG, "unknown precision");
+  if (!(o->tol > 0.0) || o->maxiter < 1) return dda_fail(h, DDA_ERR_ARG, "tol must be > 0 and maxiter >= 1");
+  if (o->prec == DDA_FP32_REFINED && !(o->inner_tol > 0.0 && o->inner_tol < 1.0))
+    return dda_fail(h, DDA_ERR_ARG, "inner_tol must be in (0, 1)");
+  if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "FP64 D-matrix not built");
+  if (o->prec == DDA_FP32_REFINED && !h->w32.have_D)
+    return dda_fail(h, DDA_ERR_STATE, "FP32 D-matrix not built");
+  return dda_solve_internal(h, o, nrhs, prop, pol, P_dev, hist, hist_len, info);
+}
+
+extern "C" int dda_scatter(dda_t h, int presc, const void* P_dev, int nrhs, const double* prop,
+                           const double* pol, int n_dir, const double* dirs, const double* w,
+                           double* F_out, double* q_out) {
+  if (!h) return DDA_ERR_ARG;
+  if (!P_dev || nrhs < 1 || !prop || !pol || n_dir < 0 || (n_dir > 0 && (!dirs || !F_out)) || !q_out)
+    return dda_fail(h, DDA_ERR_ARG, "bad dda_scatter arguments");
+  if (presc < DDA_CM || presc > DDA_CLDR) return dda_fail(h, DDA_ERR_ARG, "unknown polarizability prescription");
+  if (n_dir > 0 && !finite_all(dirs, 3 * n_dir)) return dda_fail(h, DDA_ERR_ARG, "non-finite direction");
+  return dda_scatter_internal(h, presc, P_dev, nrhs, prop, pol, n_dir, dirs, w, F_out, q_out);
+}
+
+extern "C" int dda_mueller_plane(int n_theta, const double* th, const double* Fx, const double* Fy,
+                                 double* s11) {
+  if (n_theta < 0 || (n_theta > 0 && (!th || !Fx || !Fy || !s11))) return DDA_ERR_ARG;
+  for (int i = 0; i < n_theta; ++i) {
+    const double t = th[i] * (M_PI / 180.0);
+    const double ct = std::cos(t), st = std::sin(t);
+    // theta_hat = (cos t, 0, -sin t), y_hat = (0, 1, 0)
+    const double* fx = Fx + 6 * i;
+    const double* fy = Fy + 6 * i;
+    const double s2r = ct * fx[0] - st * fx[4], s2i = ct * fx[1] - st * fx[5];
+    const double s4r = -fx[2], s4i = -fx[3];
+    const double s3r = -(ct * fy[0] - st * fy[4]), s3i = -(ct * fy[1] - st * fy[5]);
+    const double s1r = fy[2], s1i = fy[3];
+    s11[i] = 0.5 * (s1r * s1r + s1i * s1i + s2r * s2r + s2i * s2i + s3r * s3r + s3i * s3i +
+                    s4r * s4r + s4i * s4i);
+  }
+  return DDA_OK;
+}
+
+extern "C" int dda_n_occ(dda_t h, long long* n) {
+  if (!h || !n) return DDA_ERR_ARG;
+  *n = h->g.n_occ;
+  return DDA_OK;
+}
+
+extern "C" int dda_kd(dda_t h, double* kd) {
+  if (!h || !kd) return DDA_ERR_ARG;
+  *kd = h->kd;
+  return DDA_OK;
+}
+
+extern "C" int dda_grid(dda_t h, int* g3) {
+  if (!h || !g3) return DDA_ERR_ARG;
+  g3[0] = h->g.Mx; g3[1] = h->g.My; g3[2] = h->g.Mz;
+  return DDA_OK;
+}
+
+extern "C" int dda_positions(dda_t h, int* ijk) {
+  if (!h || !ijk) return DDA_ERR_ARG;
+  for (int r = 0; r < h->g.nrows; ++r) {
+    const int iy = r % h->g.ny, iz = r / h->g.ny;
+    for (long long i = h->row_off_h[r]; i < h->row_off_h[r + 1]; ++i) {
+      ijk[3 * i] = h->xi_h[i];
+      ijk[3 * i + 1] = iy;
+      ijk[3 * i + 2] = iz;
+    }
+  }
+  return DDA_OK;
+}
+
+extern "C" const char* dda_last_error(dda_t h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+extern "C" int dda_free(dda_t h) {
+  if (!h) return DDA_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  tr_destroy(&h->tracer);
+  free_work(h->w64);
+  free_work(h->w32);
+  cudaFree(h->d_row_off); cudaFree(h->d_xi); cudaFree(h->d_mat);
+  cudaFree(h->sv); cudaFree(h->d_part); cudaFree(h->d_scal); cudaFreeHost(h->h_scal);
+  cudaFree(h->d_tab); cudaFree(h->d_fpart);
+  cudaGetLastError();
+  delete h;
+  return DDA_OK;
+}

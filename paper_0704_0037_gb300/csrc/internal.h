@@ -1,0 +1,150 @@
+// Internal declarations of the DDA library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dda.h"
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace dda {
+
+// Per-kernel CUDA-event timing (dda_trace).  Kernels are identified by a
+// small fixed table of names; event pairs are resolved at sync points.
+enum TraceId {
+  TR_P1_C64, TR_P2_C64, TR_P3_C64, TR_P4_C64, TR_P5_C64,
+  TR_P1_C128, TR_P2_C128, TR_P3_C128, TR_P4_C128, TR_P5_C128,
+  TR_DB_GREEN, TR_DB_LINES, TR_DB_OCTANT, TR_FARFIELD, TR_QSUMS, TR_COUNT
+};
+struct Tracer {
+  bool on = false;
+  struct Rec { int id; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> pending;
+  cudaEvent_t open = nullptr;
+  double ms[TR_COUNT] = {};
+  long long cnt[TR_COUNT] = {};
+  long long launch_base = 0;
+};
+const char* trace_name(int id);
+void tr_begin(Tracer* t, cudaStream_t st);
+void tr_end(Tracer* t, cudaStream_t st, int id);
+void tr_flush(Tracer* t);
+void tr_reset(Tracer* t);
+void tr_destroy(Tracer* t);
+
+// Padded-grid geometry and the per-axis FFT plans.
+struct Geom {
+  int nx, ny, nz;          // lattice box
+  int Mx, My, Mz;          // padded grid, M >= 2n - 1, 7-smooth
+  int nrows;               // ny * nz rows along x
+  long long n_occ;         // occupied dipoles
+  FftPlan px, py, pz;      // plans for lengths Mx, My, Mz
+  Tracer* tr = nullptr;    // per-kernel timing, owned by the handle
+  long long oct() const { return (long long)(Mx / 2 + 1) * (My / 2 + 1) * (Mz / 2 + 1); }
+  long long b1() const { return 3LL * nrows * Mx; }          // [3][nz][ny][Mx]
+  long long b2() const { return 3LL * nz * My * Mx; }        // [3][nz][My][Mx]
+};
+
+// Lattice description on the device: occupied dipoles of row r = iz*ny + iy
+// are row_off[r] .. row_off[r+1]-1 (x-fastest order), at x = xi[i].
+struct LatticeDev {
+  const long long* row_off;
+  const uint16_t* xi;
+  const uint8_t* mat;
+};
+
+// Per-precision workspace of the FFT product.
+template <typename R>
+struct Work {
+  cpx<R>* B1 = nullptr;     // after the x pass
+  cpx<R>* B2 = nullptr;     // after the y pass (z pass in place)
+  cpx<R>* tw = nullptr;     // twiddles: [Mx] then [My] then [Mz], exp(-2 pi i m / M)
+  cpx<R>* D = nullptr;      // octant of FFT(G)/(Mx My Mz): [6][Mz/2+1][My/2+1][Mx/2+1]
+  cpx<R>* beta = nullptr;   // [nrhs][n_mat][3]
+  bool have_D = false;
+};
+
+// Launch helpers (matvec.cu)
+template <typename R>
+cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, const cpx<R>* beta,
+                          int n_mat, const cpx<R>* x, cpx<R>* y, int nrhs, bool adjoint,
+                          cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const FftPlan& p,
+                         const cpx<R>* tw, bool inverse, int n_in, int n_out, int nt, int n_outer,
+                         int n_batch, bool contig, long long in_sm, long long in_st,
+                         long long in_so, long long in_sb, long long out_sm, long long out_st,
+                         long long out_so, long long out_sb, cudaStream_t st);
+
+FftPlan make_plan(int M);
+int smooth_size(int lo);
+
+}  // namespace dda
+
+// The handle.
+struct dda_ctx {
+  dda::Geom g{};
+  int n_mat = 0;
+  std::vector<double> m;          // 2*n_mat
+  double kd = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<long long> row_off_h;
+  std::vector<uint16_t> xi_h;
+  long long* d_row_off = nullptr;
+  uint16_t* d_xi = nullptr;
+  uint8_t* d_mat = nullptr;
+  dda::Work<double> w64;
+  dda::Work<float> w32;
+  dda::Tracer tracer;
+  int beta_nrhs = 0;              // RHS count of the current beta tables
+  int beta_cap = 0;               // RHS capacity of the beta allocations
+  int beta_presc = -1;
+  std::string err;
+  // solver scratch (krylov.cu)
+  void* sv = nullptr;             // solver vectors, grown on demand
+  size_t sv_bytes = 0;
+  double* d_part = nullptr;       // reduction partials
+  void* d_scal = nullptr;         // device scalar state
+  void* h_scal = nullptr;         // pinned host mirror
+  // scatter scratch
+  double* d_tab = nullptr;
+  size_t tab_bytes = 0;
+  double* d_fpart = nullptr;
+  size_t fpart_bytes = 0;
+  dda::LatticeDev lat() const { return {d_row_off, d_xi, d_mat}; }
+};
+
+int dda_fail(dda_t h, int code, const std::string& msg);
+int dda_cuda_fail(dda_t h, cudaError_t e, const char* where);
+
+#define DDA_CK(h, call)                                      \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return dda_cuda_fail(h, e_, #call); \
+  } while (0)
+
+// beta tables on the device (api.cu)
+int dda_beta_internal(dda_t h, int presc, int nrhs, const double* prop, const double* pol);
+// D-matrix (dmatrix.cu)
+int dda_build_D_internal(dda_t h, bool want32);
+// solvers (krylov.cu)
+int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
+                       const double* pol, void* P_dev, double* hist, int hist_len,
+                       dda_solve_info* info);
+// scatter (scatter.cu)
+int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const double* prop,
+                         const double* pol, int n_dir, const double* dirs, const double* w,
+                         double* F_out, double* q_out);
+
+namespace dda {
+// Process-wide count of kernel launches made by this library (dda_trace_read
+// reports the increase since tracing was enabled).
+void count_launch();
+long long launch_total();
+}  // namespace dda

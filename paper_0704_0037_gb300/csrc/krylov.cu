@@ -1,0 +1,920 @@
+// Krylov solvers of arXiv:0704.0037, Sec. 2 (CGNR, Bi-CGSTAB, Bi-CG, QMR),
+// for A x = b of Eq. (3), with A of Eq. (2) applied by the FFT product.
+//
+// QMR and Bi-CG use the complex symmetry A = A^T (bilinear form u^T v);
+// Bi-CGSTAB and CGNR use Hermitian products (CGNR on A^H A, with
+// A^H y = conj(A conj y)).  Stopping rule (Sec. 2, 3.1): relative residual
+// ||b - A x|| / ||b|| < tol.  x0 = 0.
+//
+// Vectors live on the device in complex64 or complex128; every inner
+// product is accumulated in FP64 per thread, reduced per block with warp
+// shuffles, and the per-block partials are summed by a one-block kernel in a
+// fixed order, so reruns are bitwise identical.  The scalar recurrences
+// (Lanczos coefficients, Givens rotations, step lengths) run in FP64 on the
+// device; the host reads a small status record once per iteration.
+//
+// DDA_FP32_REFINED: complex64 inner solves of A d = r / ||r|| inside an FP64
+// iterative refinement x += ||r|| d, r = b - A x (FP64 product), which is
+// also the true residual the stop test uses.
+#include <chrono>
+#include <cmath>
+
+#include "internal.h"
+
+namespace dda {
+
+constexpr int kNB = 1024;     // max blocks of a vector kernel (partials per slot)
+constexpr int kSlots = 8;     // doubles per block in the partials array
+constexpr int kVT = 256;      // threads of vector kernels
+
+struct Scal {
+  double bnorm, res, sres, tol;
+  int done, status, half, pad;
+  c128 alpha, beta_k, beta_next, inv_beta, t, tau, delta, eps, inv_gamma, s1, s2;
+  double c1, c2;
+  c128 rho, rho_prev, omega, bstep;
+  double zz, ww;
+};
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce K per-thread values over the block and store them as this block's
+// partials part[k * kNB + blockIdx.x] (k = slot0 .. slot0+K-1).
+template <int K>
+__device__ void block_store(double (&v)[K], double* part, int slot0) {
+  __shared__ double sh[K][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = lane < nw ? sh[k][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) part[(slot0 + k) * kNB + blockIdx.x] = s;
+    }
+  }
+}
+
+// Sum slot `slot` of the partials of nb blocks; one block of kVT threads, fixed order.
+__device__ double fin(const double* part, int slot, int nb) {
+  __shared__ double sh[kVT];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[slot * kNB + i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ c128 cfin(const double* part, int slot, int nb) {
+  const double re = fin(part, slot, nb);
+  const double im = fin(part, slot + 1, nb);
+  return mk<double>(re, im);
+}
+
+__device__ __forceinline__ c128 csqrt_p(c128 z) {
+  const double r = hypot(z.x, z.y);
+  if (r == 0.0) return mk<double>(0.0, 0.0);
+  if (z.x >= 0.0) {
+    const double t = sqrt(0.5 * (r + z.x));
+    return mk<double>(t, z.y / (2.0 * t));
+  }
+  const double t = sqrt(0.5 * (r - z.x));
+  return mk<double>(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+__device__ __forceinline__ c128 cdivd(c128 a, c128 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return mk<double>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double cabs2(c128 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ bool cfinite(c128 a) { return isfinite(a.x) && isfinite(a.y); }
+
+template <typename R> __device__ __forceinline__ cpx<R> cs(c128 a) { return mk<R>((R)a.x, (R)a.y); }
+
+#define VLOOP(n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); \
+                      i += (long long)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------- generic kernels
+template <typename R, bool HERM>
+__global__ void __launch_bounds__(kVT) k_dot(const cpx<R>* __restrict__ a, const cpx<R>* __restrict__ b,
+                                             long long n, double* part, int slot, const Scal* s) {
+  if (s && s->done) return;
+  double v[2] = {0.0, 0.0};
+  VLOOP(n) {
+    const double ax = a[i].x, ay = HERM ? -(double)a[i].y : (double)a[i].y;
+    const double bx = b[i].x, by = b[i].y;
+    v[0] += ax * bx - ay * by;
+    v[1] += ax * by + ay * bx;
+  }
+  block_store<2>(v, part, slot);
+}
+
+// |a|^2 and, optionally, a^T a (bilinear)
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_norms(const cpx<R>* __restrict__ a, long long n, double* part,
+                                               const Scal* s) {
+  if (s && s->done) return;
+  double v[3] = {0.0, 0.0, 0.0};
+  VLOOP(n) {
+    const double x = a[i].x, y = a[i].y;
+    v[0] += x * x - y * y;
+    v[1] += 2.0 * x * y;
+    v[2] += x * x + y * y;
+  }
+  block_store<3>(v, part, 0);
+}
+
+template <typename R>
+__global__ void k_zero(cpx<R>* a, long long n) { VLOOP(n) a[i] = mk<R>(0, 0); }
+
+template <typename R>
+__global__ void k_copy(const cpx<R>* __restrict__ a, cpx<R>* __restrict__ b, long long n) {
+  VLOOP(n) b[i] = a[i];
+}
+
+// ---------------------------------------------------------------- RHS and P
+struct Wave { double a[3]; double e[6]; };
+
+// b_i = beta_i e exp(i kd a.r_i)  (Eq. (3)), rows in parallel, a warp per row
+template <typename R>
+__global__ void k_rhs(cpx<R>* __restrict__ b, LatticeDev lat, const c128* __restrict__ beta,
+                      long long n_occ, int nx, int ny, int nz, int nrows, double kd, Wave w) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int row = warp; row < nrows; row += nwarps) {
+    const int iy = row % ny, iz = row / ny;
+    const double ry = 0.5 * (2 * iy + 1 - ny), rz = 0.5 * (2 * iz + 1 - nz);
+    for (long long i = lat.row_off[row] + lane; i < lat.row_off[row + 1]; i += 32) {
+      const double rx = 0.5 * (2 * (int)lat.xi[i] + 1 - nx);
+      double sn, cn;
+      sincos(kd * (w.a[0] * rx + w.a[1] * ry + w.a[2] * rz), &sn, &cn);
+      const c128 ph = mk<double>(cn, sn);
+      for (int c = 0; c < 3; ++c) {
+        const c128 e = mk<double>(w.e[2 * c], w.e[2 * c + 1]);
+        const c128 v = beta[lat.mat[i] * 3 + c] * (e * ph);
+        b[c * n_occ + i] = cs<R>(v);
+      }
+    }
+  }
+}
+
+// P = beta x (Eq. (3)), FP64 output
+template <typename R>
+__global__ void k_pfinal(const cpx<R>* __restrict__ x, c128* __restrict__ P, const uint8_t* __restrict__ mat,
+                         const c128* __restrict__ beta, long long n_occ) {
+  VLOOP(3 * n_occ) {
+    const int c = (int)(i / n_occ);
+    const long long j = i - c * n_occ;
+    P[i] = beta[mat[j] * 3 + c] * to128(x[i]);
+  }
+}
+
+// ---------------------------------------------------------------- QMR-CS
+__global__ void k_qmr_init(Scal* s, const double* part, int nb, double tol) {
+  const c128 bb = cfin(part, 0, nb);
+  const double bn2 = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  s->tol = tol;
+  s->bnorm = sqrt(bn2);
+  s->res = 1.0;
+  s->done = 0; s->half = 0;
+  s->status = DDA_NOT_CONVERGED;
+  const c128 beta1 = csqrt_p(bb);
+  s->t = beta1;
+  s->beta_k = mk<double>(0.0, 0.0);
+  s->inv_beta = cabs2(beta1) > 0 ? cdivd(mk<double>(1.0, 0.0), beta1) : mk<double>(0.0, 0.0);
+  s->c1 = s->c2 = 1.0;
+  s->s1 = s->s2 = mk<double>(0.0, 0.0);
+  if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
+  else if (!isfinite(bn2) || !cfinite(bb)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
+  else if (cabs2(bb) == 0.0) { s->done = 1; s->status = DDA_BREAKDOWN; }
+}
+
+template <typename R>
+__global__ void k_qmr_start(const cpx<R>* __restrict__ b, cpx<R>* v, cpx<R>* r, cpx<R>* x,
+                            cpx<R>* vp, cpx<R>* p1, cpx<R>* p2, cpx<R>* a1, cpx<R>* a2, long long n,
+                            const Scal* s) {
+  const cpx<R> ib = cs<R>(s->inv_beta);
+  const cpx<R> z = mk<R>(0, 0);
+  VLOOP(n) {
+    const cpx<R> bi = b[i];
+    v[i] = bi * ib; r[i] = bi; x[i] = z; vp[i] = z; p1[i] = z; p2[i] = z; a1[i] = z; a2[i] = z;
+  }
+}
+
+__global__ void k_qmr_a(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const c128 a = cfin(part, 0, nb);
+  if (threadIdx.x == 0) s->alpha = a;
+}
+
+// vt = w - alpha v - beta_k vprev  (into vprev); partials of vt^T vt and |vt|^2
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ w, const cpx<R>* __restrict__ v,
+                                                cpx<R>* __restrict__ vp, long long n, const Scal* s,
+                                                double* part) {
+  if (s->done) return;
+  const cpx<R> al = cs<R>(s->alpha), bk = cs<R>(s->beta_k);
+  double acc[3] = {0.0, 0.0, 0.0};
+  VLOOP(n) {
+    const cpx<R> t = w[i] - al * v[i] - bk * vp[i];
+    vp[i] = t;
+    const double x = t.x, y = t.y;
+    acc[0] += x * x - y * y;
+    acc[1] += 2.0 * x * y;
+    acc[2] += x * x + y * y;
+  }
+  block_store<3>(acc, part, 0);
+}
+
+// Lanczos coefficient beta_{k+1}, the two previous Givens rotations applied to
+// column (beta_k, alpha_k, beta_{k+1}) of the tridiagonal matrix, the new
+// rotation, and the coefficients of the p / x / Ap / r updates.
+__global__ void k_qmr_b(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const c128 vtv = cfin(part, 0, nb);
+  const double vn2 = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  const c128 bn = csqrt_p(vtv);
+  const c128 bk = s->beta_k, al = s->alpha;
+  const c128 eps = s->s2 * bk;
+  const c128 tmp = scale<double>(bk, s->c2);
+  const c128 delta = scale<double>(tmp, s->c1) + s->s1 * al;
+  const c128 gt = scale<double>(al, s->c1) - conjg(s->s1) * tmp;
+  double c;
+  c128 sn;
+  const double ag = sqrt(cabs2(gt));
+  if (ag == 0.0) { c = 0.0; sn = mk<double>(1.0, 0.0); }
+  else {
+    c = ag / sqrt(cabs2(gt) + cabs2(bn));
+    sn = scale<double>(conjg(cdivd(bn, gt)), c);
+  }
+  const c128 gamma = scale<double>(gt, c) + sn * bn;
+  if (!cfinite(gamma) || !cfinite(vtv) || !isfinite(vn2)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  if (cabs2(gamma) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  s->tau = scale<double>(s->t, c);
+  s->t = mk<double>(0.0, 0.0) - conjg(sn) * s->t;
+  s->inv_gamma = cdivd(mk<double>(1.0, 0.0), gamma);
+  s->delta = delta;
+  s->eps = eps;
+  s->c2 = s->c1; s->s2 = s->s1;
+  s->c1 = c; s->s1 = sn;
+  s->beta_next = bn;
+  s->inv_beta = cabs2(bn) > 0.0 ? cdivd(mk<double>(1.0, 0.0), bn) : mk<double>(0.0, 0.0);
+  s->half = (sqrt(cabs2(vtv)) < 1e-30 * vn2) ? 1 : 0;
+}
+
+// v_{k+1} = vt / beta_{k+1}; p_k = (v_k - delta p_{k-1} - eps p_{k-2}) / gamma;
+// x += tau p_k; Ap_k likewise from w; r -= tau Ap_k; partial |r|^2.
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ vp, const cpx<R>* __restrict__ v,
+                                                const cpx<R>* __restrict__ w, const cpx<R>* __restrict__ p1,
+                                                cpx<R>* __restrict__ p2, const cpx<R>* __restrict__ a1,
+                                                cpx<R>* __restrict__ a2, cpx<R>* __restrict__ x,
+                                                cpx<R>* __restrict__ r, long long n, const Scal* s,
+                                                double* part) {
+  if (s->done) return;
+  const cpx<R> ib = cs<R>(s->inv_beta), ig = cs<R>(s->inv_gamma);
+  const cpx<R> de = cs<R>(s->delta), ep = cs<R>(s->eps), ta = cs<R>(s->tau);
+  double acc[1] = {0.0};
+  VLOOP(n) {
+    vp[i] = vp[i] * ib;
+    const cpx<R> p = (v[i] - de * p1[i] - ep * p2[i]) * ig;
+    p2[i] = p;
+    x[i] = x[i] + ta * p;
+    const cpx<R> ap = (w[i] - de * a1[i] - ep * a2[i]) * ig;
+    a2[i] = ap;
+    const cpx<R> rr = r[i] - ta * ap;
+    r[i] = rr;
+    acc[0] += (double)rr.x * rr.x + (double)rr.y * rr.y;
+  }
+  block_store<1>(acc, part, 0);
+}
+
+__global__ void k_qmr_c(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const double rn2 = fin(part, 0, nb);
+  if (threadIdx.x) return;
+  const double res = sqrt(rn2) / s->bnorm;
+  s->res = res;
+  if (!isfinite(res)) { s->status = DDA_ERR_NONFINITE; s->done = 1; }
+  else if (res < s->tol) { s->status = DDA_OK; s->done = 1; }
+  else if (s->half) { s->status = DDA_BREAKDOWN; s->done = 1; }
+  else s->beta_k = s->beta_next;
+}
+
+// ---------------------------------------------------------------- Bi-CG-CS (COCG)
+__global__ void k_bicg_init(Scal* s, const double* part, int nb, double tol) {
+  const c128 bb = cfin(part, 0, nb);
+  const double bn2 = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  s->tol = tol; s->bnorm = sqrt(bn2); s->res = 1.0; s->done = 0; s->half = 0;
+  s->status = DDA_NOT_CONVERGED;
+  s->rho = bb;
+  if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
+  else if (!isfinite(bn2)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
+  else if (cabs2(bb) == 0.0) { s->done = 1; s->status = DDA_BREAKDOWN; }
+}
+
+template <typename R>
+__global__ void k_start3(const cpx<R>* __restrict__ b, cpx<R>* x, cpx<R>* r, cpx<R>* p, long long n) {
+  VLOOP(n) { const cpx<R> bi = b[i]; x[i] = mk<R>(0, 0); r[i] = bi; p[i] = bi; }
+}
+
+__global__ void k_bicg_a(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const c128 mu = cfin(part, 0, nb);
+  if (threadIdx.x) return;
+  if (!cfinite(mu)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  if (cabs2(mu) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  s->alpha = cdivd(s->rho, mu);
+}
+
+// x += alpha p; r -= alpha q; partials r^T r and |r|^2
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_bicg_k1(cpx<R>* __restrict__ x, cpx<R>* __restrict__ r,
+                                                 const cpx<R>* __restrict__ p, const cpx<R>* __restrict__ q,
+                                                 long long n, const Scal* s, double* part) {
+  if (s->done) return;
+  const cpx<R> al = cs<R>(s->alpha);
+  double acc[3] = {0.0, 0.0, 0.0};
+  VLOOP(n) {
+    x[i] = x[i] + al * p[i];
+    const cpx<R> t = r[i] - al * q[i];
+    r[i] = t;
+    const double a = t.x, b = t.y;
+    acc[0] += a * a - b * b;
+    acc[1] += 2.0 * a * b;
+    acc[2] += a * a + b * b;
+  }
+  block_store<3>(acc, part, 0);
+}
+
+__global__ void k_bicg_b(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const c128 rn = cfin(part, 0, nb);
+  const double r2 = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  const double res = sqrt(r2) / s->bnorm;
+  s->res = res;
+  if (!isfinite(res) || !cfinite(rn)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  if (res < s->tol) { s->status = DDA_OK; s->done = 1; return; }
+  if (cabs2(rn) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  s->bstep = cdivd(rn, s->rho);
+  s->rho = rn;
+}
+
+// p = r + bstep p
+template <typename R>
+__global__ void k_bicg_k2(const cpx<R>* __restrict__ r, cpx<R>* __restrict__ p, long long n, const Scal* s) {
+  if (s->done) return;
+  const cpx<R> bs = cs<R>(s->bstep);
+  VLOOP(n) p[i] = r[i] + bs * p[i];
+}
+
+// ---------------------------------------------------------------- Bi-CGSTAB
+__global__ void k_bs_init(Scal* s, const double* part, int nb, double tol) {
+  const double bn2 = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  s->tol = tol; s->bnorm = sqrt(bn2); s->res = 1.0; s->done = 0; s->half = 0;
+  s->status = DDA_NOT_CONVERGED;
+  s->rho = mk<double>(bn2, 0.0);       // rhat^H r0 with rhat = r0 = b
+  s->rho_prev = mk<double>(1.0, 0.0);
+  s->alpha = mk<double>(1.0, 0.0);
+  s->omega = mk<double>(1.0, 0.0);
+  s->bstep = mk<double>(0.0, 0.0);     // p = r on the first step (p = v = 0)
+  if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
+  else if (!isfinite(bn2)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
+}
+
+template <typename R>
+__global__ void k_bs_start(const cpx<R>* __restrict__ b, cpx<R>* x, cpx<R>* r, cpx<R>* rh, cpx<R>* p,
+                           cpx<R>* v, cpx<R>* t, long long n) {
+  VLOOP(n) {
+    const cpx<R> bi = b[i];
+    x[i] = mk<R>(0, 0); r[i] = bi; rh[i] = bi; p[i] = mk<R>(0, 0); v[i] = mk<R>(0, 0);
+    t[i] = mk<R>(0, 0);
+  }
+}
+
+// p = r + bstep (p - omega v)
+template <typename R>
+__global__ void k_bs_p(const cpx<R>* __restrict__ r, cpx<R>* __restrict__ p, const cpx<R>* __restrict__ v,
+                       long long n, const Scal* s) {
+  if (s->done) return;
+  const cpx<R> bs = cs<R>(s->bstep), om = cs<R>(s->omega);
+  VLOOP(n) p[i] = r[i] + bs * (p[i] - om * v[i]);
+}
+
+__global__ void k_bs_a(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const c128 q = cfin(part, 0, nb);
+  if (threadIdx.x) return;
+  if (!cfinite(q)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  if (cabs2(q) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  s->alpha = cdivd(s->rho, q);
+}
+
+// s = r - alpha v ; partial |s|^2
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_bs_s(const cpx<R>* __restrict__ r, const cpx<R>* __restrict__ v,
+                                              cpx<R>* __restrict__ sv, long long n, const Scal* s,
+                                              double* part) {
+  if (s->done) return;
+  const cpx<R> al = cs<R>(s->alpha);
+  double acc[1] = {0.0};
+  VLOOP(n) {
+    const cpx<R> t = r[i] - al * v[i];
+    sv[i] = t;
+    acc[0] += (double)t.x * t.x + (double)t.y * t.y;
+  }
+  block_store<1>(acc, part, 0);
+}
+
+__global__ void k_bs_b(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const double s2 = fin(part, 0, nb);
+  if (threadIdx.x) return;
+  s->sres = sqrt(s2) / s->bnorm;
+  if (!isfinite(s->sres)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  s->half = s->sres < s->tol ? 1 : 0;
+}
+
+// t^H s and t^H t
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_bs_ts(const cpx<R>* __restrict__ t, const cpx<R>* __restrict__ sv,
+                                               long long n, const Scal* s, double* part) {
+  if (s->done) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  VLOOP(n) {
+    const double tx = t[i].x, ty = t[i].y, sx = sv[i].x, sy = sv[i].y;
+    acc[0] += tx * sx + ty * sy;
+    acc[1] += tx * sy - ty * sx;
+    acc[2] += tx * tx + ty * ty;
+  }
+  block_store<3>(acc, part, 0);
+}
+
+__global__ void k_bs_c(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const c128 ts = cfin(part, 0, nb);
+  const double tt = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  if (s->half || tt == 0.0) s->omega = mk<double>(0.0, 0.0);
+  else s->omega = scale<double>(ts, 1.0 / tt);
+}
+
+// x += alpha p + omega s ; r = s - omega t ; partials |r|^2 and rhat^H r
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_bs_xr(cpx<R>* __restrict__ x, cpx<R>* __restrict__ r,
+                                               const cpx<R>* __restrict__ p, const cpx<R>* __restrict__ sv,
+                                               const cpx<R>* __restrict__ t, const cpx<R>* __restrict__ rh,
+                                               long long n, const Scal* s, double* part) {
+  if (s->done) return;
+  const cpx<R> al = cs<R>(s->alpha), om = cs<R>(s->omega);
+  double acc[3] = {0.0, 0.0, 0.0};
+  VLOOP(n) {
+    const cpx<R> si = sv[i];
+    x[i] = x[i] + al * p[i] + om * si;
+    const cpx<R> ri = si - om * t[i];
+    r[i] = ri;
+    const double a = ri.x, b = ri.y, hx = rh[i].x, hy = rh[i].y;
+    acc[0] += a * a + b * b;
+    acc[1] += hx * a + hy * b;
+    acc[2] += hx * b - hy * a;
+  }
+  block_store<3>(acc, part, 0);
+}
+
+__global__ void k_bs_d(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const double r2 = fin(part, 0, nb);
+  const c128 rho = cfin(part, 1, nb);
+  if (threadIdx.x) return;
+  const double res = s->half ? s->sres : sqrt(r2) / s->bnorm;
+  s->res = res;
+  if (!isfinite(res)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  if (res < s->tol) { s->status = DDA_OK; s->done = 1; return; }
+  if (cabs2(rho) == 0.0 || cabs2(s->omega) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  s->rho_prev = s->rho;
+  s->rho = rho;
+  s->bstep = cdivd(rho, s->rho_prev) * cdivd(s->alpha, s->omega);
+}
+
+// ---------------------------------------------------------------- CGNR
+__global__ void k_set_bnorm(Scal* s, const double* part, int nb, double tol) {
+  const double bn2 = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  s->tol = tol; s->bnorm = sqrt(bn2); s->res = 1.0; s->done = 0; s->half = 0;
+  s->status = DDA_NOT_CONVERGED;
+  s->zz = 0.0;
+  if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
+  else if (!isfinite(bn2)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
+}
+
+template <typename R>
+__global__ void k_start2(const cpx<R>* __restrict__ b, cpx<R>* x, cpx<R>* r, long long n) {
+  VLOOP(n) { x[i] = mk<R>(0, 0); r[i] = b[i]; }
+}
+
+// store |.|^2 partial sum (slot 2 of k_norms) into zz (which = 0) or ww (1)
+__global__ void k_cg_take(Scal* s, const double* part, int nb, int which) {
+  if (s->done) return;
+  const double v = fin(part, 2, nb);
+  if (threadIdx.x) return;
+  if (!isfinite(v)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  if (which == 0) {           // zz of the new z: step for p = z + (zz_new/zz) p
+    s->bstep = mk<double>(s->zz > 0.0 ? v / s->zz : 0.0, 0.0);
+    s->zz = v;
+  } else {                    // ww = |A p|^2 : alpha = zz / ww
+    if (v == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+    s->ww = v;
+    s->alpha = mk<double>(s->zz / v, 0.0);
+  }
+}
+
+// x += alpha p; r -= alpha w; partial |r|^2 (slot 0)
+template <typename R>
+__global__ void __launch_bounds__(kVT) k_cg_k1(cpx<R>* __restrict__ x, cpx<R>* __restrict__ r,
+                                               const cpx<R>* __restrict__ p, const cpx<R>* __restrict__ w,
+                                               long long n, const Scal* s, double* part) {
+  if (s->done) return;
+  const cpx<R> al = cs<R>(s->alpha);
+  double acc[1] = {0.0};
+  VLOOP(n) {
+    x[i] = x[i] + al * p[i];
+    const cpx<R> t = r[i] - al * w[i];
+    r[i] = t;
+    acc[0] += (double)t.x * t.x + (double)t.y * t.y;
+  }
+  block_store<1>(acc, part, 0);
+}
+
+__global__ void k_res_check(Scal* s, const double* part, int nb) {
+  if (s->done) return;
+  const double r2 = fin(part, 0, nb);
+  if (threadIdx.x) return;
+  const double res = sqrt(r2) / s->bnorm;
+  s->res = res;
+  if (!isfinite(res)) { s->status = DDA_ERR_NONFINITE; s->done = 1; }
+  else if (res < s->tol) { s->status = DDA_OK; s->done = 1; }
+}
+
+// ---------------------------------------------------------------- refinement (FP64 outer)
+// r32 = (complex64)(r64 * scl)
+__global__ void k_to32s(const c128* __restrict__ a, c64* __restrict__ b, long long n, double scl) {
+  VLOOP(n) b[i] = mk<float>((float)(a[i].x * scl), (float)(a[i].y * scl));
+}
+// x64 += scl * d32
+__global__ void k_axpy64(c128* __restrict__ x, const c64* __restrict__ d, long long n, double scl) {
+  VLOOP(n) x[i] = mk<double>(x[i].x + scl * (double)d[i].x, x[i].y + scl * (double)d[i].y);
+}
+// r = b - w ; partial |r|^2 in slot 2 (as k_norms)
+__global__ void __launch_bounds__(kVT) k_resid(const c128* __restrict__ b, const c128* __restrict__ w,
+                                               c128* __restrict__ r, long long n, double* part) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  VLOOP(n) {
+    const c128 t = b[i] - w[i];
+    r[i] = t;
+    acc[2] += t.x * t.x + t.y * t.y;
+  }
+  block_store<3>(acc, part, 0);
+}
+__global__ void k_take_norm(Scal* s, const double* part, int nb) {
+  const double v = fin(part, 2, nb);
+  if (threadIdx.x == 0) s->sres = sqrt(v);
+}
+
+// ---------------------------------------------------------------- host orchestration
+namespace {
+
+struct Run {
+  dda_t h;
+  cudaStream_t st;
+  long long n;       // 3 * N_occ
+  int nb;            // blocks of vector kernels
+  double* part;
+  Scal* ds;
+  Scal* hs;
+  int rhs;           // RHS index (beta table)
+  int matvecs = 0, matvecs64 = 0, iters = 0;
+  std::vector<double>* hist = nullptr;
+  double hist_scale = 1.0;
+};
+
+int sync_read(Run& R_) {
+  dda_t h = R_.h;
+  DDA_CK(h, cudaMemcpyAsync(R_.hs, R_.ds, sizeof(Scal), cudaMemcpyDeviceToHost, R_.st));
+  DDA_CK(h, cudaStreamSynchronize(R_.st));
+  tr_flush(&h->tracer);
+  return DDA_OK;
+}
+
+template <typename R> Work<R>& work(dda_t h);
+template <> Work<double>& work<double>(dda_t h) { return h->w64; }
+template <> Work<float>& work<float>(dda_t h) { return h->w32; }
+
+template <typename R>
+int matvec(Run& ru, const cpx<R>* x, cpx<R>* y, bool adj) {
+  dda_t h = ru.h;
+  Work<R>& w = work<R>(h);
+  cudaError_t e = launch_matvec<R>(h->g, h->lat(), w, w.beta + (long long)ru.rhs * h->n_mat * 3,
+                                   h->n_mat, x, y, 1, adj, ru.st);
+  if (e != cudaSuccess) return dda_cuda_fail(h, e, "matvec in solver");
+  ru.matvecs++;
+  if (sizeof(R) == 8) ru.matvecs64++;
+  return DDA_OK;
+}
+
+#define RK(call) do { int rc_ = (call); if (rc_ != DDA_OK) return rc_; } while (0)
+#define LK(h) do { cudaError_t e_ = cudaGetLastError(); if (e_ != cudaSuccess) return dda_cuda_fail(h, e_, "solver kernel"); } while (0)
+
+// Run one solver in precision R on b (vector pool vec[0..]); the solution is
+// left in x.  Returns DDA_OK or an error; the solver outcome is in ru.hs->status.
+template <typename R>
+int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, double tol, int maxiter) {
+  dda_t h = ru.h;
+  const long long n = ru.n;
+  const int nb = ru.nb;
+  cudaStream_t st = ru.st;
+  double* part = ru.part;
+  Scal* s = ru.ds;
+  auto rec = [&](void) {
+    if (ru.hist) ru.hist->push_back(ru.hs->res * ru.hist_scale);
+  };
+  k_norms<R><<<nb, kVT, 0, st>>>(b, n, part, nullptr); count_launch();
+  if (solver == DDA_QMR_CS) {
+    cpx<R>*v = vec[0], *vp = vec[1], *w = vec[2], *p1 = vec[3], *p2 = vec[4], *a1 = vec[5],
+          *a2 = vec[6], *r = vec[7];
+    k_qmr_init<<<1, kVT, 0, st>>>(s, part, nb, tol); count_launch();
+    k_qmr_start<R><<<nb, kVT, 0, st>>>(b, v, r, x, vp, p1, p2, a1, a2, n, s); count_launch();
+    LK(h);
+    RK(sync_read(ru));
+    for (int k = 1; k <= maxiter && !ru.hs->done; ++k) {
+      RK(matvec<R>(ru, v, w, false));
+      k_dot<R, false><<<nb, kVT, 0, st>>>(v, w, n, part, 0, s); count_launch();
+      k_qmr_a<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_qmr_k1<R><<<nb, kVT, 0, st>>>(w, v, vp, n, s, part); count_launch();
+      k_qmr_b<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_qmr_k2<R><<<nb, kVT, 0, st>>>(vp, v, w, p1, p2, a1, a2, x, r, n, s, part); count_launch();
+      k_qmr_c<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      LK(h);
+      std::swap(v, vp); std::swap(p1, p2); std::swap(a1, a2);
+      ru.iters++;
+      RK(sync_read(ru));
+      rec();
+    }
+  } else if (solver == DDA_BICG_CS) {
+    cpx<R>*r = vec[0], *p = vec[1], *q = vec[2];
+    k_bicg_init<<<1, kVT, 0, st>>>(s, part, nb, tol); count_launch();
+    k_start3<R><<<nb, kVT, 0, st>>>(b, x, r, p, n); count_launch();
+    LK(h);
+    RK(sync_read(ru));
+    for (int k = 1; k <= maxiter && !ru.hs->done; ++k) {
+      RK(matvec<R>(ru, p, q, false));
+      k_dot<R, false><<<nb, kVT, 0, st>>>(p, q, n, part, 0, s); count_launch();
+      k_bicg_a<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_bicg_k1<R><<<nb, kVT, 0, st>>>(x, r, p, q, n, s, part); count_launch();
+      k_bicg_b<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_bicg_k2<R><<<nb, kVT, 0, st>>>(r, p, n, s); count_launch();
+      LK(h);
+      ru.iters++;
+      RK(sync_read(ru));
+      rec();
+    }
+  } else if (solver == DDA_BICGSTAB) {
+    cpx<R>*r = vec[0], *rh = vec[1], *p = vec[2], *v = vec[3], *sv = vec[4], *t = vec[5];
+    k_bs_init<<<1, kVT, 0, st>>>(s, part, nb, tol); count_launch();
+    k_bs_start<R><<<nb, kVT, 0, st>>>(b, x, r, rh, p, v, t, n); count_launch();
+    LK(h);
+    RK(sync_read(ru));
+    for (int k = 1; k <= maxiter && !ru.hs->done; ++k) {
+      k_bs_p<R><<<nb, kVT, 0, st>>>(r, p, v, n, s); count_launch();
+      RK(matvec<R>(ru, p, v, false));
+      k_dot<R, true><<<nb, kVT, 0, st>>>(rh, v, n, part, 0, s); count_launch();
+      k_bs_a<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_bs_s<R><<<nb, kVT, 0, st>>>(r, v, sv, n, s, part); count_launch();
+      k_bs_b<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      LK(h);
+      RK(sync_read(ru));
+      if (!ru.hs->done && !ru.hs->half) {
+        RK(matvec<R>(ru, sv, t, false));
+        k_bs_ts<R><<<nb, kVT, 0, st>>>(t, sv, n, s, part); count_launch();
+      }
+      k_bs_c<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_bs_xr<R><<<nb, kVT, 0, st>>>(x, r, p, sv, t, rh, n, s, part); count_launch();
+      k_bs_d<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      LK(h);
+      ru.iters++;
+      RK(sync_read(ru));
+      rec();
+    }
+  } else {  // CGNR
+    cpx<R>*r = vec[0], *z = vec[1], *p = vec[2], *w = vec[3];
+    k_set_bnorm<<<1, kVT, 0, st>>>(s, part, nb, tol); count_launch();
+    k_start2<R><<<nb, kVT, 0, st>>>(b, x, r, n); count_launch();
+    LK(h);
+    RK(sync_read(ru));
+    if (!ru.hs->done) {
+      RK(matvec<R>(ru, r, z, true));
+      k_copy<R><<<nb, kVT, 0, st>>>(z, p, n); count_launch();
+      k_norms<R><<<nb, kVT, 0, st>>>(z, n, part, s); count_launch();
+      k_cg_take<<<1, kVT, 0, st>>>(s, part, nb, 0); count_launch();
+      LK(h);
+    }
+    for (int k = 1; k <= maxiter && !ru.hs->done; ++k) {
+      RK(matvec<R>(ru, p, w, false));
+      k_norms<R><<<nb, kVT, 0, st>>>(w, n, part, s); count_launch();
+      k_cg_take<<<1, kVT, 0, st>>>(s, part, nb, 1); count_launch();
+      k_cg_k1<R><<<nb, kVT, 0, st>>>(x, r, p, w, n, s, part); count_launch();
+      k_res_check<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      LK(h);
+      ru.iters++;
+      RK(sync_read(ru));
+      rec();
+      if (ru.hs->done) break;
+      RK(matvec<R>(ru, r, z, true));
+      k_norms<R><<<nb, kVT, 0, st>>>(z, n, part, s); count_launch();
+      k_cg_take<<<1, kVT, 0, st>>>(s, part, nb, 0); count_launch();
+      k_bicg_k2<R><<<nb, kVT, 0, st>>>(z, p, n, s); count_launch();   // p = z + bstep p
+      LK(h);
+    }
+  }
+  return DDA_OK;
+}
+
+int ensure_solver_mem(dda_t h, size_t bytes) {
+  if (!h->d_part) {
+    if (cudaMalloc(&h->d_part, kSlots * kNB * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver partials"); }
+    if (cudaMalloc(&h->d_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver scalars"); }
+    if (cudaMallocHost(&h->h_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "pinned scalars"); }
+  }
+  if (h->sv_bytes < bytes) {
+    cudaFree(h->sv);
+    h->sv = nullptr;
+    h->sv_bytes = 0;
+    if (cudaMalloc(&h->sv, bytes) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver vectors"); }
+    h->sv_bytes = bytes;
+  }
+  return DDA_OK;
+}
+
+int status_rank(int s) {          // larger = worse
+  if (s < 0) return 100 - s;
+  return s;                        // OK 0 < NOT_CONVERGED 1 < BREAKDOWN 2
+}
+
+}  // namespace
+}  // namespace dda
+
+using namespace dda;
+
+int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
+                       const double* pol, void* P_dev, double* hist, int hist_len,
+                       dda_solve_info* info) {
+  int rc = dda_beta_internal(h, o->pol, nrhs, prop, pol);
+  if (rc != DDA_OK) return rc;
+  const long long n = 3 * h->g.n_occ;
+  const bool refined = o->prec == DDA_FP32_REFINED;
+  const int nvec = 10;
+  const size_t bytes = refined ? (size_t)n * (nvec * sizeof(c64) + 5 * sizeof(c128))
+                               : (size_t)n * (nvec + 1) * sizeof(c128);
+  rc = ensure_solver_mem(h, bytes);
+  if (rc != DDA_OK) return rc;
+  Run ru;
+  ru.h = h; ru.st = h->stream; ru.n = n;
+  long long nb = (n + 4LL * kVT - 1) / (4LL * kVT);
+  ru.nb = (int)(nb < 1 ? 1 : (nb > kNB ? kNB : nb));
+  ru.part = h->d_part;
+  ru.ds = (Scal*)h->d_scal;
+  ru.hs = (Scal*)h->h_scal;
+  const int rows_grid = (int)std::min<long long>((h->g.nrows + 7) / 8, 152LL * 32);
+  int worst = DDA_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    auto t0 = std::chrono::steady_clock::now();
+    ru.rhs = r; ru.matvecs = 0; ru.matvecs64 = 0; ru.iters = 0;
+    std::vector<double> hv;
+    hv.push_back(1.0);
+    ru.hist = &hv;
+    ru.hist_scale = 1.0;
+    Wave wv;
+    for (int q = 0; q < 3; ++q) wv.a[q] = prop[3 * r + q];
+    for (int q = 0; q < 6; ++q) wv.e[q] = pol[6 * r + q];
+    const c128* beta64 = h->w64.beta + (long long)r * h->n_mat * 3;
+    dda_solve_info& inf = info[r];
+    inf = dda_solve_info{};
+    int st_rhs = DDA_NOT_CONVERGED;
+    double res_true = NAN, res_recur = NAN;
+    int outer = 0;
+    if (!refined) {
+      c128* base = (c128*)h->sv;
+      c128* vec[nvec];
+      for (int i = 0; i < nvec; ++i) vec[i] = base + (size_t)i * n;
+      c128* b = base + (size_t)nvec * n;   // b lives after the pool
+      c128* x = vec[9];
+      k_rhs<double><<<rows_grid, 256, 0, ru.st>>>(b, h->lat(), beta64, h->g.n_occ, h->g.nx, h->g.ny,
+                                                 h->g.nz, h->g.nrows, h->kd, wv); count_launch();
+      LK(h);
+      RK(run_solver<double>(ru, o->solver, b, x, vec, o->tol, o->maxiter));
+      st_rhs = ru.hs->status;
+      res_recur = ru.hs->res;
+      const double bn = ru.hs->bnorm;
+      // true residual in FP64 (stop test at exit)
+      c128* w = vec[0];
+      c128* rr = vec[1];
+      RK(matvec<double>(ru, x, w, false));
+      k_resid<<<ru.nb, kVT, 0, ru.st>>>(b, w, rr, n, ru.part); count_launch();
+      k_take_norm<<<1, kVT, 0, ru.st>>>(ru.ds, ru.part, ru.nb); count_launch();
+      LK(h);
+      RK(sync_read(ru));
+      res_true = bn > 0 ? ru.hs->sres / bn : 0.0;
+      if (st_rhs == DDA_OK && !(res_true < o->tol)) st_rhs = DDA_NOT_CONVERGED;
+      k_pfinal<double><<<ru.nb, kVT, 0, ru.st>>>(x, (c128*)P_dev + (size_t)r * n, h->d_mat, beta64, h->g.n_occ); count_launch();
+      LK(h);
+    } else {
+      c64* base = (c64*)h->sv;
+      c64* vec[nvec];
+      for (int i = 0; i < nvec; ++i) vec[i] = base + (size_t)i * n;
+      c64* x32 = vec[9];
+      c64* b32 = vec[8];
+      c128* b64 = (c128*)(base + (size_t)nvec * n);
+      c128* x64 = b64 + n;
+      c128* r64 = x64 + n;
+      c128* w64 = r64 + n;
+      k_rhs<double><<<rows_grid, 256, 0, ru.st>>>(b64, h->lat(), beta64, h->g.n_occ, h->g.nx, h->g.ny,
+                                                 h->g.nz, h->g.nrows, h->kd, wv); count_launch();
+      k_norms<double><<<ru.nb, kVT, 0, ru.st>>>(b64, n, ru.part, nullptr); count_launch();
+      k_take_norm<<<1, kVT, 0, ru.st>>>(ru.ds, ru.part, ru.nb); count_launch();
+      k_copy<double><<<ru.nb, kVT, 0, ru.st>>>(b64, r64, n); count_launch();
+      k_zero<double><<<ru.nb, kVT, 0, ru.st>>>(x64, n); count_launch();
+      LK(h);
+      RK(sync_read(ru));
+      const double bn = ru.hs->sres;
+      double rn = bn;
+      int left = o->maxiter;
+      st_rhs = bn > 0 ? DDA_NOT_CONVERGED : DDA_OK;
+      res_true = bn > 0 ? 1.0 : 0.0;
+      while (bn > 0 && left > 0 && outer < 64) {
+        if (rn / bn < o->tol) { st_rhs = DDA_OK; break; }
+        const double target = std::max(o->inner_tol, 0.5 * o->tol * bn / rn);
+        k_to32s<<<ru.nb, kVT, 0, ru.st>>>(r64, b32, n, 1.0 / rn); count_launch();
+        LK(h);
+        ru.hist_scale = rn / bn;
+        const int it0 = ru.iters;
+        RK(run_solver<float>(ru, o->solver, b32, x32, vec, target, left));
+        const int inner_status = ru.hs->status;
+        left -= ru.iters - it0;
+        outer++;
+        k_axpy64<<<ru.nb, kVT, 0, ru.st>>>(x64, x32, n, rn); count_launch();
+        RK(matvec<double>(ru, x64, w64, false));
+        k_resid<<<ru.nb, kVT, 0, ru.st>>>(b64, w64, r64, n, ru.part); count_launch();
+        k_take_norm<<<1, kVT, 0, ru.st>>>(ru.ds, ru.part, ru.nb); count_launch();
+        LK(h);
+        RK(sync_read(ru));
+        const double rn_new = ru.hs->sres;
+        res_true = rn_new / bn;
+        if (!std::isfinite(rn_new)) { st_rhs = DDA_ERR_NONFINITE; break; }
+        if (res_true < o->tol) { st_rhs = DDA_OK; break; }
+        if (inner_status == DDA_BREAKDOWN || inner_status == DDA_ERR_NONFINITE) { st_rhs = inner_status; break; }
+        if (!(rn_new < 0.999 * rn)) { st_rhs = DDA_NOT_CONVERGED; break; }   // refinement stalled
+        rn = rn_new;
+      }
+      res_recur = res_true;
+      k_pfinal<double><<<ru.nb, kVT, 0, ru.st>>>(x64, (c128*)P_dev + (size_t)r * n, h->d_mat, beta64, h->g.n_occ); count_launch();
+      LK(h);
+    }
+    DDA_CK(h, cudaStreamSynchronize(ru.st));
+    auto t1 = std::chrono::steady_clock::now();
+    inf.status = st_rhs;
+    inf.iters = ru.iters;
+    inf.matvecs = ru.matvecs;
+    inf.matvecs_fp64 = ru.matvecs64;
+    inf.outer = outer;
+    inf.rel_res_true = res_true;
+    inf.rel_res_recur = res_recur;
+    inf.seconds = std::chrono::duration<double>(t1 - t0).count();
+    if (hist) {
+      double* hr = hist + (size_t)r * hist_len;
+      for (int i = 0; i < hist_len; ++i) hr[i] = i < (int)hv.size() ? hv[i] : -1.0;
+    }
+    if (status_rank(st_rhs) > status_rank(worst)) worst = st_rhs;
+  }
+  return worst;
+}

@@ -1,0 +1,395 @@
+// The FFT interaction-matrix product y = A x of Eq. (2)-(3):
+//     y_i = x_i - beta_i sum_j G(r_i - r_j) beta_j x_j ,
+// done as a zero-padded circular convolution on an Mx*My*Mz grid
+// (M >= 2n - 1), split into 1D transforms with pruning (arXiv:0704.0037,
+// Sec. 2: the forward input is mostly zeros and only part of the backward
+// output is used; only the real dipoles carry vector data).
+//
+// Five passes, per right-hand side:
+//   P1  x-FFT of the n_y*n_z occupied rows, fused with the gather of x from
+//       the compact dipole order and the multiply by beta   -> B1[3][nz][ny][Mx]
+//   P2  y-FFT of n_y nonzero inputs, all My outputs          -> B2[3][nz][My][Mx]
+//   P3  per (kx, ky): z-FFT of n_z nonzero inputs, 3x3 product with the octant
+//       of FFT(G) (parity signs restore the other octants), inverse z-FFT,
+//       keep z < n_z; in place in B2
+//   P4  inverse y-FFT, keep y < n_y                          -> B1
+//   P5  inverse x-FFT, keep the occupied x, y = x - beta u   -> compact y
+#include "internal.h"
+
+namespace dda {
+
+static __device__ __forceinline__ int ldm_for(int logT, bool contig) {
+  return (1 << logT) + (contig ? 1 : 0);
+}
+
+template <typename R>
+__device__ __forceinline__ void load_tw(cpx<R>* s_tw, const cpx<R>* __restrict__ tw, int M) {
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s_tw[i] = tw[i];
+}
+
+// ---------------------------------------------------------------- P1
+template <typename R, bool CONJ>
+__global__ void __launch_bounds__(256) k_p1(const cpx<R>* __restrict__ x, cpx<R>* __restrict__ B1,
+                                            LatticeDev lat, const cpx<R>* __restrict__ beta,
+                                            long long n_occ, int nrows, FftPlan p,
+                                            const cpx<R>* __restrict__ tw, int logT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = p.M;
+  const int T = 1 << logT;
+  const int ldm = ldm_for(logT, true);
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* b0 = s_tw + M;
+  cpx<R>* b1 = b0 + (size_t)M * ldm;
+  const int c = blockIdx.y;
+  const int r0 = blockIdx.x * T;
+  load_tw(s_tw, tw, M);
+  for (int i = threadIdx.x; i < M * ldm; i += blockDim.x) b0[i] = mk<R>(0, 0);
+  __syncthreads();
+  const cpx<R>* xc = x + (long long)c * n_occ;
+  for (int t = 0; t < T; ++t) {
+    const int row = r0 + t;
+    if (row >= nrows) break;
+    const long long s = lat.row_off[row], e = lat.row_off[row + 1];
+    for (long long i = s + threadIdx.x; i < e; i += blockDim.x) {
+      cpx<R> v = xc[i];
+      if (CONJ) v = conjg(v);
+      b0[(int)lat.xi[i] * ldm + t] = beta[lat.mat[i] * 3 + c] * v;
+    }
+  }
+  __syncthreads();
+  cpx<R>* res = stockham<R, false>(b0, b1, ldm, logT, p, s_tw);
+  cpx<R>* out = B1 + (long long)c * nrows * M;
+  for (int it = threadIdx.x; it < M * T; it += blockDim.x) {
+    const int t = it / M, m = it - t * M;
+    const int row = r0 + t;
+    if (row < nrows) out[(long long)row * M + m] = res[m * ldm + t];
+  }
+}
+
+// ---------------------------------------------------------------- P5
+template <typename R, bool CONJ>
+__global__ void __launch_bounds__(256) k_p5(const cpx<R>* __restrict__ B1, const cpx<R>* __restrict__ x,
+                                            cpx<R>* __restrict__ y, LatticeDev lat,
+                                            const cpx<R>* __restrict__ beta, long long n_occ,
+                                            int nrows, FftPlan p, const cpx<R>* __restrict__ tw,
+                                            int logT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = p.M;
+  const int T = 1 << logT;
+  const int ldm = ldm_for(logT, true);
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* b0 = s_tw + M;
+  cpx<R>* b1 = b0 + (size_t)M * ldm;
+  const int c = blockIdx.y;
+  const int r0 = blockIdx.x * T;
+  load_tw(s_tw, tw, M);
+  const cpx<R>* in = B1 + (long long)c * nrows * M;
+  for (int it = threadIdx.x; it < M * T; it += blockDim.x) {
+    const int t = it / M, m = it - t * M;
+    const int row = r0 + t;
+    b0[m * ldm + t] = row < nrows ? in[(long long)row * M + m] : mk<R>(0, 0);
+  }
+  __syncthreads();
+  cpx<R>* res = stockham<R, true>(b0, b1, ldm, logT, p, s_tw);
+  const cpx<R>* xc = x + (long long)c * n_occ;
+  cpx<R>* yc = y + (long long)c * n_occ;
+  for (int t = 0; t < T; ++t) {
+    const int row = r0 + t;
+    if (row >= nrows) break;
+    const long long s = lat.row_off[row], e = lat.row_off[row + 1];
+    for (long long i = s + threadIdx.x; i < e; i += blockDim.x) {
+      cpx<R> v = xc[i];
+      if (CONJ) v = conjg(v);
+      cpx<R> o = v - beta[lat.mat[i] * 3 + c] * res[(int)lat.xi[i] * ldm + t];
+      if (CONJ) o = conjg(o);
+      yc[i] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- P2 / P4 and generic lines
+struct LineGeom {
+  int n_in, n_out, nt;
+  int contig;
+  long long in_sm, in_st, in_so, in_sb;
+  long long out_sm, out_st, out_so, out_sb;
+};
+
+// in may equal out (in-place passes of the D-matrix build): every block reads
+// all its lines before the barrier and writes the same lines after it.
+template <typename R, bool INV>
+__global__ void __launch_bounds__(256) k_lines(const cpx<R>* in, cpx<R>* out,
+                                               LineGeom lg, FftPlan p, const cpx<R>* __restrict__ tw,
+                                               int logT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = p.M;
+  const int T = 1 << logT;
+  const int Tm = T - 1;
+  const int ldm = ldm_for(logT, lg.contig != 0);
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* b0 = s_tw + M;
+  cpx<R>* b1 = b0 + (size_t)M * ldm;
+  const int t0 = blockIdx.x * T;
+  const long long ib = blockIdx.z * lg.in_sb + blockIdx.y * lg.in_so;
+  const long long ob = blockIdx.z * lg.out_sb + blockIdx.y * lg.out_so;
+  load_tw(s_tw, tw, M);
+  const int nload = lg.n_in * T;
+  for (int it = threadIdx.x; it < nload; it += blockDim.x) {
+    int t, m;
+    if (lg.contig) { t = it / lg.n_in; m = it - t * lg.n_in; }
+    else { t = it & Tm; m = it >> logT; }
+    const int tt = t0 + t;
+    b0[m * ldm + t] = tt < lg.nt ? in[ib + (long long)tt * lg.in_st + (long long)m * lg.in_sm]
+                                 : mk<R>(0, 0);
+  }
+  for (int it = nload + threadIdx.x; it < M * T; it += blockDim.x) {
+    const int t = it & Tm, m = it >> logT;
+    b0[m * ldm + t] = mk<R>(0, 0);
+  }
+  __syncthreads();
+  cpx<R>* res = stockham<R, INV>(b0, b1, ldm, logT, p, s_tw);
+  const int nst = lg.n_out * T;
+  for (int it = threadIdx.x; it < nst; it += blockDim.x) {
+    int t, m;
+    if (lg.contig) { t = it / lg.n_out; m = it - t * lg.n_out; }
+    else { t = it & Tm; m = it >> logT; }
+    const int tt = t0 + t;
+    if (tt < lg.nt) out[ob + (long long)tt * lg.out_st + (long long)m * lg.out_sm] = res[m * ldm + t];
+  }
+}
+
+// ---------------------------------------------------------------- P3
+// D octant index and parity sign for frequency k on an axis of length M.
+static __device__ __forceinline__ int fold(int k, int M, int& neg) {
+  if (2 * k > M) { neg = 1; return M - k; }
+  neg = 0;
+  return k;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_p3(cpx<R>* __restrict__ B2, const cpx<R>* __restrict__ D,
+                                            int nz, int Mx, int My, FftPlan p,
+                                            const cpx<R>* __restrict__ tw, int logT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Mz = p.M;
+  const int T = 1 << logT;
+  const int Tm = T - 1;
+  const int ldm = T;
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* buf[4];
+  buf[0] = s_tw + Mz;
+  for (int i = 1; i < 4; ++i) buf[i] = buf[i - 1] + (size_t)Mz * ldm;
+  const int kx0 = blockIdx.x * T;
+  const int ky = blockIdx.y;
+  const long long plane = (long long)My * Mx;
+  const long long comp = (long long)nz * plane;
+  load_tw(s_tw, tw, Mz);
+  // load the three components (z < nz), zero the padding
+  for (int c = 0; c < 3; ++c) {
+    cpx<R>* b = buf[c];
+    for (int it = threadIdx.x; it < Mz * T; it += blockDim.x) {
+      const int t = it & Tm, z = it >> logT;
+      const int kx = kx0 + t;
+      b[z * ldm + t] = (z < nz && kx < Mx) ? B2[c * comp + z * plane + (long long)ky * Mx + kx]
+                                           : mk<R>(0, 0);
+    }
+  }
+  __syncthreads();
+  cpx<R>* cp[3] = {buf[0], buf[1], buf[2]};
+  cpx<R>* fr = buf[3];
+  for (int c = 0; c < 3; ++c) {
+    cpx<R>* res = stockham<R, false>(cp[c], fr, ldm, logT, p, s_tw);
+    if (res == fr) { fr = cp[c]; cp[c] = res; }
+  }
+  // 3x3 symmetric multiply in Fourier space
+  const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = Mz / 2 + 1;
+  const long long octs = (long long)hx * hy * hz;
+  int ny_;
+  const int fy = fold(ky, My, ny_);
+  for (int it = threadIdx.x; it < Mz * T; it += blockDim.x) {
+    const int t = it & Tm, kz = it >> logT;
+    const int kx = kx0 + t;
+    if (kx >= Mx) continue;
+    int nx_, nz_;
+    const int fx = fold(kx, Mx, nx_);
+    const int fz = fold(kz, Mz, nz_);
+    const long long o = ((long long)fz * hy + fy) * hx + fx;
+    cpx<R> dxx = D[o], dxy = D[octs + o], dxz = D[2 * octs + o];
+    cpx<R> dyy = D[3 * octs + o], dyz = D[4 * octs + o], dzz = D[5 * octs + o];
+    if (nx_ ^ ny_) dxy = mk<R>(-dxy.x, -dxy.y);
+    if (nx_ ^ nz_) dxz = mk<R>(-dxz.x, -dxz.y);
+    if (ny_ ^ nz_) dyz = mk<R>(-dyz.x, -dyz.y);
+    const int e = kz * ldm + t;
+    const cpx<R> vx = cp[0][e], vy = cp[1][e], vz = cp[2][e];
+    cp[0][e] = dxx * vx + dxy * vy + dxz * vz;
+    cp[1][e] = dxy * vx + dyy * vy + dyz * vz;
+    cp[2][e] = dxz * vx + dyz * vy + dzz * vz;
+  }
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) {
+    cpx<R>* res = stockham<R, true>(cp[c], fr, ldm, logT, p, s_tw);
+    if (res == fr) { fr = cp[c]; cp[c] = res; }
+  }
+  for (int c = 0; c < 3; ++c) {
+    const cpx<R>* b = cp[c];
+    for (int it = threadIdx.x; it < nz * T; it += blockDim.x) {
+      const int t = it & Tm, z = it >> logT;
+      const int kx = kx0 + t;
+      if (kx < Mx) B2[c * comp + z * plane + (long long)ky * Mx + kx] = b[z * ldm + t];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+static int pick_logT(int M, size_t elem, int nbuf, int extra_col, int logTmax) {
+  const size_t budget = 100 * 1024;
+  int lt = logTmax;
+  while (lt > 0) {
+    size_t need = ((size_t)nbuf * M * ((1 << lt) + extra_col) + M) * elem;
+    if (need <= budget) break;
+    --lt;
+  }
+  return lt;
+}
+
+static size_t smem_bytes(int M, size_t elem, int nbuf, int logT, int extra_col) {
+  return ((size_t)nbuf * M * ((1 << logT) + extra_col) + M) * elem;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const FftPlan& p,
+                         const cpx<R>* tw, bool inverse, int n_in, int n_out, int nt, int n_outer,
+                         int n_batch, bool contig, long long in_sm, long long in_st,
+                         long long in_so, long long in_sb, long long out_sm, long long out_st,
+                         long long out_so, long long out_sb, cudaStream_t st) {
+  (void)g;
+  const int logTmax = sizeof(R) == 4 ? 4 : 3;
+  const int lt = pick_logT(p.M, sizeof(cpx<R>), 2, contig ? 1 : 0, logTmax);
+  const size_t sm = smem_bytes(p.M, sizeof(cpx<R>), 2, lt, contig ? 1 : 0);
+  LineGeom lg{n_in, n_out, nt, contig ? 1 : 0, in_sm, in_st, in_so, in_sb,
+              out_sm, out_st, out_so, out_sb};
+  dim3 grid((nt + (1 << lt) - 1) >> lt, n_outer, n_batch);
+  cudaError_t e;
+  if (inverse) {
+    e = allow_smem(k_lines<R, true>, sm);
+    if (e != cudaSuccess) return e;
+    k_lines<R, true><<<grid, 256, sm, st>>>(in, out, lg, p, tw, lt); count_launch();
+  } else {
+    e = allow_smem(k_lines<R, false>, sm);
+    if (e != cudaSuccess) return e;
+    k_lines<R, false><<<grid, 256, sm, st>>>(in, out, lg, p, tw, lt); count_launch();
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, const cpx<R>* beta,
+                          int n_mat, const cpx<R>* x, cpx<R>* y, int nrhs, bool adjoint,
+                          cudaStream_t st) {
+  const int logTmax = sizeof(R) == 4 ? 4 : 3;
+  const size_t el = sizeof(cpx<R>);
+  const cpx<R>* twx = w.tw;
+  const cpx<R>* twy = w.tw + g.Mx;
+  const cpx<R>* twz = w.tw + g.Mx + g.My;
+  const int lt1 = pick_logT(g.Mx, el, 2, 1, logTmax);
+  const size_t sm1 = smem_bytes(g.Mx, el, 2, lt1, 1);
+  const int lt3 = pick_logT(g.Mz, el, 4, 0, logTmax - 1);
+  const size_t sm3 = smem_bytes(g.Mz, el, 4, lt3, 0);
+  cudaError_t e;
+  if ((e = allow_smem(k_p1<R, false>, sm1)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_p1<R, true>, sm1)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_p5<R, false>, sm1)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_p5<R, true>, sm1)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_p3<R>, sm3)) != cudaSuccess) return e;
+  const long long nv = 3LL * g.n_occ;
+  for (int r = 0; r < nrhs; ++r) {
+    const cpx<R>* xr = x + r * nv;
+    cpx<R>* yr = y + r * nv;
+    const cpx<R>* br = beta + (long long)r * n_mat * 3;
+    dim3 g1((g.nrows + (1 << lt1) - 1) >> lt1, 3);
+    const int tb = sizeof(R) == 4 ? TR_P1_C64 : TR_P1_C128;
+    tr_begin(g.tr, st);
+    if (adjoint) {
+      k_p1<R, true><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+    } else {
+      k_p1<R, false><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+    }
+    tr_end(g.tr, st, tb);
+    tr_begin(g.tr, st);
+    // P2: y lines of B1 [3][nz][ny][Mx] -> B2 [3][nz][My][Mx]
+    e = launch_lines<R>(g, w.B1, w.B2, g.py, twy, false, g.ny, g.My, g.Mx, g.nz, 3, false,
+                        g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx,
+                        g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx, st);
+    if (e != cudaSuccess) return e;
+    tr_end(g.tr, st, tb + 1);
+    dim3 g3((g.Mx + (1 << lt3) - 1) >> lt3, g.My);
+    tr_begin(g.tr, st);
+    k_p3<R><<<g3, 256, sm3, st>>>(w.B2, w.D, g.nz, g.Mx, g.My, g.pz, twz, lt3); count_launch();
+    tr_end(g.tr, st, tb + 2);
+    tr_begin(g.tr, st);
+    // P4: inverse y, keep y < ny
+    e = launch_lines<R>(g, w.B2, w.B1, g.py, twy, true, g.My, g.ny, g.Mx, g.nz, 3, false,
+                        g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx,
+                        g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx, st);
+    if (e != cudaSuccess) return e;
+    tr_end(g.tr, st, tb + 3);
+    tr_begin(g.tr, st);
+    if (adjoint) {
+      k_p5<R, true><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+    } else {
+      k_p5<R, false><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+    }
+    tr_end(g.tr, st, tb + 4);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_matvec<float>(const Geom&, const LatticeDev&, Work<float>&,
+                                          const c64*, int, const c64*, c64*, int, bool,
+                                          cudaStream_t);
+template cudaError_t launch_matvec<double>(const Geom&, const LatticeDev&, Work<double>&,
+                                           const c128*, int, const c128*, c128*, int, bool,
+                                           cudaStream_t);
+template cudaError_t launch_lines<double>(const Geom&, const c128*, c128*, const FftPlan&,
+                                          const c128*, bool, int, int, int, int, int, bool,
+                                          long long, long long, long long, long long, long long,
+                                          long long, long long, long long, cudaStream_t);
+template cudaError_t launch_lines<float>(const Geom&, const c64*, c64*, const FftPlan&,
+                                         const c64*, bool, int, int, int, int, int, bool,
+                                         long long, long long, long long, long long, long long,
+                                         long long, long long, long long, cudaStream_t);
+
+// Factor M into radices 8, 4, 2, 3, 5, 7 (in that order of preference).
+FftPlan make_plan(int M) {
+  FftPlan p{};
+  p.M = M;
+  p.nst = 0;
+  int r = M;
+  const int order[] = {8, 4, 2, 3, 5, 7};
+  for (int q : order) {
+    while (r % q == 0 && p.nst < kMaxStages) {
+      p.radix[p.nst++] = q;
+      r /= q;
+    }
+  }
+  if (r != 1) p.nst = -1;  // not 7-smooth
+  return p;
+}
+
+int smooth_size(int lo) {
+  int m = lo < 1 ? 1 : lo;
+  for (;; ++m) {
+    int r = m;
+    for (int q : {2, 3, 5, 7})
+      while (r % q == 0) r /= q;
+    if (r == 1) return m;
+  }
+}
+
+}  // namespace dda

@@ -1,0 +1,314 @@
+"""Thin ctypes binding of the C-ABI in include/dda.h (argument marshalling only).
+
+Every function here has the name and meaning of the C entry point it wraps;
+all arithmetic runs in libdda.so (hand-written sm_103a CUDA).  Device buffers
+are torch CUDA tensors (complex128 or complex64, contiguous, [nrhs][3][N_occ]);
+host arrays are numpy arrays.  Negative statuses raise DDAError carrying
+dda_last_error(); the non-fatal solver outcomes (DDA_NOT_CONVERGED,
+DDA_BREAKDOWN) are returned.
+
+There is no CPU fallback: if libdda.so is missing or cannot be loaded this
+module raises on first use.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdda.so")
+
+DDA_OK, DDA_NOT_CONVERGED, DDA_BREAKDOWN = 0, 1, 2
+DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM, DDA_ERR_STATE, DDA_ERR_NONFINITE, DDA_ERR_TIMEOUT = \
+    -1, -2, -3, -4, -5, -6
+DDA_CM, DDA_RR, DDA_LDR, DDA_CLDR = 0, 1, 2, 3
+DDA_QMR_CS, DDA_BICG_CS, DDA_BICGSTAB, DDA_CGNR = 0, 1, 2, 3
+DDA_FP64, DDA_FP32_REFINED = 0, 1
+
+STATUS_NAMES = {0: "ok", 1: "not_converged", 2: "breakdown", -1: "err_arg", -2: "err_cuda",
+                -3: "err_oom", -4: "err_state", -5: "err_nonfinite", -6: "err_timeout"}
+POL = {"cm": DDA_CM, "rr": DDA_RR, "ldr": DDA_LDR, "cldr": DDA_CLDR}
+SOLVER = {"qmr_cs": DDA_QMR_CS, "bicg_cs": DDA_BICG_CS, "bicgstab": DDA_BICGSTAB, "cgnr": DDA_CGNR}
+PREC = {"fp64": DDA_FP64, "fp32_refined": DDA_FP32_REFINED}
+
+# every entry point declared in include/dda.h
+EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec",
+           "dda_matvec_adjoint", "dda_solve", "dda_scatter", "dda_mueller_plane", "dda_trace",
+           "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
+           "dda_free")
+
+
+class DDAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("pol", ctypes.c_int), ("prec", ctypes.c_int),
+                ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("checkpoint_every", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("matvecs_fp64", ctypes.c_int), ("outer", ctypes.c_int),
+                ("rel_res_true", ctypes.c_double), ("rel_res_recur", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.c_int
+
+
+def lib():
+    """Load libdda.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "paper_0704_0037_gb300.build.build() (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "dda_init_lattice": ([ctypes.POINTER(_vp), _ip, _ip, _ip, ctypes.POINTER(ctypes.c_uint8), _ip,
+                              _dp, ctypes.c_double, _ip, _vp], _ip),
+        "dda_build_Dmatrix": ([_vp, _ip], _ip),
+        "dda_set_beta": ([_vp, _ip, _ip, _dp, _dp], _ip),
+        "dda_matvec": ([_vp, _ip, _vp, _vp, _ip], _ip),
+        "dda_matvec_adjoint": ([_vp, _ip, _vp, _vp, _ip], _ip),
+        "dda_solve": ([_vp, ctypes.POINTER(SolveOpts), _ip, _dp, _dp, _vp, _dp, _ip,
+                       ctypes.POINTER(SolveInfo)], _ip),
+        "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
+        "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
+        "dda_trace": ([_vp, _ip], _ip),
+        "dda_trace_read": ([_vp, _ip, ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_longlong),
+                            ctypes.POINTER(ctypes.c_int)], _ip),
+        "dda_n_occ": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
+        "dda_kd": ([_vp, _dp], _ip),
+        "dda_grid": ([_vp, ctypes.POINTER(ctypes.c_int)], _ip),
+        "dda_positions": ([_vp, ctypes.POINTER(ctypes.c_int)], _ip),
+        "dda_last_error": ([_vp], ctypes.c_char_p),
+        "dda_free": ([_vp], _ip),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _check(h, rc):
+    if rc < 0:
+        msg = lib().dda_last_error(h).decode() if h else ""
+        raise DDAError(rc, msg)
+    return rc
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    return _vp(int(stream))
+
+
+def _dev_ptr(t, dtype=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return _vp(t.data_ptr())
+
+
+def _vecs(prop, pol, nrhs):
+    a = np.ascontiguousarray(np.asarray(prop, dtype=np.float64).reshape(nrhs, 3))
+    e = np.asarray(pol, dtype=np.complex128).reshape(nrhs, 3)
+    e2 = np.ascontiguousarray(np.stack([e.real, e.imag], axis=-1).reshape(nrhs, 6))
+    return a, e2
+
+
+# ---------------------------------------------------------------- entry points
+
+def dda_init_lattice(occ, m_list, kd, volume_corrected=False, stream=None):
+    """occ: uint8 (nz, ny, nx) material indices; m_list: refractive indices.
+    Returns the handle (ctypes void pointer)."""
+    occ = np.ascontiguousarray(occ, dtype=np.uint8)
+    nz, ny, nx = occ.shape
+    m = np.asarray(m_list, dtype=np.complex128).reshape(-1)
+    m2 = np.ascontiguousarray(np.stack([m.real, m.imag], axis=-1).reshape(-1))
+    h = _vp()
+    rc = lib().dda_init_lattice(ctypes.byref(h), nx, ny, nz,
+                                occ.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), m.size,
+                                _dptr(m2), float(kd), int(bool(volume_corrected)),
+                                _stream_ptr(stream))
+    if rc < 0:
+        raise DDAError(rc, "dda_init_lattice failed")
+    return h
+
+
+def dda_build_Dmatrix(h, prec=DDA_FP64):
+    return _check(h, lib().dda_build_Dmatrix(h, int(prec)))
+
+
+def dda_set_beta(h, pol_prescription, prop, pol):
+    nrhs = int(np.asarray(prop).size // 3)
+    a, e = _vecs(prop, pol, nrhs)
+    return _check(h, lib().dda_set_beta(h, int(pol_prescription), nrhs, _dptr(a), _dptr(e)))
+
+
+def dda_matvec(h, prec, x, y, nrhs=1):
+    import torch
+    dt = torch.complex128 if prec == DDA_FP64 else torch.complex64
+    return _check(h, lib().dda_matvec(h, int(prec), _dev_ptr(x, dt), _dev_ptr(y, dt), int(nrhs)))
+
+
+def dda_matvec_adjoint(h, prec, x, y, nrhs=1):
+    import torch
+    dt = torch.complex128 if prec == DDA_FP64 else torch.complex64
+    return _check(h, lib().dda_matvec_adjoint(h, int(prec), _dev_ptr(x, dt), _dev_ptr(y, dt),
+                                              int(nrhs)))
+
+
+def dda_solve(h, opts, prop, pol, P, hist_len=0):
+    """opts: SolveOpts or dict.  Returns (status, [info dicts], hist or None)."""
+    import torch
+    if isinstance(opts, dict):
+        o = SolveOpts(solver=opts.get("solver", DDA_QMR_CS), pol=opts.get("pol", DDA_LDR),
+                      prec=opts.get("prec", DDA_FP64), tol=opts.get("tol", 1e-5),
+                      maxiter=opts.get("maxiter", 10000), inner_tol=opts.get("inner_tol", 1e-3),
+                      checkpoint_every=0)
+    else:
+        o = opts
+    nrhs = int(np.asarray(prop).size // 3)
+    a, e = _vecs(prop, pol, nrhs)
+    info = (SolveInfo * nrhs)()
+    hist = np.full((nrhs, hist_len), -1.0) if hist_len > 0 else None
+    rc = lib().dda_solve(h, ctypes.byref(o), nrhs, _dptr(a), _dptr(e),
+                         _dev_ptr(P, torch.complex128), _dptr(hist), int(hist_len), info)
+    _check(h, rc)
+    return rc, [i.as_dict() for i in info], hist
+
+
+def dda_scatter(h, pol_prescription, P, prop, pol, dirs=None, weights=None):
+    """Returns (F (nrhs, n_dir, 3) complex, q (nrhs, 3) = Q_ext, Q_abs, Q_sca)."""
+    import torch
+    nrhs = int(np.asarray(prop).size // 3)
+    a, e = _vecs(prop, pol, nrhs)
+    d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3)) if dirs is not None \
+        else np.zeros((0, 3))
+    n_dir = d.shape[0]
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64)) if weights is not None else None
+    F = np.zeros((nrhs, max(n_dir, 1), 6))
+    q = np.zeros((nrhs, 3))
+    rc = lib().dda_scatter(h, int(pol_prescription), _dev_ptr(P, torch.complex128), nrhs, _dptr(a),
+                           _dptr(e), n_dir, _dptr(d) if n_dir else None, _dptr(w), _dptr(F),
+                           _dptr(q))
+    _check(h, rc)
+    Fc = (F[..., 0::2] + 1j * F[..., 1::2])[:, :n_dir, :]
+    return Fc, q
+
+
+def dda_mueller_plane(theta_deg, F_xpol, F_ypol):
+    th = np.ascontiguousarray(np.asarray(theta_deg, dtype=np.float64))
+    fx = np.asarray(F_xpol, dtype=np.complex128).reshape(-1, 3)
+    fy = np.asarray(F_ypol, dtype=np.complex128).reshape(-1, 3)
+    fx2 = np.ascontiguousarray(np.stack([fx.real, fx.imag], axis=-1).reshape(-1))
+    fy2 = np.ascontiguousarray(np.stack([fy.real, fy.imag], axis=-1).reshape(-1))
+    out = np.zeros(th.size)
+    rc = lib().dda_mueller_plane(th.size, _dptr(th), _dptr(fx2), _dptr(fy2), _dptr(out))
+    if rc < 0:
+        raise DDAError(rc, "dda_mueller_plane")
+    return out
+
+
+def dda_trace(h, enable=True):
+    return _check(h, lib().dda_trace(h, int(bool(enable))))
+
+
+def dda_trace_read(h, max_n=32):
+    """Returns {kernel name: (total ms, launches)}."""
+    names = ctypes.create_string_buffer(32 * max_n)
+    ms = np.zeros(max_n)
+    cnt = np.zeros(max_n, dtype=np.int64)
+    n = ctypes.c_int()
+    _check(h, lib().dda_trace_read(h, max_n, names, _dptr(ms),
+                                   cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                   ctypes.byref(n)))
+    out = {}
+    for k in range(min(n.value, max_n)):
+        nm = names.raw[32 * k:32 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[k]), int(cnt[k]))
+    return out
+
+
+def dda_n_occ(h):
+    n = ctypes.c_longlong()
+    _check(h, lib().dda_n_occ(h, ctypes.byref(n)))
+    return n.value
+
+
+def dda_kd(h):
+    v = ctypes.c_double()
+    _check(h, lib().dda_kd(h, ctypes.byref(v)))
+    return v.value
+
+
+def dda_grid(h):
+    g = (ctypes.c_int * 3)()
+    _check(h, lib().dda_grid(h, g))
+    return tuple(g)
+
+
+def dda_positions(h):
+    n = dda_n_occ(h)
+    ijk = np.zeros((n, 3), dtype=np.int32)
+    _check(h, lib().dda_positions(h, ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return ijk
+
+
+def dda_last_error(h):
+    return lib().dda_last_error(h).decode()
+
+
+def dda_free(h):
+    return lib().dda_free(h)
+
+
+class Particle:
+    """Owns one handle; frees it on close / garbage collection."""
+
+    def __init__(self, occ, m_list, kd, volume_corrected=False, stream=None):
+        self.h = dda_init_lattice(occ, m_list, kd, volume_corrected, stream)
+        self.n_occ = dda_n_occ(self.h)
+        self.kd = dda_kd(self.h)
+        self.grid = dda_grid(self.h)
+
+    def close(self):
+        if self.h is not None:
+            dda_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
