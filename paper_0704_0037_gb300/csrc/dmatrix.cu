@@ -117,15 +117,18 @@ int dda_build_D_internal(dda_t h, bool want32) {
                                                  g.nz, g.Mx, g.My, g.Mz); count_launch();
     tr_end(g.tr, st, TR_DB_GREEN);
     tr_begin(g.tr, st);
-    // x lines (contiguous), y lines, z lines, all in place on the full grid
+    // x lines (contiguous) over the whole grid; then only the octant is
+    // needed, so y lines run for kx <= Mx/2 and z lines for kx <= Mx/2,
+    // ky <= My/2 (in place; the other entries are left untransformed).
+    const int hx = g.Mx / 2 + 1, hy = g.My / 2 + 1;
     e = launch_lines<double>(g, grid, grid, g.px, twx, false, g.Mx, g.Mx,
                              g.My * g.Mz, 1, 1, true, 1, g.Mx, 0, 0, 1, g.Mx, 0, 0, st);
     if (e != cudaSuccess) break;
-    e = launch_lines<double>(g, grid, grid, g.py, twy, false, g.My, g.My, g.Mx, g.Mz, 1, false,
+    e = launch_lines<double>(g, grid, grid, g.py, twy, false, g.My, g.My, hx, g.Mz, 1, false,
                              g.Mx, 1, (long long)g.My * g.Mx, 0, g.Mx, 1,
                              (long long)g.My * g.Mx, 0, st);
     if (e != cudaSuccess) break;
-    e = launch_lines<double>(g, grid, grid, g.pz, twz, false, g.Mz, g.Mz, g.Mx, g.My, 1, false,
+    e = launch_lines<double>(g, grid, grid, g.pz, twz, false, g.Mz, g.Mz, hx, hy, 1, false,
                              (long long)g.My * g.Mx, 1, g.Mx, 0, (long long)g.My * g.Mx, 1, g.Mx,
                              0, st);
     if (e != cudaSuccess) break;

@@ -117,6 +117,8 @@ struct dda_ctx {
   size_t tab_bytes = 0;
   double* d_fpart = nullptr;
   size_t fpart_bytes = 0;
+  void* d_coll = nullptr;         // y-collapsed polarization + its lattice
+  size_t coll_bytes = 0;
   dda::LatticeDev lat() const { return {d_row_off, d_xi, d_mat}; }
 };
 

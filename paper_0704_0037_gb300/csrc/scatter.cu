@@ -119,6 +119,34 @@ __global__ void k_farfield_fin(const double* __restrict__ part, int n_chunks, in
   }
 }
 
+// Directions with n_y = 0 (e.g. the xz scattering plane) see no phase along
+// y, so sum_j P_j exp(-i kappa n.r_j) = sum_{x,z} Q(x, z) exp(-i kappa n.r)
+// with Q(x, z) = sum_y P(x, y, z).  One block per z: the rows of that z-slab
+// are added in y order into a shared [nx][3] accumulator (dipoles of one row
+// have distinct x, so the order of every sum is fixed).  Q is laid out as the
+// dipole vector of a full nx x 1 x nz lattice: [3][nz*nx].
+__global__ void __launch_bounds__(256) k_collapse_y(const c128* __restrict__ P, LatticeDev lat,
+                                                    long long n_occ, int nx, int ny,
+                                                    c128* __restrict__ Q, long long nq) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  c128* acc = reinterpret_cast<c128*>(smem_raw);
+  const int z = blockIdx.x;
+  for (int i = threadIdx.x; i < 3 * nx; i += blockDim.x) acc[i] = mk<double>(0.0, 0.0);
+  __syncthreads();
+  for (int y = 0; y < ny; ++y) {
+    const int row = z * ny + y;
+    for (long long i = lat.row_off[row] + threadIdx.x; i < lat.row_off[row + 1]; i += blockDim.x) {
+      const int x = lat.xi[i];
+      for (int c = 0; c < 3; ++c) acc[3 * x + c] = acc[3 * x + c] + P[c * n_occ + i];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < 3 * nx; i += blockDim.x) {
+    const int x = i / 3, c = i - 3 * x;
+    Q[c * nq + (long long)z * nx + x] = acc[i];
+  }
+}
+
 struct Wave2 { double a[3]; double e[6]; };
 
 // per-row-chunk partials of sum Im(E_inc^* . P) and sum w |P|^2
@@ -176,14 +204,45 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
   const long long n = 3 * g.n_occ;
   const double xsz = h->kd * std::cbrt(3.0 * (double)g.n_occ / (4.0 * M_PI));
   const double k3 = h->kd * h->kd * h->kd;
-  const int L = g.nx + g.ny + g.nz;
+  // far-field lattice: the particle's, or its y-collapse when no direction
+  // has a y component (the xz scattering plane of Sec. 3.1)
+  bool collapse = n_dir > 0 && g.ny > 1 && (size_t)g.nx * 3 * sizeof(c128) <= 96 * 1024;
+  for (int d = 0; d < n_dir && collapse; ++d)
+    if (dirs[3 * d + 1] != 0.0) collapse = false;
+  const int fnx = g.nx, fny = collapse ? 1 : g.ny, fnz = g.nz;
+  const int fnrows = collapse ? g.nz : g.nrows;
+  const long long fnocc = collapse ? (long long)g.nx * g.nz : g.n_occ;
+  LatticeDev flat = h->lat();
+  c128* Qc = nullptr;
+  if (collapse) {
+    const size_t need = (size_t)fnocc * 3 * sizeof(c128) + (size_t)(g.nz + 1) * sizeof(long long) +
+                        (size_t)fnocc * sizeof(uint16_t) + 64;
+    if (h->coll_bytes < need) {
+      cudaFree(h->d_coll); h->d_coll = nullptr; h->coll_bytes = 0;
+      if (cudaMalloc(&h->d_coll, need) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter collapse buffer"); }
+      h->coll_bytes = need;
+    }
+    Qc = (c128*)h->d_coll;
+    long long* roff = (long long*)(Qc + (size_t)fnocc * 3);
+    uint16_t* xis = (uint16_t*)(roff + g.nz + 1);
+    std::vector<long long> ro(g.nz + 1);
+    std::vector<uint16_t> xv((size_t)fnocc);
+    for (int z = 0; z <= g.nz; ++z) ro[z] = (long long)z * g.nx;
+    for (long long i = 0; i < fnocc; ++i) xv[i] = (uint16_t)(i % g.nx);
+    DDA_CK(h, cudaMemcpy(roff, ro.data(), ro.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    DDA_CK(h, cudaMemcpy(xis, xv.data(), xv.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    flat.row_off = roff;
+    flat.xi = xis;
+    flat.mat = nullptr;
+  }
+  const int L = fnx + fny + fnz;
   const int qblocks = (int)std::min<long long>((g.nrows + 7) / 8, 1024);
-  int n_chunks = 1, rows_per_chunk = g.nrows;
+  int n_chunks = 1, rows_per_chunk = fnrows;
   if (n_dir > 0) {
     const int dblocks = (n_dir + kDB - 1) / kDB;
-    n_chunks = std::max(1, std::min((152 * 4 + dblocks - 1) / dblocks, (g.nrows + 31) / 32));
-    rows_per_chunk = (g.nrows + n_chunks - 1) / n_chunks;
-    n_chunks = (g.nrows + rows_per_chunk - 1) / rows_per_chunk;
+    n_chunks = std::max(1, std::min((152 * 4 + dblocks - 1) / dblocks, (fnrows + 31) / 32));
+    rows_per_chunk = (fnrows + n_chunks - 1) / n_chunks;
+    n_chunks = (fnrows + rows_per_chunk - 1) / rows_per_chunk;
   }
   const size_t tab_b = (size_t)std::max(n_dir, 1) * L * sizeof(c128) + (size_t)std::max(n_dir, 1) * 3 * sizeof(double);
   const size_t fp_b = std::max((size_t)n_chunks * std::max(n_dir, 1) * 6, (size_t)2 * qblocks) * sizeof(double) +
@@ -205,7 +264,7 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
   if (n_dir > 0) {
     DDA_CK(h, cudaMemcpyAsync(d_dirs, dirs, (size_t)n_dir * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
     const long long tt = (long long)n_dir * L;
-    k_phase_tab<<<(int)std::min<long long>((tt + 255) / 256, 4096), 256, 0, st>>>(d_dirs, n_dir, h->kd, g.nx, g.ny, g.nz, tab); count_launch();
+    k_phase_tab<<<(int)std::min<long long>((tt + 255) / 256, 4096), 256, 0, st>>>(d_dirs, n_dir, h->kd, fnx, fny, fnz, tab); count_launch();
     DDA_CK(h, cudaGetLastError());
   }
   std::vector<double> qp(2 * qblocks);
@@ -215,7 +274,14 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
     if (n_dir > 0) {
       dim3 grid((n_dir + kDB - 1) / kDB, n_chunks);
       tr_begin(g.tr, st);
-      k_farfield<<<grid, 256, 0, st>>>(P, h->lat(), tab, n_dir, g.nx, g.ny, g.nz, g.nrows, g.n_occ,
+      const c128* Pf = P;
+      if (collapse) {
+        const size_t sm = (size_t)g.nx * 3 * sizeof(c128);
+        DDA_CK(h, cudaFuncSetAttribute(k_collapse_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_collapse_y<<<g.nz, 256, sm, st>>>(P, h->lat(), g.n_occ, g.nx, g.ny, Qc, fnocc); count_launch();
+        Pf = Qc;
+      }
+      k_farfield<<<grid, 256, 0, st>>>(Pf, flat, tab, n_dir, fnx, fny, fnz, fnrows, fnocc,
                                        rows_per_chunk, part); count_launch();
       tr_end(g.tr, st, TR_FARFIELD);
       k_farfield_fin<<<(n_dir + 127) / 128, 128, 0, st>>>(part, n_chunks, n_dir, d_dirs, h->kd, d_F); count_launch();
