@@ -208,6 +208,31 @@ int dda_mueller_plane(int n_theta, const double* theta_deg_host, const double* F
                       const double* F_ypol_host, double* s11_out_host);
 
 /*
+ * dda_farfield_noalloc -- the scattering amplitude F(n) of dda_scatter for
+ * one polarization vector, computed without allocating any device memory.
+ * (The paper has no counterpart: this is an interface for callers that cannot
+ * let a library call cudaMalloc -- code running under CUDA stream capture,
+ * processes whose device memory comes from their own allocator or is fixed
+ * at start-up.)
+ *   P_dev    : device [3][N_occ] complex128 polarization (one RHS), read only.
+ *   n_dir    : number of directions, >= 1.
+ *   dirs_dev : device [n_dir][3] doubles, unit directions n.
+ *   F_dev    : device [n_dir][3] complex128 (re, im) output,
+ *              F(n) = -i kd^3 (I - n n) sum_j P_j exp(-i kd n.r_j).
+ * Working memory is one fixed 8 MiB array in device global memory that the
+ * library image carries (every GPU that loads the library holds it until the
+ * process exits); a request needing more than that (about n_dir *
+ * (nx+ny+nz) * 16 bytes plus the partial sums) returns DDA_ERR_ARG with the
+ * size in dda_last_error.  The first call on a device looks up the array's
+ * address with that device current: make it before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU race; the array
+ * keeps the last call's contents, which no call depends on.  Asynchronous on
+ * the handle's stream; calls no cudaMalloc or cudaFree.
+ */
+int dda_farfield_noalloc(dda_t h, const void* P_dev, int n_dir, const double* dirs_dev,
+                         void* F_dev);
+
+/*
  * dda_trace -- per-kernel timing (the paper reports only whole-run times,
  * Fig. 3; this is the library's own tracing).  enable != 0 starts recording a
  * CUDA event pair around each launch of the product passes P1..P5, the

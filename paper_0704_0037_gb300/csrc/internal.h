@@ -150,3 +150,16 @@ namespace dda {
 void count_launch();
 long long launch_total();
 }  // namespace dda
+
+namespace dda {
+// Far-field kernels (scatter.cu), shared with the allocation-free entry point.
+constexpr int kFarfieldDB = 4;   // directions per block of k_farfield
+__global__ void k_phase_tab(const double* dirs, int n_dir, double kd, int nx, int ny, int nz,
+                            c128* tab);
+__global__ void __launch_bounds__(256) k_farfield(const c128* P, LatticeDev lat, const c128* tab,
+                                                  int n_dir, int nx, int ny, int nz, int nrows,
+                                                  long long n_occ, int rows_per_chunk,
+                                                  double* part);
+__global__ void k_farfield_fin(const double* part, int n_chunks, int n_dir, const double* dirs,
+                               double kd, double* F);
+}  // namespace dda

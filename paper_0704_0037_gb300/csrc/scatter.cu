@@ -16,7 +16,7 @@
 
 namespace dda {
 
-constexpr int kDB = 4;        // directions per block
+constexpr int kDB = kFarfieldDB;        // directions per block
 
 __global__ void k_phase_tab(const double* __restrict__ dirs, int n_dir, double kd, int nx, int ny,
                             int nz, c128* __restrict__ tab) {

@@ -33,7 +33,8 @@ PREC = {"fp64": DDA_FP64, "fp32_refined": DDA_FP32_REFINED}
 
 # every entry point declared in include/dda.h
 EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec",
-           "dda_matvec_adjoint", "dda_solve", "dda_scatter", "dda_mueller_plane", "dda_trace",
+           "dda_matvec_adjoint", "dda_solve", "dda_scatter", "dda_mueller_plane",
+           "dda_farfield_noalloc", "dda_trace",
            "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
            "dda_free")
 
@@ -88,6 +89,7 @@ def lib():
                        ctypes.POINTER(SolveInfo)], _ip),
         "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
+        "dda_farfield_noalloc": ([_vp, _vp, _ip, _vp, _vp], _ip),
         "dda_trace": ([_vp, _ip], _ip),
         "dda_trace_read": ([_vp, _ip, ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_int)], _ip),
@@ -232,6 +234,17 @@ def dda_mueller_plane(theta_deg, F_xpol, F_ypol):
     if rc < 0:
         raise DDAError(rc, "dda_mueller_plane")
     return out
+
+
+def dda_farfield_noalloc(h, P, dirs, F):
+    """F(n) for one polarization vector without any device allocation by the
+    library.  P: CUDA complex128 [3][N_occ] (or [1][3][N_occ]); dirs: CUDA
+    float64 [n_dir][3]; F: CUDA complex128 [n_dir][3] (written)."""
+    import torch
+    n_dir = int(dirs.shape[0])
+    return _check(h, lib().dda_farfield_noalloc(h, _dev_ptr(P, torch.complex128), n_dir,
+                                                _dev_ptr(dirs, torch.float64),
+                                                _dev_ptr(F, torch.complex128)))
 
 
 def dda_trace(h, enable=True):
