@@ -84,6 +84,10 @@ enum dda_prec { DDA_FP64 = 0, DDA_FP32_REFINED = 1 };
  *   cuda_stream: cudaStream_t on which all device work is enqueued.
  * Errors: DDA_ERR_ARG (bad sizes, no occupied cell, material index > n_mat),
  *   DDA_ERR_CUDA / DDA_ERR_OOM.  Copies what it needs from the host arrays.
+ * The FFT passes use register-resident kernels for padded lengths with a
+ * compiled split (32, 64, 128, 256, 270) and shared-memory Stockham kernels
+ * otherwise; environment variable DDA_FFT_ENGINE=stockham at this call forces
+ * the latter for the handle (both give the same product to rounding).
  */
 int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_t* occ_host,
                      int n_mat, const double* m_host, double kd, int volume_corrected,

@@ -2,6 +2,7 @@
 // Equation and section references are to Yurkin, Maltsev & Hoekstra,
 // arXiv:0704.0037.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -219,6 +220,8 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   g.Mz = smooth_size(2 * nz - 1);
   g.px = make_plan(g.Mx); g.py = make_plan(g.My); g.pz = make_plan(g.Mz);
   g.tr = &h->tracer;
+  const char* eng = std::getenv("DDA_FFT_ENGINE");
+  g.engine = (eng && std::strcmp(eng, "stockham") == 0) ? 1 : 0;
   h->n_mat = n_mat;
   h->m.assign(m, m + 2 * n_mat);
   // Sec. 3.1 volume correction: N_occ d^3 = (4/3) pi a^3  =>  kd = x (4 pi / (3 N_occ))^(1/3)

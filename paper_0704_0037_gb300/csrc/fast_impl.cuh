@@ -1,0 +1,31 @@
+// Dispatch of one product pass to the Passes<R, M1, M2> launchers.
+#pragma once
+
+#include "fastfft.cuh"
+
+namespace dda {
+namespace fast {
+
+template <typename R, int M1, int M2>
+cudaError_t run_pass(int pass, const FastArgs& a) {
+  using P = Passes<R, M1, M2>;
+  const cpx<R>* tw = (const cpx<R>*)a.tw;
+  switch (pass) {
+    case FP_XFWD:
+      return P::xfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.lat, (const cpx<R>*)a.beta, a.n_occ,
+                     a.nrows, tw, a.adj, a.st);
+    case FP_YFWD:
+      return P::yfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.st);
+    case FP_ZCONV:
+      return P::zconv((cpx<R>*)a.out, (const cpx<R>*)a.D, a.nz, a.Mx, a.My, tw, a.st);
+    case FP_YINV:
+      return P::yinv((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.st);
+    case FP_XINV:
+      return P::xinv((const cpx<R>*)a.in, (const cpx<R>*)a.x, (cpx<R>*)a.out, a.lat,
+                     (const cpx<R>*)a.beta, a.n_occ, a.nrows, tw, a.adj, a.st);
+  }
+  return cudaErrorNotSupported;
+}
+
+}  // namespace fast
+}  // namespace dda

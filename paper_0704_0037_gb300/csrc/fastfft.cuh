@@ -1,0 +1,449 @@
+// Register-resident two-level FFT passes of the interaction-matrix product.
+//
+// Same five passes as matvec.cu (arXiv:0704.0037, Sec. 2: 1D transforms with
+// pruned input and partial output), for padded lengths M = M1 * M2 known at
+// compile time.  A length-M line is split with n = j + M2 i (j < M2, i < M1)
+// and k = k1 + M1 k2:
+//   phase 1: for each column j, an M1-point DFT over i (registers), then the
+//            twiddle exp(-2 pi i j k1 / M) (shared-memory table);
+//   phase 2: for each k1, an M2-point DFT over j (registers) gives X[k1 + M1 k2].
+// The inverse runs the two phases in reverse with conjugate twiddles.
+// Element (r, t) of T lines lives in shared memory as row r = k1 * M2 + j.
+// Thread (t, q) handles line t: q is the column j in phase 1 and k1 in phase 2,
+// so each thread only ever touches its own rows between the two barriers.
+//
+// Lines along y and z are strided in global memory; T adjacent lines (along
+// x) are contiguous, so every global access of a warp covers T consecutive
+// complex numbers.  Lines along x are contiguous; their tiles sit in shared
+// memory as [t][LD] with LD odd (bank-conflict free) and are loaded and
+// stored row by row.
+#pragma once
+
+#include "codelets.cuh"
+#include "internal.h"
+
+namespace dda {
+namespace fast {
+
+template <int M1, int M2> constexpr int kQ = M1 > M2 ? M1 : M2;
+
+template <typename R>
+__device__ __forceinline__ cpx<R> zero() { return mk<R>((R)0, (R)0); }
+
+template <typename R>
+__device__ __forceinline__ void load_tw(cpx<R>* s_tw, const cpx<R>* __restrict__ tw, int M, int nt) {
+  for (int i = threadIdx.x; i < M; i += nt) s_tw[i] = tw[i];
+}
+
+// ---------------------------------------------------------------- P2: y forward
+// B1 [3][nz][ny][Mx] -> B2 [3][nz][M][Mx]; grid (ceil(Mx/T), nz, 3)
+template <typename R, int M1, int M2, int T>
+__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restrict__ in,
+                                                          cpx<R>* __restrict__ out, int ny, int nz,
+                                                          int Mx, const cpx<R>* __restrict__ tw) {
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* s = s_tw + M;
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  const int kx = blockIdx.x * T + t;
+  const long long ib = ((long long)blockIdx.z * nz + blockIdx.y) * ny * Mx;
+  const long long ob = ((long long)blockIdx.z * nz + blockIdx.y) * M * Mx;
+  load_tw(s_tw, tw, M, NT);
+  __syncthreads();
+  if (q < M2) {
+    const int j = q;
+    cpx<R> v[M1];
+#pragma unroll
+    for (int i = 0; i < M1; ++i) {
+      const int y = j + M2 * i;
+      v[i] = (y < ny && kx < Mx) ? in[ib + (long long)y * Mx + kx] : zero<R>();
+    }
+    cl::Dft<R, false, M1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < M1; ++k1) s[(k1 * M2 + j) * T + t] = v[k1];
+  }
+  __syncthreads();
+  if (q < M1 && kx < Mx) {
+    const int k1 = q;
+    cpx<R> u[M2];
+#pragma unroll
+    for (int j = 0; j < M2; ++j) u[j] = s[(k1 * M2 + j) * T + t];
+    cl::Dft<R, false, M2>::run(u);
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) out[ob + (long long)(k1 + M1 * k2) * Mx + kx] = u[k2];
+  }
+}
+
+// ---------------------------------------------------------------- P4: y inverse
+// B2 [3][nz][M][Mx] -> B1 [3][nz][ny][Mx] (y < ny kept); grid (ceil(Mx/T), nz, 3)
+template <typename R, int M1, int M2, int T>
+__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yinv(const cpx<R>* __restrict__ in,
+                                                          cpx<R>* __restrict__ out, int ny, int nz,
+                                                          int Mx, const cpx<R>* __restrict__ tw) {
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* s = s_tw + M;
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  const int kx = blockIdx.x * T + t;
+  const long long ib = ((long long)blockIdx.z * nz + blockIdx.y) * M * Mx;
+  const long long ob = ((long long)blockIdx.z * nz + blockIdx.y) * ny * Mx;
+  load_tw(s_tw, tw, M, NT);
+  __syncthreads();
+  if (q < M1) {
+    const int k1 = q;
+    cpx<R> u[M2];
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2)
+      u[k2] = kx < Mx ? in[ib + (long long)(k1 + M1 * k2) * Mx + kx] : zero<R>();
+    cl::Dft<R, true, M2>::run(u);
+#pragma unroll
+    for (int j = 1; j < M2; ++j) u[j] = twiddle<R, true>(u[j], s_tw[j * k1]);
+#pragma unroll
+    for (int j = 0; j < M2; ++j) s[(k1 * M2 + j) * T + t] = u[j];
+  }
+  __syncthreads();
+  if (q < M2 && kx < Mx) {
+    const int j = q;
+    cpx<R> v[M1];
+#pragma unroll
+    for (int k1 = 0; k1 < M1; ++k1) v[k1] = s[(k1 * M2 + j) * T + t];
+    cl::Dft<R, true, M1>::run(v);
+#pragma unroll
+    for (int i = 0; i < M1; ++i) {
+      const int y = j + M2 * i;
+      if (y < ny) out[ob + (long long)y * Mx + kx] = v[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- P3: z fused
+// In place on B2 [3][nz][My][Mx]: per (kx, ky) line, forward z transform of the
+// nz nonzero inputs, 3x3 product with the octant of FFT(G) (parity signs),
+// inverse z transform, z < nz kept.  grid (ceil(Mx/T), My).
+__device__ __forceinline__ int fold_axis(int k, int M, int& neg) {
+  if (2 * k > M) { neg = 1; return M - k; }
+  neg = 0;
+  return k;
+}
+
+template <typename R, int M1, int M2, int T>
+__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_zconv(cpx<R>* __restrict__ B2,
+                                                           const cpx<R>* __restrict__ D, int nz,
+                                                           int Mx, int My,
+                                                           const cpx<R>* __restrict__ tw) {
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* s = s_tw + M;                      // [3][M][T]
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  const int kx = blockIdx.x * T + t;
+  const int ky = blockIdx.y;
+  const long long plane = (long long)My * Mx;
+  const long long comp = (long long)nz * plane;
+  const long long col = (long long)ky * Mx + kx;
+  load_tw(s_tw, tw, M, NT);
+  __syncthreads();
+  if (q < M2) {
+    const int j = q;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cpx<R> v[M1];
+#pragma unroll
+      for (int i = 0; i < M1; ++i) {
+        const int z = j + M2 * i;
+        v[i] = (z < nz && kx < Mx) ? B2[c * comp + z * plane + col] : zero<R>();
+      }
+      cl::Dft<R, false, M1>::run(v);
+#pragma unroll
+      for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
+      cpx<R>* sc = s + c * M * T;
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) sc[(k1 * M2 + j) * T + t] = v[k1];
+    }
+  }
+  __syncthreads();
+  if (q < M1 && kx < Mx) {
+    const int k1 = q;
+    // forward phase 2 of each component, written back to this thread's rows
+    // (row k1*M2 + k2 holds kz = k1 + M1*k2)
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cpx<R>* sc = s + c * M * T;
+      cpx<R> u[M2];
+#pragma unroll
+      for (int j = 0; j < M2; ++j) u[j] = sc[(k1 * M2 + j) * T + t];
+      cl::Dft<R, false, M2>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < M2; ++k2) sc[(k1 * M2 + k2) * T + t] = u[k2];
+    }
+    // Fourier-space product with the octant of FFT(G)
+    const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
+    const long long octs = (long long)hx * hy * hz;
+    int nxs, nys;
+    const int fx = fold_axis(kx, Mx, nxs);
+    const int fy = fold_axis(ky, My, nys);
+#pragma unroll 2
+    for (int k2 = 0; k2 < M2; ++k2) {
+      const int kz = k1 + M1 * k2;
+      int nzs;
+      const int fz = fold_axis(kz, M, nzs);
+      const long long o = ((long long)fz * hy + fy) * hx + fx;
+      const cpx<R> dxx = D[o], dyy = D[3 * octs + o], dzz = D[5 * octs + o];
+      cpx<R> dxy = D[octs + o], dxz = D[2 * octs + o], dyz = D[4 * octs + o];
+      if (nxs ^ nys) dxy = mk<R>(-dxy.x, -dxy.y);
+      if (nxs ^ nzs) dxz = mk<R>(-dxz.x, -dxz.y);
+      if (nys ^ nzs) dyz = mk<R>(-dyz.x, -dyz.y);
+      const int e = (k1 * M2 + k2) * T + t;
+      const cpx<R> vx = s[e], vy = s[M * T + e], vz = s[2 * M * T + e];
+      s[e] = dxx * vx + dxy * vy + dxz * vz;
+      s[M * T + e] = dxy * vx + dyy * vy + dyz * vz;
+      s[2 * M * T + e] = dxz * vx + dyz * vy + dzz * vz;
+    }
+    // inverse phase A of each component: M2-point inverse over k2, conjugate twiddle
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cpx<R>* sc = s + c * M * T;
+      cpx<R> u[M2];
+#pragma unroll
+      for (int k2 = 0; k2 < M2; ++k2) u[k2] = sc[(k1 * M2 + k2) * T + t];
+      cl::Dft<R, true, M2>::run(u);
+#pragma unroll
+      for (int j = 1; j < M2; ++j) u[j] = twiddle<R, true>(u[j], s_tw[j * k1]);
+#pragma unroll
+      for (int j = 0; j < M2; ++j) sc[(k1 * M2 + j) * T + t] = u[j];
+    }
+  }
+  __syncthreads();
+  if (q < M2 && kx < Mx) {
+    const int j = q;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      const cpx<R>* sc = s + c * M * T;
+      cpx<R> v[M1];
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) v[k1] = sc[(k1 * M2 + j) * T + t];
+      cl::Dft<R, true, M1>::run(v);
+#pragma unroll
+      for (int i = 0; i < M1; ++i) {
+        const int z = j + M2 * i;
+        if (z < nz) B2[c * comp + z * plane + col] = v[i];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- P1: x forward
+// gather beta*x of T rows into a [t][LD] tile, transform, store rows of
+// B1 [3][nrows][M]; grid (ceil(nrows/T), 3)
+template <int M> constexpr int kLD = (M % 2 == 1) ? M : M + 1;
+
+template <typename R, int M1, int M2, int T, bool CONJ>
+__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_xfwd(const cpx<R>* __restrict__ x,
+                                                          cpx<R>* __restrict__ B1, LatticeDev lat,
+                                                          const cpx<R>* __restrict__ beta,
+                                                          long long n_occ, int nrows,
+                                                          const cpx<R>* __restrict__ tw) {
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* a = s_tw + M;                      // [T][LD]
+  const int c = blockIdx.y;
+  const int r0 = blockIdx.x * T;
+  load_tw(s_tw, tw, M, NT);
+  for (int i = threadIdx.x; i < T * LD; i += NT) a[i] = zero<R>();
+  __syncthreads();
+  const cpx<R>* xc = x + (long long)c * n_occ;
+  for (int t = 0; t < T; ++t) {
+    const int row = r0 + t;
+    if (row >= nrows) break;
+    const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
+    for (long long i = s0 + threadIdx.x; i < s1; i += NT) {
+      cpx<R> v = xc[i];
+      if (CONJ) v = conjg(v);
+      a[t * LD + lat.xi[i]] = beta[lat.mat[i] * 3 + c] * v;
+    }
+  }
+  __syncthreads();
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  cpx<R>* at = a + t * LD;
+  if (q < M2) {              // phase 1: reads and writes the same set {j + M2 i}
+    const int j = q;
+    cpx<R> v[M1];
+#pragma unroll
+    for (int i = 0; i < M1; ++i) v[i] = at[j + M2 * i];
+    cl::Dft<R, false, M1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < M1; ++k1) at[k1 * M2 + j] = v[k1];
+  }
+  __syncthreads();
+  cpx<R> u[M2];
+  if (q < M1) {
+    const int k1 = q;
+#pragma unroll
+    for (int j = 0; j < M2; ++j) u[j] = at[k1 * M2 + j];
+    cl::Dft<R, false, M2>::run(u);
+  }
+  __syncthreads();
+  if (q < M1) {              // natural order k = k1 + M1 k2
+    const int k1 = q;
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) at[k1 + M1 * k2] = u[k2];
+  }
+  __syncthreads();
+  cpx<R>* out = B1 + (long long)c * nrows * M;
+  for (int idx = threadIdx.x; idx < T * M; idx += NT) {
+    const int tt = idx / M, m = idx - tt * M;
+    const int row = r0 + tt;
+    if (row < nrows) out[(long long)row * M + m] = a[tt * LD + m];
+  }
+}
+
+// ---------------------------------------------------------------- P5: x inverse
+// rows of B1 -> [t][LD] tile, inverse transform, y = x - beta u at the
+// occupied x; grid (ceil(nrows/T), 3)
+template <typename R, int M1, int M2, int T, bool CONJ>
+__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_xinv(const cpx<R>* __restrict__ B1,
+                                                          const cpx<R>* __restrict__ x,
+                                                          cpx<R>* __restrict__ y, LatticeDev lat,
+                                                          const cpx<R>* __restrict__ beta,
+                                                          long long n_occ, int nrows,
+                                                          const cpx<R>* __restrict__ tw) {
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* a = s_tw + M;                      // [T][LD]
+  const int c = blockIdx.y;
+  const int r0 = blockIdx.x * T;
+  load_tw(s_tw, tw, M, NT);
+  const cpx<R>* in = B1 + (long long)c * nrows * M;
+  for (int idx = threadIdx.x; idx < T * M; idx += NT) {
+    const int tt = idx / M, m = idx - tt * M;
+    const int row = r0 + tt;
+    a[tt * LD + m] = row < nrows ? in[(long long)row * M + m] : zero<R>();
+  }
+  __syncthreads();
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  cpx<R>* at = a + t * LD;
+  cpx<R> u[M2];
+  if (q < M1) {              // phase A reads k = k1 + M1 k2
+    const int k1 = q;
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) u[k2] = at[k1 + M1 * k2];
+    cl::Dft<R, true, M2>::run(u);
+#pragma unroll
+    for (int j = 1; j < M2; ++j) u[j] = twiddle<R, true>(u[j], s_tw[j * k1]);
+  }
+  __syncthreads();
+  if (q < M1) {
+    const int k1 = q;
+#pragma unroll
+    for (int j = 0; j < M2; ++j) at[k1 * M2 + j] = u[j];
+  }
+  __syncthreads();
+  if (q < M2) {              // phase B reads and writes the same set {j + M2 i}
+    const int j = q;
+    cpx<R> v[M1];
+#pragma unroll
+    for (int k1 = 0; k1 < M1; ++k1) v[k1] = at[k1 * M2 + j];
+    cl::Dft<R, true, M1>::run(v);
+#pragma unroll
+    for (int i = 0; i < M1; ++i) at[j + M2 * i] = v[i];
+  }
+  __syncthreads();
+  const cpx<R>* xc = x + (long long)c * n_occ;
+  cpx<R>* yc = y + (long long)c * n_occ;
+  for (int tt = 0; tt < T; ++tt) {
+    const int row = r0 + tt;
+    if (row >= nrows) break;
+    const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
+    for (long long i = s0 + threadIdx.x; i < s1; i += NT) {
+      cpx<R> v = xc[i];
+      if (CONJ) v = conjg(v);
+      cpx<R> o = v - beta[lat.mat[i] * 3 + c] * a[tt * LD + lat.xi[i]];
+      if (CONJ) o = conjg(o);
+      yc[i] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename R> constexpr int kT = sizeof(R) == 4 ? 16 : 8;
+
+template <typename K>
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Launches of one pass for a compile-time length; returns cudaErrorNotSupported
+// for a length without a specialisation.
+template <typename R, int M1, int M2>
+struct Passes {
+  static constexpr int M = M1 * M2, T = kT<R>, NT = T * kQ<M1, M2>;
+  static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
+                          const cpx<R>* tw, cudaStream_t st) {
+    const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
+    if (e != cudaSuccess) return e;
+    fk_yfwd<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3), NT, sm, st>>>(in, out, ny, nz, Mx, tw);
+    count_launch();
+    return cudaGetLastError();
+  }
+  static cudaError_t yinv(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
+                          const cpx<R>* tw, cudaStream_t st) {
+    const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_yinv<R, M1, M2, T>, sm);
+    if (e != cudaSuccess) return e;
+    fk_yinv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3), NT, sm, st>>>(in, out, ny, nz, Mx, tw);
+    count_launch();
+    return cudaGetLastError();
+  }
+  static cudaError_t zconv(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
+                           cudaStream_t st) {
+    const size_t sm = (size_t)(M + 3 * M * T) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_zconv<R, M1, M2, T>, sm);
+    if (e != cudaSuccess) return e;
+    fk_zconv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, My), NT, sm, st>>>(B2, D, nz, Mx, My, tw);
+    count_launch();
+    return cudaGetLastError();
+  }
+  static cudaError_t xfwd(const cpx<R>* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,
+                          long long n_occ, int nrows, const cpx<R>* tw, bool adj, cudaStream_t st) {
+    const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
+    const dim3 grid((nrows + T - 1) / T, 3);
+    cudaError_t e;
+    if (adj) {
+      if ((e = set_smem(fk_xfwd<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
+      fk_xfwd<R, M1, M2, T, true><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw);
+    } else {
+      if ((e = set_smem(fk_xfwd<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
+      fk_xfwd<R, M1, M2, T, false><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw);
+    }
+    count_launch();
+    return cudaGetLastError();
+  }
+  static cudaError_t xinv(const cpx<R>* B1, const cpx<R>* x, cpx<R>* y, const LatticeDev& lat,
+                          const cpx<R>* beta, long long n_occ, int nrows, const cpx<R>* tw, bool adj,
+                          cudaStream_t st) {
+    const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
+    const dim3 grid((nrows + T - 1) / T, 3);
+    cudaError_t e;
+    if (adj) {
+      if ((e = set_smem(fk_xinv<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
+      fk_xinv<R, M1, M2, T, true><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw);
+    } else {
+      if ((e = set_smem(fk_xinv<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
+      fk_xinv<R, M1, M2, T, false><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw);
+    }
+    count_launch();
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace fast
+}  // namespace dda

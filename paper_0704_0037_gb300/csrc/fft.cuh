@@ -39,14 +39,14 @@ struct FftPlan {
 #define DDA_R2 0.7071067811865475244008444
 
 template <typename R, bool INV>
-__device__ __forceinline__ void bfly2(cpx<R>& a, cpx<R>& b) {
+__host__ __device__ __forceinline__ void bfly2(cpx<R>& a, cpx<R>& b) {
   cpx<R> t = a - b;
   a = a + b;
   b = t;
 }
 
 template <typename R, bool INV>
-__device__ __forceinline__ void bfly3(cpx<R>& a, cpx<R>& b, cpx<R>& c) {
+__host__ __device__ __forceinline__ void bfly3(cpx<R>& a, cpx<R>& b, cpx<R>& c) {
   cpx<R> t = b + c;
   cpx<R> d = a - scale<R>(t, (R)0.5);
   cpx<R> e = mul_mi<R, INV>(scale<R>(b - c, (R)DDA_S3));
@@ -56,7 +56,7 @@ __device__ __forceinline__ void bfly3(cpx<R>& a, cpx<R>& b, cpx<R>& c) {
 }
 
 template <typename R, bool INV>
-__device__ __forceinline__ void bfly4(cpx<R>& a, cpx<R>& b, cpx<R>& c, cpx<R>& d) {
+__host__ __device__ __forceinline__ void bfly4(cpx<R>& a, cpx<R>& b, cpx<R>& c, cpx<R>& d) {
   cpx<R> s0 = a + c, s1 = a - c, s2 = b + d;
   cpx<R> s3 = mul_mi<R, INV>(b - d);
   a = s0 + s2;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void bfly4(cpx<R>& a, cpx<R>& b, cpx<R>& c, cpx<R>& d
 }
 
 template <typename R, bool INV>
-__device__ __forceinline__ void bfly5(cpx<R>* v) {
+__host__ __device__ __forceinline__ void bfly5(cpx<R>* v) {
   cpx<R> t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
   cpx<R> a1 = v[0] + scale<R>(t1, (R)DDA_C51) + scale<R>(t2, (R)DDA_C52);
   cpx<R> a2 = v[0] + scale<R>(t1, (R)DDA_C52) + scale<R>(t2, (R)DDA_C51);
@@ -80,7 +80,7 @@ __device__ __forceinline__ void bfly5(cpx<R>* v) {
 }
 
 template <typename R, bool INV>
-__device__ __forceinline__ void bfly7(cpx<R>* v) {
+__host__ __device__ __forceinline__ void bfly7(cpx<R>* v) {
   cpx<R> t1 = v[1] + v[6], t2 = v[2] + v[5], t3 = v[3] + v[4];
   cpx<R> u1 = v[1] - v[6], u2 = v[2] - v[5], u3 = v[3] - v[4];
   cpx<R> x0 = v[0];
@@ -98,7 +98,7 @@ __device__ __forceinline__ void bfly7(cpx<R>* v) {
 
 // z * w8^k, w8 = exp(-i pi/4) (forward) or its conjugate (inverse)
 template <typename R, bool INV, int K>
-__device__ __forceinline__ cpx<R> rot8(cpx<R> z) {
+__host__ __device__ __forceinline__ cpx<R> rot8(cpx<R> z) {
   const R r2 = (R)DDA_R2;
   if (K == 1) return INV ? mk<R>((z.x - z.y) * r2, (z.x + z.y) * r2)
                          : mk<R>((z.x + z.y) * r2, (z.y - z.x) * r2);
@@ -109,7 +109,7 @@ __device__ __forceinline__ cpx<R> rot8(cpx<R> z) {
 }
 
 template <typename R, bool INV>
-__device__ __forceinline__ void bfly8(cpx<R>* v) {
+__host__ __device__ __forceinline__ void bfly8(cpx<R>* v) {
   cpx<R> a0 = v[0] + v[4], a1 = v[1] + v[5], a2 = v[2] + v[6], a3 = v[3] + v[7];
   cpx<R> b0 = v[0] - v[4];
   cpx<R> b1 = rot8<R, INV, 1>(v[1] - v[5]);

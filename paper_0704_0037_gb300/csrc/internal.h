@@ -45,6 +45,7 @@ struct Geom {
   long long n_occ;         // occupied dipoles
   FftPlan px, py, pz;      // plans for lengths Mx, My, Mz
   Tracer* tr = nullptr;    // per-kernel timing, owned by the handle
+  int engine = 0;          // 0: register-resident passes where available; 1: Stockham only
   long long oct() const { return (long long)(Mx / 2 + 1) * (My / 2 + 1) * (Mz / 2 + 1); }
   long long b1() const { return 3LL * nrows * Mx; }          // [3][nz][ny][Mx]
   long long b2() const { return 3LL * nz * My * Mx; }        // [3][nz][My][Mx]
@@ -162,4 +163,29 @@ __global__ void __launch_bounds__(256) k_farfield(const c128* P, LatticeDev lat,
                                                   double* part);
 __global__ void k_farfield_fin(const double* part, int n_chunks, int n_dir, const double* dirs,
                                double kd, double* F);
+}  // namespace dda
+
+namespace dda {
+// Register-resident product passes for padded lengths with a compile-time
+// split M = M1 * M2 (fastfft.cuh).  fast_supported(M) tells whether a length
+// has one; fast_pass returns cudaErrorNotSupported otherwise.
+enum FastPass { FP_XFWD, FP_YFWD, FP_ZCONV, FP_YINV, FP_XINV };
+struct FastArgs {
+  const void* in;        // pass input (B1, B2, or x for FP_XFWD)
+  void* out;             // pass output (B1, B2, or y for FP_XINV); FP_ZCONV: B2 in place
+  const void* x;         // FP_XINV: the product's input vector
+  const void* beta;      // [n_mat][3] for this right-hand side
+  const void* D;         // FP_ZCONV: octant of FFT(G)
+  const void* tw;        // twiddles of this axis, exp(-2 pi i m / M)
+  LatticeDev lat;
+  long long n_occ;
+  int nrows, ny, nz, Mx, My;
+  bool adj;
+  cudaStream_t st;
+};
+bool fast_supported(int M);
+template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a);
+template <typename R> cudaError_t fast_pass_270(int pass, const FastArgs& a);
+template <typename R> cudaError_t fast_pass_256(int pass, const FastArgs& a);
+template <typename R> cudaError_t fast_pass_small(int M, int pass, const FastArgs& a);
 }  // namespace dda

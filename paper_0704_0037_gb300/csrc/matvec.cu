@@ -308,14 +308,26 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
   if ((e = allow_smem(k_p5<R, true>, sm1)) != cudaSuccess) return e;
   if ((e = allow_smem(k_p3<R>, sm3)) != cudaSuccess) return e;
   const long long nv = 3LL * g.n_occ;
+  // per axis: the register-resident passes when the padded length has a
+  // compile-time split, the shared-memory Stockham passes otherwise
+  const bool fx = g.engine == 0 && fast_supported(g.Mx);
+  const bool fy = g.engine == 0 && fast_supported(g.My);
+  const bool fz = g.engine == 0 && fast_supported(g.Mz);
   for (int r = 0; r < nrhs; ++r) {
     const cpx<R>* xr = x + r * nv;
     cpx<R>* yr = y + r * nv;
     const cpx<R>* br = beta + (long long)r * n_mat * 3;
+    FastArgs fa{};
+    fa.lat = lat; fa.beta = br; fa.D = w.D; fa.n_occ = g.n_occ; fa.nrows = g.nrows;
+    fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = adjoint; fa.st = st;
     dim3 g1((g.nrows + (1 << lt1) - 1) >> lt1, 3);
     const int tb = sizeof(R) == 4 ? TR_P1_C64 : TR_P1_C128;
+    // P1: x lines of the occupied rows, gather and beta -> B1 [3][nz][ny][Mx]
     tr_begin(g.tr, st);
-    if (adjoint) {
+    if (fx) {
+      fa.in = xr; fa.out = w.B1; fa.tw = twx;
+      if ((e = fast_pass<R>(g.Mx, FP_XFWD, fa)) != cudaSuccess) return e;
+    } else if (adjoint) {
       k_p1<R, true><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
     } else {
       k_p1<R, false><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
@@ -323,24 +335,44 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
     tr_end(g.tr, st, tb);
     tr_begin(g.tr, st);
     // P2: y lines of B1 [3][nz][ny][Mx] -> B2 [3][nz][My][Mx]
-    e = launch_lines<R>(g, w.B1, w.B2, g.py, twy, false, g.ny, g.My, g.Mx, g.nz, 3, false,
-                        g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx,
-                        g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx, st);
+    if (fy) {
+      fa.in = w.B1; fa.out = w.B2; fa.tw = twy;
+      e = fast_pass<R>(g.My, FP_YFWD, fa);
+    } else {
+      e = launch_lines<R>(g, w.B1, w.B2, g.py, twy, false, g.ny, g.My, g.Mx, g.nz, 3, false,
+                          g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx,
+                          g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx, st);
+    }
     if (e != cudaSuccess) return e;
     tr_end(g.tr, st, tb + 1);
     dim3 g3((g.Mx + (1 << lt3) - 1) >> lt3, g.My);
     tr_begin(g.tr, st);
-    k_p3<R><<<g3, 256, sm3, st>>>(w.B2, w.D, g.nz, g.Mx, g.My, g.pz, twz, lt3); count_launch();
+    // P3: z lines, product with the octant of FFT(G), inverse z lines (in place)
+    if (fz) {
+      fa.out = w.B2; fa.tw = twz;
+      if ((e = fast_pass<R>(g.Mz, FP_ZCONV, fa)) != cudaSuccess) return e;
+    } else {
+      k_p3<R><<<g3, 256, sm3, st>>>(w.B2, w.D, g.nz, g.Mx, g.My, g.pz, twz, lt3); count_launch();
+    }
     tr_end(g.tr, st, tb + 2);
     tr_begin(g.tr, st);
     // P4: inverse y, keep y < ny
-    e = launch_lines<R>(g, w.B2, w.B1, g.py, twy, true, g.My, g.ny, g.Mx, g.nz, 3, false,
-                        g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx,
-                        g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx, st);
+    if (fy) {
+      fa.in = w.B2; fa.out = w.B1; fa.tw = twy;
+      e = fast_pass<R>(g.My, FP_YINV, fa);
+    } else {
+      e = launch_lines<R>(g, w.B2, w.B1, g.py, twy, true, g.My, g.ny, g.Mx, g.nz, 3, false,
+                          g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx,
+                          g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx, st);
+    }
     if (e != cudaSuccess) return e;
     tr_end(g.tr, st, tb + 3);
     tr_begin(g.tr, st);
-    if (adjoint) {
+    // P5: inverse x, keep the occupied x, y = x - beta u
+    if (fx) {
+      fa.in = w.B1; fa.x = xr; fa.out = yr; fa.tw = twx;
+      if ((e = fast_pass<R>(g.Mx, FP_XINV, fa)) != cudaSuccess) return e;
+    } else if (adjoint) {
       k_p5<R, true><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
     } else {
       k_p5<R, false><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();

@@ -84,6 +84,55 @@ def test_matvec_multi_rhs_and_adjoint():
         assert rel_l2(y, ref) <= 1e-12
 
 
+ENGINE_CASES = [
+    ("sphere16_M32", inputs.sphere(16)),
+    ("sphere32_M64", inputs.sphere(32)),
+    ("sphere64_M128", inputs.sphere(64)),
+    ("ellipsoid64x60x33", inputs.ellipsoid(64, 60, 33)),   # x fast (128), y and z Stockham
+    ("ellipsoid70x128x100", inputs.ellipsoid(70, 128, 100)),  # y fast (256), x and z Stockham
+    ("ellipsoid20x24x128", inputs.ellipsoid(20, 24, 128)),    # z fast (256)
+    ("ellipsoid134x12x134", inputs.ellipsoid(134, 12, 134)),  # x and z fast (270)
+]
+
+
+@pytest.mark.parametrize("name,occ", ENGINE_CASES, ids=[c[0] for c in ENGINE_CASES])
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
+def test_register_engine_matches_stockham_and_oracle(name, occ, prec_name, monkeypatch):
+    """The register-resident passes (compiled lengths 32, 64, 128, 256, 270)
+    and the shared-memory Stockham passes give the same product, and both match
+    the oracle."""
+    torch, dda = need_gpu()
+    prec = dda.PREC[prec_name]
+    dt = torch.complex128 if prec == dda.DDA_FP64 else torch.complex64
+    tol = 1e-12 if prec == dda.DDA_FP64 else 1e-5
+    ys = {}
+    for engine in ("auto", "stockham"):
+        if engine == "stockham":
+            monkeypatch.setenv("DDA_FFT_ENGINE", "stockham")
+        else:
+            monkeypatch.delenv("DDA_FFT_ENGINE", raising=False)
+        p, prob = twin(occ, [1.3 + 0.02j], 0.5)
+        with p:
+            dda.dda_build_Dmatrix(p.h, prec)
+            dda.dda_set_beta(p.h, dda.DDA_CLDR, [(0.6, 0.0, 0.8)], [(0.8, 0.0, -0.6)])
+            x = inputs.random_vectors(13, 1, p.n_occ)
+            xd = torch.from_numpy(x).to("cuda", dt)
+            yd = torch.empty_like(xd)
+            dda.dda_matvec(p.h, prec, xd, yd)
+            yd2 = torch.empty_like(xd)
+            dda.dda_matvec_adjoint(p.h, prec, xd, yd2)
+            ys[engine] = (yd.cpu().numpy()[0], yd2.cpu().numpy()[0])
+    monkeypatch.delenv("DDA_FFT_ENGINE", raising=False)
+    from oracle.fft_matvec import matvec_fft
+    beta = prob.beta("cldr", (0.6, 0.0, 0.8), (0.8, 0.0, -0.6))
+    ref = matvec_fft(prob.occ, beta, prob.dmat(), x[0])
+    ref_h = matvec_fft(prob.occ, beta, prob.dmat(), x[0], conj=True)
+    for engine, (y, yh) in ys.items():
+        assert rel_l2(y, ref) <= tol, engine
+        assert rel_l2(yh, ref_h) <= tol, engine
+    assert rel_l2(ys["auto"][0], ys["stockham"][0]) <= tol
+
+
 def test_matvec_is_deterministic():
     torch, dda = need_gpu()
     occ = inputs.sphere(20)
