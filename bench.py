@@ -37,7 +37,7 @@ METRIC = "DDA matvecs/s & time-to-residual-1e-5 vs plain FP64 form on same GB300
 UNIT = "matvec/s"
 N_SPHERE, X_SIZE, M_INDEX = 134, 40.0, 1.05
 TOL = 1e-5
-INNER_TOL = 3e-3
+INNER_TOL = 5e-6
 N_ANGLES = 181
 
 

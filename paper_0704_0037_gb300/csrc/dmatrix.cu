@@ -18,9 +18,50 @@
 
 namespace dda {
 
-__global__ void k_green_fill(c128* __restrict__ grid, int mu, int nu, double kd, int nx, int ny,
-                             int nz, int Mx, int My, int Mz) {
+// G for every non-negative offset (dx, dy, dz) < (nx, ny, nz), all six
+// components from one evaluation of exp(i kappa rho): table[6][nz][ny][nx].
+__global__ void k_green_table(c128* __restrict__ table, double kd, int nx, int ny, int nz) {
+  const long long total = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % nx);
+    const long long q = i / nx;
+    const int iy = (int)(q % ny);
+    const int iz = (int)(q / ny);
+    const double d[3] = {(double)ix, (double)iy, (double)iz};
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    c128 g[6];
+    for (int c = 0; c < 6; ++c) g[c] = mk<double>(0.0, 0.0);
+    if (r2 > 0.0) {
+      const double rho = sqrt(r2);
+      const double kr = kd * rho;
+      double s, c;
+      sincos(kr, &s, &c);
+      const double inv3 = 1.0 / (r2 * rho);
+      const c128 pref = mk<double>(c * inv3, s * inv3);
+      const c128 a = mk<double>(kr * kr - 1.0, kr);
+      const c128 b = mk<double>((kr * kr - 3.0) / r2, 3.0 * kr / r2);
+      const int mu_of[6] = {0, 0, 0, 1, 1, 2}, nu_of[6] = {0, 1, 2, 1, 2, 2};
+      for (int k = 0; k < 6; ++k) {
+        const double dd = d[mu_of[k]] * d[nu_of[k]];
+        c128 t = mk<double>(-b.x * dd, -b.y * dd);
+        if (mu_of[k] == nu_of[k]) t = t + a;
+        g[k] = pref * t;
+      }
+    }
+    for (int k = 0; k < 6; ++k) table[(long long)k * total + i] = g[k];
+  }
+}
+
+// Component (mu, nu) of G on the padded grid from the table: grid index j
+// stands for offset j (j < n) or j - M (j > M - n), zero otherwise; a
+// negative offset along an axis flips the sign iff exactly one of mu, nu is
+// that axis (G_mu,nu is odd along it).
+__global__ void k_green_fill(c128* __restrict__ grid, const c128* __restrict__ table, int mu,
+                             int nu, int nx, int ny, int nz, int Mx, int My, int Mz) {
   const long long total = (long long)Mx * My * Mz;
+  const long long tsz = (long long)nx * ny * nz;
+  const int comp = mu == 0 ? nu : (mu == 1 ? 2 + nu : 5);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % Mx);
@@ -32,25 +73,15 @@ __global__ void k_green_fill(c128* __restrict__ grid, int mu, int nu, double kd,
     const bool uy = iy < ny || iy > My - ny;
     const bool uz = iz < nz || iz > Mz - nz;
     if (ux && uy && uz) {
-      double d[3];
-      d[0] = ix < nx ? (double)ix : (double)(ix - Mx);
-      d[1] = iy < ny ? (double)iy : (double)(iy - My);
-      d[2] = iz < nz ? (double)iz : (double)(iz - Mz);
-      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      if (r2 > 0.0) {
-        const double rho = sqrt(r2);
-        const double kr = kd * rho;
-        double s, c;
-        sincos(kr, &s, &c);
-        const double inv3 = 1.0 / (r2 * rho);
-        const c128 pref = mk<double>(c * inv3, s * inv3);
-        const c128 a = mk<double>(kr * kr - 1.0, kr);
-        const c128 b = mk<double>((kr * kr - 3.0) / r2, 3.0 * kr / r2);
-        const double dd = d[mu] * d[nu];
-        c128 t = mk<double>(-b.x * dd, -b.y * dd);
-        if (mu == nu) t = t + a;
-        out = pref * t;
-      }
+      const int ax = ix < nx ? ix : Mx - ix;
+      const int ay = iy < ny ? iy : My - iy;
+      const int az = iz < nz ? iz : Mz - iz;
+      const bool neg[3] = {ix >= nx, iy >= ny, iz >= nz};
+      bool flip = false;
+      for (int a = 0; a < 3; ++a)
+        if (neg[a] && ((mu == a) != (nu == a))) flip = !flip;
+      out = table[comp * tsz + ((long long)az * ny + ay) * nx + ax];
+      if (flip) out = mk<double>(-out.x, -out.y);
     }
     grid[i] = out;
   }
@@ -101,10 +132,22 @@ int dda_build_D_internal(dda_t h, bool want32) {
     }
   }
   c128* grid = nullptr;
-  if (cudaMalloc(&grid, full * sizeof(c128)) != cudaSuccess) {
+  c128* grid2 = nullptr;
+  c128* table = nullptr;
+  const long long tsz = (long long)g.nx * g.ny * g.nz;
+  const bool fast = g.engine == 0 && fast_supported(g.Mx) && fast_supported(g.My) &&
+                    fast_supported(g.Mz);
+  if (cudaMalloc(&grid, full * sizeof(c128)) != cudaSuccess ||
+      cudaMalloc(&table, 6 * tsz * sizeof(c128)) != cudaSuccess ||
+      (fast && cudaMalloc(&grid2, full * sizeof(c128)) != cudaSuccess)) {
     cudaGetLastError();
+    cudaFree(grid);
+    cudaFree(table);
     return dda_fail(h, DDA_ERR_OOM, "cannot allocate the Green's tensor grid");
   }
+  tr_begin(g.tr, st);
+  k_green_table<<<grid_for(tsz), 256, 0, st>>>(table, h->kd, g.nx, g.ny, g.nz); count_launch();
+  tr_end(g.tr, st, TR_DB_GREEN);
   const int comps[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
   const double inv = 1.0 / (double)full;
   const c128* twx = h->w64.tw;
@@ -113,34 +156,50 @@ int dda_build_D_internal(dda_t h, bool want32) {
   cudaError_t e = cudaSuccess;
   for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
     tr_begin(g.tr, st);
-    k_green_fill<<<grid_for(full), 256, 0, st>>>(grid, comps[c][0], comps[c][1], h->kd, g.nx, g.ny,
+    k_green_fill<<<grid_for(full), 256, 0, st>>>(grid, table, comps[c][0], comps[c][1], g.nx, g.ny,
                                                  g.nz, g.Mx, g.My, g.Mz); count_launch();
     tr_end(g.tr, st, TR_DB_GREEN);
     tr_begin(g.tr, st);
     // x lines (contiguous) over the whole grid; then only the octant is
     // needed, so y lines run for kx <= Mx/2 and z lines for kx <= Mx/2,
-    // ky <= My/2 (in place; the other entries are left untransformed).
+    // ky <= My/2 (the other entries are left untransformed).
     const int hx = g.Mx / 2 + 1, hy = g.My / 2 + 1;
-    e = launch_lines<double>(g, grid, grid, g.px, twx, false, g.Mx, g.Mx,
-                             g.My * g.Mz, 1, 1, true, 1, g.Mx, 0, 0, 1, g.Mx, 0, 0, st);
-    if (e != cudaSuccess) break;
-    e = launch_lines<double>(g, grid, grid, g.py, twy, false, g.My, g.My, hx, g.Mz, 1, false,
-                             g.Mx, 1, (long long)g.My * g.Mx, 0, g.Mx, 1,
-                             (long long)g.My * g.Mx, 0, st);
-    if (e != cudaSuccess) break;
-    e = launch_lines<double>(g, grid, grid, g.pz, twz, false, g.Mz, g.Mz, hx, hy, 1, false,
-                             (long long)g.My * g.Mx, 1, g.Mx, 0, (long long)g.My * g.Mx, 1, g.Mx,
-                             0, st);
-    if (e != cudaSuccess) break;
+    const c128* spec = grid;
+    if (grid2) {   // register-resident passes, grid -> grid2 -> grid -> grid2
+      FastArgs fa{};
+      fa.st = st;
+      fa.in = grid; fa.out = grid2; fa.tw = twx; fa.nrows = g.My * g.Mz;
+      if ((e = fast_pass<double>(g.Mx, FP_XFULL, fa)) != cudaSuccess) break;
+      fa.in = grid2; fa.out = grid; fa.tw = twy; fa.nrows = hx; fa.nz = g.Mz; fa.Mx = g.Mx;
+      if ((e = fast_pass<double>(g.My, FP_SFULL, fa)) != cudaSuccess) break;
+      fa.in = grid; fa.out = grid2; fa.tw = twz; fa.nrows = hy * g.Mx; fa.nz = 1;
+      fa.Mx = g.My * g.Mx;
+      if ((e = fast_pass<double>(g.Mz, FP_SFULL, fa)) != cudaSuccess) break;
+      spec = grid2;
+    } else {       // shared-memory Stockham passes, in place
+      e = launch_lines<double>(g, grid, grid, g.px, twx, false, g.Mx, g.Mx,
+                               g.My * g.Mz, 1, 1, true, 1, g.Mx, 0, 0, 1, g.Mx, 0, 0, st);
+      if (e != cudaSuccess) break;
+      e = launch_lines<double>(g, grid, grid, g.py, twy, false, g.My, g.My, hx, g.Mz, 1, false,
+                               g.Mx, 1, (long long)g.My * g.Mx, 0, g.Mx, 1,
+                               (long long)g.My * g.Mx, 0, st);
+      if (e != cudaSuccess) break;
+      e = launch_lines<double>(g, grid, grid, g.pz, twz, false, g.Mz, g.Mz, hx, hy, 1, false,
+                               (long long)g.My * g.Mx, 1, g.Mx, 0, (long long)g.My * g.Mx, 1,
+                               g.Mx, 0, st);
+      if (e != cudaSuccess) break;
+    }
     tr_end(g.tr, st, TR_DB_LINES);
     tr_begin(g.tr, st);
-    k_octant<<<grid_for(oct), 256, 0, st>>>(grid, h->w64.D + c * oct, g.Mx, g.My, g.Mz, inv); count_launch();
+    k_octant<<<grid_for(oct), 256, 0, st>>>(spec, h->w64.D + c * oct, g.Mx, g.My, g.Mz, inv); count_launch();
     tr_end(g.tr, st, TR_DB_OCTANT);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   tr_flush(g.tr);
   cudaFree(grid);
+  cudaFree(grid2);
+  cudaFree(table);
   if (e != cudaSuccess) return dda_cuda_fail(h, e, "D-matrix build");
   h->w64.have_D = true;
   if (want32) {

@@ -131,7 +131,7 @@ __device__ __forceinline__ int fold_axis(int k, int M, int& neg) {
 }
 
 template <typename R, int M1, int M2, int T>
-__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_zconv(cpx<R>* __restrict__ B2,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict__ B2,
                                                            const cpx<R>* __restrict__ D, int nz,
                                                            int Mx, int My,
                                                            const cpx<R>* __restrict__ tw) {
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_zconv(cpx<R>* __restrict__ 
     int nxs, nys;
     const int fx = fold_axis(kx, Mx, nxs);
     const int fy = fold_axis(ky, My, nys);
-#pragma unroll 2
+#pragma unroll 1
     for (int k2 = 0; k2 < M2; ++k2) {
       const int kz = k1 + M1 * k2;
       int nzs;
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_zconv(cpx<R>* __restrict__ 
 template <int M> constexpr int kLD = (M % 2 == 1) ? M : M + 1;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_xfwd(const cpx<R>* __restrict__ x,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const cpx<R>* __restrict__ x,
                                                           cpx<R>* __restrict__ B1, LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
@@ -257,14 +257,19 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_xfwd(const cpx<R>* __restri
   for (int i = threadIdx.x; i < T * LD; i += NT) a[i] = zero<R>();
   __syncthreads();
   const cpx<R>* xc = x + (long long)c * n_occ;
-  for (int t = 0; t < T; ++t) {
-    const int row = r0 + t;
-    if (row >= nrows) break;
-    const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
-    for (long long i = s0 + threadIdx.x; i < s1; i += NT) {
-      cpx<R> v = xc[i];
-      if (CONJ) v = conjg(v);
-      a[t * LD + lat.xi[i]] = beta[lat.mat[i] * 3 + c] * v;
+  {
+    // one warp per row: the dipoles of a row are contiguous in x
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int t = wid; t < T && wid < NW; t += NW) {   // a trailing partial warp idles
+      const int row = r0 + t;
+      if (row >= nrows) break;
+      const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
+      for (long long i = s0 + lane; i < s1; i += 32) {
+        cpx<R> v = xc[i];
+        if (CONJ) v = conjg(v);
+        a[t * LD + lat.xi[i]] = beta[lat.mat[i] * 3 + c] * v;
+      }
     }
   }
   __syncthreads();
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_xfwd(const cpx<R>* __restri
 // rows of B1 -> [t][LD] tile, inverse transform, y = x - beta u at the
 // occupied x; grid (ceil(nrows/T), 3)
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>) fk_xinv(const cpx<R>* __restrict__ B1,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __restrict__ B1,
                                                           const cpx<R>* __restrict__ x,
                                                           cpx<R>* __restrict__ y, LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
@@ -358,17 +363,71 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_xinv(const cpx<R>* __restri
   __syncthreads();
   const cpx<R>* xc = x + (long long)c * n_occ;
   cpx<R>* yc = y + (long long)c * n_occ;
-  for (int tt = 0; tt < T; ++tt) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int tt = wid; tt < T && wid < NW; tt += NW) {   // one warp per row; a partial warp idles
     const int row = r0 + tt;
     if (row >= nrows) break;
     const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
-    for (long long i = s0 + threadIdx.x; i < s1; i += NT) {
+    for (long long i = s0 + lane; i < s1; i += 32) {
       cpx<R> v = xc[i];
       if (CONJ) v = conjg(v);
       cpx<R> o = v - beta[lat.mat[i] * 3 + c] * a[tt * LD + lat.xi[i]];
       if (CONJ) o = conjg(o);
       yc[i] = o;
     }
+  }
+}
+
+// ---------------------------------------------------------------- full x lines
+// Whole contiguous lines of length M (no pruning): rows of in -> rows of out;
+// grid (ceil(nrows/T)).  Used by the D-matrix build.
+template <typename R, int M1, int M2, int T>
+__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfull(const cpx<R>* __restrict__ in,
+                                                           cpx<R>* __restrict__ out, long long nrows,
+                                                           const cpx<R>* __restrict__ tw) {
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* a = s_tw + M;                      // [T][LD]
+  const long long r0 = (long long)blockIdx.x * T;
+  load_tw(s_tw, tw, M, NT);
+  for (int idx = threadIdx.x; idx < T * M; idx += NT) {
+    const int tt = idx / M, m = idx - tt * M;
+    a[tt * LD + m] = r0 + tt < nrows ? in[(r0 + tt) * M + m] : zero<R>();
+  }
+  __syncthreads();
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  cpx<R>* at = a + t * LD;
+  if (q < M2) {
+    const int j = q;
+    cpx<R> v[M1];
+#pragma unroll
+    for (int i = 0; i < M1; ++i) v[i] = at[j + M2 * i];
+    cl::Dft<R, false, M1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < M1; ++k1) at[k1 * M2 + j] = v[k1];
+  }
+  __syncthreads();
+  cpx<R> u[M2];
+  if (q < M1) {
+    const int k1 = q;
+#pragma unroll
+    for (int j = 0; j < M2; ++j) u[j] = at[k1 * M2 + j];
+    cl::Dft<R, false, M2>::run(u);
+  }
+  __syncthreads();
+  if (q < M1) {
+    const int k1 = q;
+#pragma unroll
+    for (int k2 = 0; k2 < M2; ++k2) at[k1 + M1 * k2] = u[k2];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < T * M; idx += NT) {
+    const int tt = idx / M, m = idx - tt * M;
+    if (r0 + tt < nrows) out[(r0 + tt) * M + m] = a[tt * LD + m];
   }
 }
 
@@ -408,6 +467,10 @@ struct Passes {
     const size_t sm = (size_t)(M + 3 * M * T) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_zconv<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
+    // two ~106 KB blocks per SM need the largest shared-memory carveout
+    e = cudaFuncSetAttribute(fk_zconv<R, M1, M2, T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             100);
+    if (e != cudaSuccess) return e;
     fk_zconv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, My), NT, sm, st>>>(B2, D, nz, Mx, My, tw);
     count_launch();
     return cudaGetLastError();
@@ -424,6 +487,29 @@ struct Passes {
       if ((e = set_smem(fk_xfwd<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
       fk_xfwd<R, M1, M2, T, false><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw);
     }
+    count_launch();
+    return cudaGetLastError();
+  }
+  // whole contiguous lines (rows of length M)
+  static cudaError_t xfull(const cpx<R>* in, cpx<R>* out, long long nrows, const cpx<R>* tw,
+                           cudaStream_t st) {
+    const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_xfull<R, M1, M2, T>, sm);
+    if (e != cudaSuccess) return e;
+    fk_xfull<R, M1, M2, T><<<(unsigned)((nrows + T - 1) / T), NT, sm, st>>>(in, out, nrows, tw);
+    count_launch();
+    return cudaGetLastError();
+  }
+  // whole lines along a strided axis: element stride `stride`, lines 0..nlines-1
+  // adjacent in memory, n_outer groups M*stride apart (the y pass kernel with
+  // every input present)
+  static cudaError_t sfull(const cpx<R>* in, cpx<R>* out, int nlines, int n_outer, int stride,
+                           const cpx<R>* tw, cudaStream_t st) {
+    const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
+    if (e != cudaSuccess) return e;
+    fk_yfwd<R, M1, M2, T><<<dim3((nlines + T - 1) / T, n_outer, 1), NT, sm, st>>>(in, out, M, n_outer,
+                                                                                 stride, tw);
     count_launch();
     return cudaGetLastError();
   }

@@ -169,7 +169,9 @@ namespace dda {
 // Register-resident product passes for padded lengths with a compile-time
 // split M = M1 * M2 (fastfft.cuh).  fast_supported(M) tells whether a length
 // has one; fast_pass returns cudaErrorNotSupported otherwise.
-enum FastPass { FP_XFWD, FP_YFWD, FP_ZCONV, FP_YINV, FP_XINV };
+// FP_XFULL: whole contiguous lines, nrows rows.  FP_SFULL: whole strided
+// lines, nrows lines of element stride Mx in nz groups (D-matrix build).
+enum FastPass { FP_XFWD, FP_YFWD, FP_ZCONV, FP_YINV, FP_XINV, FP_XFULL, FP_SFULL };
 struct FastArgs {
   const void* in;        // pass input (B1, B2, or x for FP_XFWD)
   void* out;             // pass output (B1, B2, or y for FP_XINV); FP_ZCONV: B2 in place
