@@ -166,14 +166,25 @@ int dda_build_D_internal(dda_t h, bool want32) {
     const int hx = g.Mx / 2 + 1, hy = g.My / 2 + 1;
     const c128* spec = grid;
     if (grid2) {   // register-resident passes, grid -> grid2 -> grid -> grid2
+      // Component (mu, nu) is even or odd along y and z, and transforms along
+      // the other axes keep that: line y > My/2 is sy times line My - y.  So
+      // the x pass runs only on rows y <= My/2, z <= Mz/2, the y pass only on
+      // planes z <= Mz/2 and reads rows y <= My/2 (mirroring the rest), and
+      // the z pass reads planes z <= Mz/2.
+      const int mu = comps[c][0], nu = comps[c][1];
+      const int sy = ((mu == 1) != (nu == 1)) ? -1 : 1;
+      const int sz = ((mu == 2) != (nu == 2)) ? -1 : 1;
+      const int hz = g.Mz / 2 + 1;
       FastArgs fa{};
       fa.st = st;
-      fa.in = grid; fa.out = grid2; fa.tw = twx; fa.nrows = g.My * g.Mz;
+      fa.in = grid; fa.out = grid2; fa.tw = twx;
+      fa.nrows = hy * hz; fa.ny = hy; fa.My = g.My;
       if ((e = fast_pass<double>(g.Mx, FP_XFULL, fa)) != cudaSuccess) break;
-      fa.in = grid2; fa.out = grid; fa.tw = twy; fa.nrows = hx; fa.nz = g.Mz; fa.Mx = g.Mx;
+      fa.in = grid2; fa.out = grid; fa.tw = twy; fa.nrows = hx; fa.nz = hz; fa.Mx = g.Mx;
+      fa.msign = sy;
       if ((e = fast_pass<double>(g.My, FP_SFULL, fa)) != cudaSuccess) break;
       fa.in = grid; fa.out = grid2; fa.tw = twz; fa.nrows = hy * g.Mx; fa.nz = 1;
-      fa.Mx = g.My * g.Mx;
+      fa.Mx = g.My * g.Mx; fa.msign = sz;
       if ((e = fast_pass<double>(g.Mz, FP_SFULL, fa)) != cudaSuccess) break;
       spec = grid2;
     } else {       // shared-memory Stockham passes, in place

@@ -24,9 +24,9 @@ cudaError_t run_pass(int pass, const FastArgs& a) {
       return P::xinv((const cpx<R>*)a.in, (const cpx<R>*)a.x, (cpx<R>*)a.out, a.lat,
                      (const cpx<R>*)a.beta, a.n_occ, a.nrows, tw, a.adj, a.st);
     case FP_XFULL:
-      return P::xfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, tw, a.st);
+      return P::xfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.ny, a.My, tw, a.st);
     case FP_SFULL:
-      return P::sfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.nz, a.Mx, tw, a.st);
+      return P::sfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.nz, a.Mx, a.msign, tw, a.st);
   }
   return cudaErrorNotSupported;
 }

@@ -36,11 +36,14 @@ __device__ __forceinline__ void load_tw(cpx<R>* s_tw, const cpx<R>* __restrict__
 }
 
 // ---------------------------------------------------------------- P2: y forward
-// B1 [3][nz][ny][Mx] -> B2 [3][nz][M][Mx]; grid (ceil(Mx/T), nz, 3)
+// B1 [3][nz][ny][Mx] -> B2 [3][nz][M][Mx]; grid (ceil(Mx/T), nz, 3).
+// msign != 0 (D-matrix build, whole lines): only elements y <= M/2 are read;
+// element y > M/2 is msign times element M - y (the line has that parity).
 template <typename R, int M1, int M2, int T>
 __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restrict__ in,
                                                           cpx<R>* __restrict__ out, int ny, int nz,
-                                                          int Mx, const cpx<R>* __restrict__ tw) {
+                                                          int Mx, const cpx<R>* __restrict__ tw,
+                                                          int msign) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -54,10 +57,22 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
   if (q < M2) {
     const int j = q;
     cpx<R> v[M1];
+    if (msign == 0) {
 #pragma unroll
-    for (int i = 0; i < M1; ++i) {
-      const int y = j + M2 * i;
-      v[i] = (y < ny && kx < Mx) ? in[ib + (long long)y * Mx + kx] : zero<R>();
+      for (int i = 0; i < M1; ++i) {
+        const int y = j + M2 * i;
+        v[i] = (y < ny && kx < Mx) ? in[ib + (long long)y * Mx + kx] : zero<R>();
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < M1; ++i) {
+        const int y = j + M2 * i;
+        const bool mir = 2 * y > M;
+        const int ys = mir ? M - y : y;
+        cpx<R> w = kx < Mx ? in[ib + (long long)ys * Mx + kx] : zero<R>();
+        if (mir && msign < 0) w = mk<R>(-w.x, -w.y);
+        v[i] = w;
+      }
     }
     cl::Dft<R, false, M1>::run(v);
 #pragma unroll
@@ -180,29 +195,46 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict
 #pragma unroll
       for (int k2 = 0; k2 < M2; ++k2) sc[(k1 * M2 + k2) * T + t] = u[k2];
     }
-    // Fourier-space product with the octant of FFT(G)
+  }
+  __syncthreads();
+  {
+    // Fourier-space product with the octant of FFT(G).  Work item (t, fz):
+    // the six octant values at (fx, fy, fz) are loaded once and applied to
+    // both kz = fz and kz = M - fz (sign flips for the components odd in z);
+    // kz = k1 + M1 k2 lives in row k1*M2 + k2.
     const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
     const long long octs = (long long)hx * hy * hz;
-    int nxs, nys;
-    const int fx = fold_axis(kx, Mx, nxs);
+    int nys;
     const int fy = fold_axis(ky, My, nys);
-#pragma unroll 1
-    for (int k2 = 0; k2 < M2; ++k2) {
-      const int kz = k1 + M1 * k2;
-      int nzs;
-      const int fz = fold_axis(kz, M, nzs);
+    const int kx0 = blockIdx.x * T;
+#pragma unroll 2
+    for (int it = threadIdx.x; it < T * hz; it += NT) {
+      const int t2 = it % T, fz = it / T;
+      const int kx2 = kx0 + t2;
+      if (kx2 >= Mx) continue;
+      int nxs;
+      const int fx = fold_axis(kx2, Mx, nxs);
       const long long o = ((long long)fz * hy + fy) * hx + fx;
       const cpx<R> dxx = D[o], dyy = D[3 * octs + o], dzz = D[5 * octs + o];
       cpx<R> dxy = D[octs + o], dxz = D[2 * octs + o], dyz = D[4 * octs + o];
       if (nxs ^ nys) dxy = mk<R>(-dxy.x, -dxy.y);
-      if (nxs ^ nzs) dxz = mk<R>(-dxz.x, -dxz.y);
-      if (nys ^ nzs) dyz = mk<R>(-dyz.x, -dyz.y);
-      const int e = (k1 * M2 + k2) * T + t;
-      const cpx<R> vx = s[e], vy = s[M * T + e], vz = s[2 * M * T + e];
-      s[e] = dxx * vx + dxy * vy + dxz * vz;
-      s[M * T + e] = dxy * vx + dyy * vy + dyz * vz;
-      s[2 * M * T + e] = dxz * vx + dyz * vy + dzz * vz;
+      const int nkz = (fz == 0 || 2 * fz == M) ? 1 : 2;
+      for (int h = 0; h < nkz; ++h) {
+        const int kz = h ? M - fz : fz;
+        cpx<R> ez = dxz, fzz = dyz;
+        if (nxs ^ h) ez = mk<R>(-ez.x, -ez.y);
+        if (nys ^ h) fzz = mk<R>(-fzz.x, -fzz.y);
+        const int e = ((kz % M1) * M2 + kz / M1) * T + t2;
+        const cpx<R> vx = s[e], vy = s[M * T + e], vz = s[2 * M * T + e];
+        s[e] = dxx * vx + dxy * vy + ez * vz;
+        s[M * T + e] = dxy * vx + dyy * vy + fzz * vz;
+        s[2 * M * T + e] = ez * vx + fzz * vy + dzz * vz;
+      }
     }
+  }
+  __syncthreads();
+  if (q < M1 && kx < Mx) {
+    const int k1 = q;
     // inverse phase A of each component: M2-point inverse over k2, conjugate twiddle
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
@@ -381,10 +413,13 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
 
 // ---------------------------------------------------------------- full x lines
 // Whole contiguous lines of length M (no pruning): rows of in -> rows of out;
-// grid (ceil(nrows/T)).  Used by the D-matrix build.
+// grid (ceil(nrows/T)).  Used by the D-matrix build.  Row r of the launch is
+// memory row (r / rows_y) * plane_rows + r % rows_y, so a sub-block of rows
+// (y < rows_y in every plane) can be transformed.
 template <typename R, int M1, int M2, int T>
 __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfull(const cpx<R>* __restrict__ in,
                                                            cpx<R>* __restrict__ out, long long nrows,
+                                                           int rows_y, long long plane_rows,
                                                            const cpx<R>* __restrict__ tw) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -394,7 +429,9 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfull(const cpx<R>* __re
   load_tw(s_tw, tw, M, NT);
   for (int idx = threadIdx.x; idx < T * M; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
-    a[tt * LD + m] = r0 + tt < nrows ? in[(r0 + tt) * M + m] : zero<R>();
+    const long long r = r0 + tt;
+    const long long mr = (r / rows_y) * plane_rows + r % rows_y;
+    a[tt * LD + m] = r < nrows ? in[mr * M + m] : zero<R>();
   }
   __syncthreads();
   const int t = threadIdx.x % T, q = threadIdx.x / T;
@@ -427,7 +464,9 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfull(const cpx<R>* __re
   __syncthreads();
   for (int idx = threadIdx.x; idx < T * M; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
-    if (r0 + tt < nrows) out[(r0 + tt) * M + m] = a[tt * LD + m];
+    const long long r = r0 + tt;
+    const long long mr = (r / rows_y) * plane_rows + r % rows_y;
+    if (r < nrows) out[mr * M + m] = a[tt * LD + m];
   }
 }
 
@@ -436,7 +475,7 @@ template <typename R> constexpr int kT = sizeof(R) == 4 ? 16 : 8;
 
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return ensure_smem((const void*)kernel, bytes);
 }
 
 // Launches of one pass for a compile-time length; returns cudaErrorNotSupported
@@ -449,7 +488,8 @@ struct Passes {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
-    fk_yfwd<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3), NT, sm, st>>>(in, out, ny, nz, Mx, tw);
+    fk_yfwd<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3), NT, sm, st>>>(in, out, ny, nz, Mx, tw,
+                                                                         0);
     count_launch();
     return cudaGetLastError();
   }
@@ -468,8 +508,7 @@ struct Passes {
     cudaError_t e = set_smem(fk_zconv<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
     // two ~106 KB blocks per SM need the largest shared-memory carveout
-    e = cudaFuncSetAttribute(fk_zconv<R, M1, M2, T>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             100);
+    e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, T>);
     if (e != cudaSuccess) return e;
     fk_zconv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, My), NT, sm, st>>>(B2, D, nz, Mx, My, tw);
     count_launch();
@@ -490,26 +529,28 @@ struct Passes {
     count_launch();
     return cudaGetLastError();
   }
-  // whole contiguous lines (rows of length M)
-  static cudaError_t xfull(const cpx<R>* in, cpx<R>* out, long long nrows, const cpx<R>* tw,
-                           cudaStream_t st) {
+  // whole contiguous lines (rows of length M): rows y < rows_y of each plane
+  // of plane_rows rows, nrows rows in all
+  static cudaError_t xfull(const cpx<R>* in, cpx<R>* out, long long nrows, int rows_y,
+                           long long plane_rows, const cpx<R>* tw, cudaStream_t st) {
     const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_xfull<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
-    fk_xfull<R, M1, M2, T><<<(unsigned)((nrows + T - 1) / T), NT, sm, st>>>(in, out, nrows, tw);
+    fk_xfull<R, M1, M2, T><<<(unsigned)((nrows + T - 1) / T), NT, sm, st>>>(in, out, nrows, rows_y,
+                                                                          plane_rows, tw);
     count_launch();
     return cudaGetLastError();
   }
   // whole lines along a strided axis: element stride `stride`, lines 0..nlines-1
   // adjacent in memory, n_outer groups M*stride apart (the y pass kernel with
-  // every input present)
+  // every input present); msign != 0 reads only elements <= M/2 and mirrors
   static cudaError_t sfull(const cpx<R>* in, cpx<R>* out, int nlines, int n_outer, int stride,
-                           const cpx<R>* tw, cudaStream_t st) {
+                           int msign, const cpx<R>* tw, cudaStream_t st) {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
     fk_yfwd<R, M1, M2, T><<<dim3((nlines + T - 1) / T, n_outer, 1), NT, sm, st>>>(in, out, M, n_outer,
-                                                                                 stride, tw);
+                                                                                 stride, tw, msign);
     count_launch();
     return cudaGetLastError();
   }

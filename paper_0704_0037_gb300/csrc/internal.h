@@ -169,8 +169,9 @@ namespace dda {
 // Register-resident product passes for padded lengths with a compile-time
 // split M = M1 * M2 (fastfft.cuh).  fast_supported(M) tells whether a length
 // has one; fast_pass returns cudaErrorNotSupported otherwise.
-// FP_XFULL: whole contiguous lines, nrows rows.  FP_SFULL: whole strided
-// lines, nrows lines of element stride Mx in nz groups (D-matrix build).
+// FP_XFULL: whole contiguous lines, nrows rows: rows y < ny of planes of My
+// rows.  FP_SFULL: whole strided lines, nrows lines of element stride Mx in
+// nz groups, msign as fk_yfwd (D-matrix build).
 enum FastPass { FP_XFWD, FP_YFWD, FP_ZCONV, FP_YINV, FP_XINV, FP_XFULL, FP_SFULL };
 struct FastArgs {
   const void* in;        // pass input (B1, B2, or x for FP_XFWD)
@@ -183,6 +184,7 @@ struct FastArgs {
   long long n_occ;
   int nrows, ny, nz, Mx, My;
   bool adj;
+  int msign;
   cudaStream_t st;
 };
 bool fast_supported(int M);
@@ -190,4 +192,12 @@ template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_270(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_256(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_small(int M, int pass, const FastArgs& a);
+}  // namespace dda
+
+namespace dda {
+// Kernel attributes set once per (kernel, device) instead of before every
+// launch: the dynamic shared-memory limit (raised when a larger size is
+// needed) and the maximum shared-memory carveout.
+cudaError_t ensure_smem(const void* func, size_t bytes);
+cudaError_t ensure_carveout_max(const void* func);
 }  // namespace dda

@@ -117,10 +117,11 @@ __global__ void __launch_bounds__(kVT) k_dot(const cpx<R>* __restrict__ a, const
   if (s && s->done) return;
   double v[2] = {0.0, 0.0};
   VLOOP(n) {
-    const double ax = a[i].x, ay = HERM ? -(double)a[i].y : (double)a[i].y;
-    const double bx = b[i].x, by = b[i].y;
-    v[0] += ax * bx - ay * by;
-    v[1] += ax * by + ay * bx;
+    // each term's product in the vectors' precision, the running sum in FP64
+    const R ax = a[i].x, ay = HERM ? -a[i].y : a[i].y;
+    const R bx = b[i].x, by = b[i].y;
+    v[0] += (double)(ax * bx - ay * by);
+    v[1] += (double)(ax * by + ay * bx);
   }
   block_store<2>(v, part, slot);
 }
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ vp, const c
     a2[i] = ap;
     const cpx<R> rr = r[i] - ta * ap;
     r[i] = rr;
-    acc[0] += (double)rr.x * rr.x + (double)rr.y * rr.y;
+    acc[0] += (double)(rr.x * rr.x + rr.y * rr.y);
   }
   block_store<1>(acc, part, 0);
 }
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(kVT) k_bs_s(const cpx<R>* __restrict__ r, cons
   VLOOP(n) {
     const cpx<R> t = r[i] - al * v[i];
     sv[i] = t;
-    acc[0] += (double)t.x * t.x + (double)t.y * t.y;
+    acc[0] += (double)(t.x * t.x + t.y * t.y);
   }
   block_store<1>(acc, part, 0);
 }
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kVT) k_cg_k1(cpx<R>* __restrict__ x, cpx<R>* _
     x[i] = x[i] + al * p[i];
     const cpx<R> t = r[i] - al * w[i];
     r[i] = t;
-    acc[0] += (double)t.x * t.x + (double)t.y * t.y;
+    acc[0] += (double)(t.x * t.x + t.y * t.y);
   }
   block_store<1>(acc, part, 0);
 }
@@ -623,7 +624,6 @@ int sync_read(Run& R_) {
   dda_t h = R_.h;
   DDA_CK(h, cudaMemcpyAsync(R_.hs, R_.ds, sizeof(Scal), cudaMemcpyDeviceToHost, R_.st));
   DDA_CK(h, cudaStreamSynchronize(R_.st));
-  tr_flush(&h->tracer);
   return DDA_OK;
 }
 
@@ -901,6 +901,7 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
       LK(h);
     }
     DDA_CK(h, cudaStreamSynchronize(ru.st));
+    tr_flush(&h->tracer);
     auto t1 = std::chrono::steady_clock::now();
     inf.status = st_rhs;
     inf.iters = ru.iters;

@@ -259,7 +259,7 @@ static size_t smem_bytes(int M, size_t elem, int nbuf, int logT, int extra_col) 
 
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return ensure_smem((const void*)kernel, bytes);
 }
 
 template <typename R>

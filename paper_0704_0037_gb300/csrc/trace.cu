@@ -108,3 +108,41 @@ extern "C" int dda_trace_read(dda_t h, int max_n, char* names, double* ms, long 
   *n_out = k;
   return DDA_OK;
 }
+
+// ---------------------------------------------------------------- kernel attributes
+#include <map>
+#include <mutex>
+#include <utility>
+
+namespace dda {
+
+static std::mutex g_attr_mu;
+static std::map<std::pair<const void*, int>, size_t> g_smem;
+static std::map<std::pair<const void*, int>, bool> g_carve;
+
+cudaError_t ensure_smem(const void* func, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto key = std::make_pair(func, dev);
+  auto it = g_smem.find(key);
+  if (it != g_smem.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g_smem[key] = bytes;
+  return e;
+}
+
+cudaError_t ensure_carveout_max(const void* func) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto key = std::make_pair(func, dev);
+  if (g_carve.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) g_carve[key] = true;
+  return e;
+}
+
+}  // namespace dda
