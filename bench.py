@@ -37,7 +37,10 @@ METRIC = "DDA matvecs/s & time-to-residual-1e-5 vs plain FP64 form on same GB300
 UNIT = "matvec/s"
 N_SPHERE, X_SIZE, M_INDEX = 134, 40.0, 1.05
 TOL = 1e-5
-INNER_TOL = 5e-6
+# inner complex64 solves stop at 8e-6 of the current residual: above the
+# complex64 rounding floor of this problem (5e-6 to 7.5e-6 measured), so one
+# FP64 refinement step normally ends the solve below TOL
+INNER_TOL = 8e-6
 N_ANGLES = 181
 
 
@@ -136,10 +139,11 @@ def kernel_models(n, M, n_occ):
         out[f"p3_zconv_{suf}"] = dict(bytes=2 * b2 + oct_, flops=3 * M * M * 2 * 5 * M * lg + 66 * M ** 3)
         out[f"p4_yifft_{suf}"] = dict(bytes=b2 + b1, flops=3 * n * M * 5 * M * lg)
         out[f"p5_xifft_{suf}"] = dict(bytes=b1 + 2 * vec + idx, flops=3 * n * n * 5 * M * lg)
-    # D build: x lines over the whole grid, y lines for kx <= M/2, z lines for
-    # kx, ky <= M/2 (only the octant is kept); all three passes per component
+    # D build, register-resident passes with parity mirroring: x lines for
+    # y, z <= M/2, y lines for kx, z <= M/2, z lines for ky <= M/2 (every kx);
+    # all three passes per component
     h = M // 2 + 1
-    lines = M * M + h * M + h * h
+    lines = h * h + h * h + h * M
     out["dbuild_lines"] = dict(bytes=2 * lines * M * 16, flops=lines * 5 * M * lg)
     return out
 

@@ -386,7 +386,7 @@ extern "C" int dda_free(dda_t h) {
   free_work(h->w64);
   free_work(h->w32);
   cudaFree(h->d_row_off); cudaFree(h->d_xi); cudaFree(h->d_mat);
-  cudaFree(h->sv); cudaFree(h->d_part); cudaFree(h->d_scal); cudaFreeHost(h->h_scal);
+  cudaFree(h->sv); cudaFree(h->d_part); cudaFree(h->d_mvpart); cudaFree(h->d_scal); cudaFreeHost(h->h_scal);
   cudaFree(h->d_tab); cudaFree(h->d_fpart); cudaFree(h->d_coll);
   cudaGetLastError();
   delete h;

@@ -22,7 +22,7 @@ cudaError_t run_pass(int pass, const FastArgs& a) {
       return P::yinv((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.st);
     case FP_XINV:
       return P::xinv((const cpx<R>*)a.in, (const cpx<R>*)a.x, (cpx<R>*)a.out, a.lat,
-                     (const cpx<R>*)a.beta, a.n_occ, a.nrows, tw, a.adj, a.st);
+                     (const cpx<R>*)a.beta, a.n_occ, a.nrows, tw, a.adj, a.dotp, a.st);
     case FP_XFULL:
       return P::xfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.ny, a.My, tw, a.st);
     case FP_SFULL:

@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
                                                           cpx<R>* __restrict__ y, LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
-                                                          const cpx<R>* __restrict__ tw) {
+                                                          const cpx<R>* __restrict__ tw,
+                                                          double* __restrict__ dotp) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -397,16 +398,44 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
   cpx<R>* yc = y + (long long)c * n_occ;
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double dre = 0.0, dim = 0.0;       // partial x^T y (bilinear) when dotp is set
   for (int tt = wid; tt < T && wid < NW; tt += NW) {   // one warp per row; a partial warp idles
     const int row = r0 + tt;
     if (row >= nrows) break;
     const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
+    R fr = 0, fi = 0;
     for (long long i = s0 + lane; i < s1; i += 32) {
       cpx<R> v = xc[i];
       if (CONJ) v = conjg(v);
       cpx<R> o = v - beta[lat.mat[i] * 3 + c] * a[tt * LD + lat.xi[i]];
       if (CONJ) o = conjg(o);
       yc[i] = o;
+      const cpx<R> xv = xc[i];
+      fr += xv.x * o.x - xv.y * o.y;
+      fi += xv.x * o.y + xv.y * o.x;
+    }
+    dre += (double)fr;
+    dim += (double)fi;
+  }
+  if (dotp) {
+    // block partial of the product's input times its output, for the solver
+    // (only full warps did work; a trailing partial warp holds zeros and skips)
+    __shared__ double sd[2][NT / 32 + 1];
+    if (wid < NW) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dre += __shfl_down_sync(0xffffffffu, dre, o);
+        dim += __shfl_down_sync(0xffffffffu, dim, o);
+      }
+      if (lane == 0) { sd[0][wid] = dre; sd[1][wid] = dim; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sr = 0.0, si = 0.0;
+      for (int w = 0; w < NW; ++w) { sr += sd[0][w]; si += sd[1][w]; }
+      const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+      dotp[2 * b] = sr;
+      dotp[2 * b + 1] = si;
     }
   }
 }
@@ -556,20 +585,24 @@ struct Passes {
   }
   static cudaError_t xinv(const cpx<R>* B1, const cpx<R>* x, cpx<R>* y, const LatticeDev& lat,
                           const cpx<R>* beta, long long n_occ, int nrows, const cpx<R>* tw, bool adj,
-                          cudaStream_t st) {
+                          double* dotp, cudaStream_t st) {
     const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
     const dim3 grid((nrows + T - 1) / T, 3);
     cudaError_t e;
     if (adj) {
       if ((e = set_smem(fk_xinv<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
-      fk_xinv<R, M1, M2, T, true><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw);
+      fk_xinv<R, M1, M2, T, true><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
+                                                        dotp);
     } else {
       if ((e = set_smem(fk_xinv<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
-      fk_xinv<R, M1, M2, T, false><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw);
+      fk_xinv<R, M1, M2, T, false><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
+                                                         dotp);
     }
     count_launch();
     return cudaGetLastError();
   }
+  // number of blocks (partials written to dotp) of xinv for nrows rows
+  static int xinv_blocks(int nrows) { return 3 * ((nrows + T - 1) / T); }
 };
 
 }  // namespace fast

@@ -48,7 +48,7 @@ __host__ __device__ __forceinline__ void bfly2(cpx<R>& a, cpx<R>& b) {
 template <typename R, bool INV>
 __host__ __device__ __forceinline__ void bfly3(cpx<R>& a, cpx<R>& b, cpx<R>& c) {
   cpx<R> t = b + c;
-  cpx<R> d = a - scale<R>(t, (R)0.5);
+  cpx<R> d = fmas<R>(t, (R)-0.5, a);
   cpx<R> e = mul_mi<R, INV>(scale<R>(b - c, (R)DDA_S3));
   a = a + t;
   b = d + e;
@@ -68,10 +68,10 @@ __host__ __device__ __forceinline__ void bfly4(cpx<R>& a, cpx<R>& b, cpx<R>& c, 
 template <typename R, bool INV>
 __host__ __device__ __forceinline__ void bfly5(cpx<R>* v) {
   cpx<R> t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
-  cpx<R> a1 = v[0] + scale<R>(t1, (R)DDA_C51) + scale<R>(t2, (R)DDA_C52);
-  cpx<R> a2 = v[0] + scale<R>(t1, (R)DDA_C52) + scale<R>(t2, (R)DDA_C51);
-  cpx<R> b1 = mul_mi<R, INV>(scale<R>(t3, (R)DDA_S51) + scale<R>(t4, (R)DDA_S52));
-  cpx<R> b2 = mul_mi<R, INV>(scale<R>(t3, (R)DDA_S52) - scale<R>(t4, (R)DDA_S51));
+  cpx<R> a1 = fmas<R>(t2, (R)DDA_C52, fmas<R>(t1, (R)DDA_C51, v[0]));
+  cpx<R> a2 = fmas<R>(t2, (R)DDA_C51, fmas<R>(t1, (R)DDA_C52, v[0]));
+  cpx<R> b1 = mul_mi<R, INV>(fmas<R>(t4, (R)DDA_S52, scale<R>(t3, (R)DDA_S51)));
+  cpx<R> b2 = mul_mi<R, INV>(fmas<R>(t4, (R)(-DDA_S51), scale<R>(t3, (R)DDA_S52)));
   v[0] = v[0] + t1 + t2;
   v[1] = a1 + b1;
   v[4] = a1 - b1;
@@ -84,12 +84,12 @@ __host__ __device__ __forceinline__ void bfly7(cpx<R>* v) {
   cpx<R> t1 = v[1] + v[6], t2 = v[2] + v[5], t3 = v[3] + v[4];
   cpx<R> u1 = v[1] - v[6], u2 = v[2] - v[5], u3 = v[3] - v[4];
   cpx<R> x0 = v[0];
-  cpx<R> a1 = x0 + scale<R>(t1, (R)DDA_C71) + scale<R>(t2, (R)DDA_C72) + scale<R>(t3, (R)DDA_C73);
-  cpx<R> a2 = x0 + scale<R>(t1, (R)DDA_C72) + scale<R>(t2, (R)DDA_C73) + scale<R>(t3, (R)DDA_C71);
-  cpx<R> a3 = x0 + scale<R>(t1, (R)DDA_C73) + scale<R>(t2, (R)DDA_C71) + scale<R>(t3, (R)DDA_C72);
-  cpx<R> b1 = mul_mi<R, INV>(scale<R>(u1, (R)DDA_S71) + scale<R>(u2, (R)DDA_S72) + scale<R>(u3, (R)DDA_S73));
-  cpx<R> b2 = mul_mi<R, INV>(scale<R>(u1, (R)DDA_S72) - scale<R>(u2, (R)DDA_S73) - scale<R>(u3, (R)DDA_S71));
-  cpx<R> b3 = mul_mi<R, INV>(scale<R>(u1, (R)DDA_S73) - scale<R>(u2, (R)DDA_S71) + scale<R>(u3, (R)DDA_S72));
+  cpx<R> a1 = fmas<R>(t3, (R)DDA_C73, fmas<R>(t2, (R)DDA_C72, fmas<R>(t1, (R)DDA_C71, x0)));
+  cpx<R> a2 = fmas<R>(t3, (R)DDA_C71, fmas<R>(t2, (R)DDA_C73, fmas<R>(t1, (R)DDA_C72, x0)));
+  cpx<R> a3 = fmas<R>(t3, (R)DDA_C72, fmas<R>(t2, (R)DDA_C71, fmas<R>(t1, (R)DDA_C73, x0)));
+  cpx<R> b1 = mul_mi<R, INV>(fmas<R>(u3, (R)DDA_S73, fmas<R>(u2, (R)DDA_S72, scale<R>(u1, (R)DDA_S71))));
+  cpx<R> b2 = mul_mi<R, INV>(fmas<R>(u3, (R)(-DDA_S71), fmas<R>(u2, (R)(-DDA_S73), scale<R>(u1, (R)DDA_S72))));
+  cpx<R> b3 = mul_mi<R, INV>(fmas<R>(u3, (R)DDA_S72, fmas<R>(u2, (R)(-DDA_S71), scale<R>(u1, (R)DDA_S73))));
   v[0] = x0 + t1 + t2 + t3;
   v[1] = a1 + b1; v[6] = a1 - b1;
   v[2] = a2 + b2; v[5] = a2 - b2;

@@ -71,10 +71,12 @@ struct Work {
 };
 
 // Launch helpers (matvec.cu)
+// With dotp != null (nrhs == 1), the last pass also writes per-block partials
+// of x^T y to dotp when it can (*dot_nb = their count, else 0).
 template <typename R>
 cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, const cpx<R>* beta,
                           int n_mat, const cpx<R>* x, cpx<R>* y, int nrhs, bool adjoint,
-                          cudaStream_t st);
+                          cudaStream_t st, double* dotp = nullptr, int* dot_nb = nullptr);
 
 template <typename R>
 cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const FftPlan& p,
@@ -111,6 +113,7 @@ struct dda_ctx {
   void* sv = nullptr;             // solver vectors, grown on demand
   size_t sv_bytes = 0;
   double* d_part = nullptr;       // reduction partials
+  double* d_mvpart = nullptr;     // per-block x^T y partials of the product's last pass
   void* d_scal = nullptr;         // device scalar state
   void* h_scal = nullptr;         // pinned host mirror
   // scatter scratch
@@ -185,8 +188,11 @@ struct FastArgs {
   int nrows, ny, nz, Mx, My;
   bool adj;
   int msign;
+  double* dotp;          // FP_XINV: per-block partials of x^T y (re, im), or null
   cudaStream_t st;
 };
+// number of (re, im) partials FP_XINV writes to dotp for nrows rows
+inline int fast_xinv_blocks(int nrows, bool fp32) { return 3 * ((nrows + (fp32 ? 16 : 8) - 1) / (fp32 ? 16 : 8)); }
 bool fast_supported(int M);
 template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_270(int pass, const FastArgs& a);

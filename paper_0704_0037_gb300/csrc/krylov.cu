@@ -88,6 +88,53 @@ __device__ __forceinline__ c128 cfin(const double* part, int slot, int nb) {
   return mk<double>(re, im);
 }
 
+// K sums at once: entry (k, i) of the partials sits at p[k * ks + i * is],
+// i < nb.  One block of kVT threads; fixed order (per-thread strided sums,
+// warp shuffles, then the warps in order), the same result in every thread.
+template <int K>
+__device__ void fin_k(const double* p, long long ks, long long is, int nb, double (&out)[K]) {
+  __shared__ double sh[K][kVT / 32];
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += p[k * ks + i * is];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = warp_sum(v[k]);
+    if (lane == 0) sh[k][wid] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += sh[k][w];
+    out[k] = x;
+  }
+  __syncthreads();
+}
+
+// Running sum of FP64 products for complex128 vectors; for complex64 vectors
+// runs of 16 terms are summed in FP32 and each run is added in FP64 (the FP64
+// pipe is ~1/60 of the FP32 rate on this part).
+template <typename R> struct Acc {
+  double d = 0.0;
+  __device__ __forceinline__ void add(R v) { d += v; }
+  __device__ __forceinline__ double get() const { return d; }
+};
+template <> struct Acc<float> {
+  double d = 0.0;
+  float f = 0.0f;
+  int k = 0;
+  __device__ __forceinline__ void add(float v) {
+    f += v;
+    if (++k == 16) { d += (double)f; f = 0.0f; k = 0; }
+  }
+  __device__ __forceinline__ double get() const { return d + (double)f; }
+};
+
 __device__ __forceinline__ c128 csqrt_p(c128 z) {
   const double r = hypot(z.x, z.y);
   if (r == 0.0) return mk<double>(0.0, 0.0);
@@ -115,14 +162,14 @@ template <typename R, bool HERM>
 __global__ void __launch_bounds__(kVT) k_dot(const cpx<R>* __restrict__ a, const cpx<R>* __restrict__ b,
                                              long long n, double* part, int slot, const Scal* s) {
   if (s && s->done) return;
-  double v[2] = {0.0, 0.0};
+  Acc<R> a0, a1;
   VLOOP(n) {
-    // each term's product in the vectors' precision, the running sum in FP64
     const R ax = a[i].x, ay = HERM ? -a[i].y : a[i].y;
     const R bx = b[i].x, by = b[i].y;
-    v[0] += (double)(ax * bx - ay * by);
-    v[1] += (double)(ax * by + ay * bx);
+    a0.add(ax * bx - ay * by);
+    a1.add(ax * by + ay * bx);
   }
+  double v[2] = {a0.get(), a1.get()};
   block_store<2>(v, part, slot);
 }
 
@@ -220,10 +267,12 @@ __global__ void k_qmr_start(const cpx<R>* __restrict__ b, cpx<R>* v, cpx<R>* r, 
   }
 }
 
-__global__ void k_qmr_a(Scal* s, const double* part, int nb) {
+// alpha = v^T w from partials: entry (k, i) at part[k * ks + i * is]
+__global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is, int nb) {
   if (s->done) return;
-  const c128 a = cfin(part, 0, nb);
-  if (threadIdx.x == 0) s->alpha = a;
+  double a[2];
+  fin_k<2>(part, ks, is, nb, a);
+  if (threadIdx.x == 0) s->alpha = mk<double>(a[0], a[1]);
 }
 
 // vt = w - alpha v - beta_k vprev  (into vprev); partials of vt^T vt and |vt|^2
@@ -233,15 +282,16 @@ __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ w, co
                                                 double* part) {
   if (s->done) return;
   const cpx<R> al = cs<R>(s->alpha), bk = cs<R>(s->beta_k);
-  double acc[3] = {0.0, 0.0, 0.0};
+  Acc<R> q0, q1, q2;
   VLOOP(n) {
     const cpx<R> t = w[i] - al * v[i] - bk * vp[i];
     vp[i] = t;
-    const double x = t.x, y = t.y;
-    acc[0] += x * x - y * y;
-    acc[1] += 2.0 * x * y;
-    acc[2] += x * x + y * y;
+    const R x = t.x, y = t.y;
+    q0.add(x * x - y * y);
+    q1.add((R)2 * x * y);
+    q2.add(x * x + y * y);
   }
+  double acc[3] = {q0.get(), q1.get(), q2.get()};
   block_store<3>(acc, part, 0);
 }
 
@@ -250,8 +300,10 @@ __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ w, co
 // rotation, and the coefficients of the p / x / Ap / r updates.
 __global__ void k_qmr_b(Scal* s, const double* part, int nb) {
   if (s->done) return;
-  const c128 vtv = cfin(part, 0, nb);
-  const double vn2 = fin(part, 2, nb);
+  double f[3];
+  fin_k<3>(part, kNB, 1, nb, f);
+  const c128 vtv = mk<double>(f[0], f[1]);
+  const double vn2 = f[2];
   if (threadIdx.x) return;
   const c128 bn = csqrt_p(vtv);
   const c128 bk = s->beta_k, al = s->alpha;
@@ -294,7 +346,7 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ vp, const c
   if (s->done) return;
   const cpx<R> ib = cs<R>(s->inv_beta), ig = cs<R>(s->inv_gamma);
   const cpx<R> de = cs<R>(s->delta), ep = cs<R>(s->eps), ta = cs<R>(s->tau);
-  double acc[1] = {0.0};
+  Acc<R> q;
   VLOOP(n) {
     vp[i] = vp[i] * ib;
     const cpx<R> p = (v[i] - de * p1[i] - ep * p2[i]) * ig;
@@ -304,14 +356,17 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ vp, const c
     a2[i] = ap;
     const cpx<R> rr = r[i] - ta * ap;
     r[i] = rr;
-    acc[0] += (double)(rr.x * rr.x + rr.y * rr.y);
+    q.add(rr.x * rr.x + rr.y * rr.y);
   }
+  double acc[1] = {q.get()};
   block_store<1>(acc, part, 0);
 }
 
 __global__ void k_qmr_c(Scal* s, const double* part, int nb) {
   if (s->done) return;
-  const double rn2 = fin(part, 0, nb);
+  double f[1];
+  fin_k<1>(part, kNB, 1, nb, f);
+  const double rn2 = f[0];
   if (threadIdx.x) return;
   const double res = sqrt(rn2) / s->bnorm;
   s->res = res;
@@ -618,6 +673,12 @@ struct Run {
   int matvecs = 0, matvecs64 = 0, iters = 0;
   std::vector<double>* hist = nullptr;
   double hist_scale = 1.0;
+  // Inner complex64 solves stop when their residual, already below 1e-4,
+  // has not improved by 1 % in stall_window iterations (the complex64
+  // rounding floor); the FP64 refinement then continues.  0 = off.
+  int stall_window = 0;
+  double best = 1e300;
+  int best_k = 0;
 };
 
 int sync_read(Run& R_) {
@@ -632,11 +693,12 @@ template <> Work<double>& work<double>(dda_t h) { return h->w64; }
 template <> Work<float>& work<float>(dda_t h) { return h->w32; }
 
 template <typename R>
-int matvec(Run& ru, const cpx<R>* x, cpx<R>* y, bool adj) {
+int matvec(Run& ru, const cpx<R>* x, cpx<R>* y, bool adj, double* dotp = nullptr,
+           int* dot_nb = nullptr) {
   dda_t h = ru.h;
   Work<R>& w = work<R>(h);
   cudaError_t e = launch_matvec<R>(h->g, h->lat(), w, w.beta + (long long)ru.rhs * h->n_mat * 3,
-                                   h->n_mat, x, y, 1, adj, ru.st);
+                                   h->n_mat, x, y, 1, adj, ru.st, dotp, dot_nb);
   if (e != cudaSuccess) return dda_cuda_fail(h, e, "matvec in solver");
   ru.matvecs++;
   if (sizeof(R) == 8) ru.matvecs64++;
@@ -656,8 +718,17 @@ int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, do
   cudaStream_t st = ru.st;
   double* part = ru.part;
   Scal* s = ru.ds;
+  ru.best = 1e300;
+  ru.best_k = ru.iters;
   auto rec = [&](void) {
-    if (ru.hist) ru.hist->push_back(ru.hs->res * ru.hist_scale);
+    const double r = ru.hs->res;
+    if (ru.hist) ru.hist->push_back(r * ru.hist_scale);
+    if (r < 0.99 * ru.best) {
+      ru.best = r;
+      ru.best_k = ru.iters;
+    } else if (ru.stall_window > 0 && r < 1e-4 && ru.iters - ru.best_k >= ru.stall_window) {
+      ru.hs->done = 1;   // host copy only: ends this loop, status stays NOT_CONVERGED
+    }
   };
   k_norms<R><<<nb, kVT, 0, st>>>(b, n, part, nullptr); count_launch();
   if (solver == DDA_QMR_CS) {
@@ -668,9 +739,15 @@ int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, do
     LK(h);
     RK(sync_read(ru));
     for (int k = 1; k <= maxiter && !ru.hs->done; ++k) {
-      RK(matvec<R>(ru, v, w, false));
-      k_dot<R, false><<<nb, kVT, 0, st>>>(v, w, n, part, 0, s); count_launch();
-      k_qmr_a<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      // w = A v; alpha = v^T w, from the product's last pass when it can
+      int dnb = 0;
+      RK(matvec<R>(ru, v, w, false, h->d_mvpart, &dnb));
+      if (dnb > 0) {
+        k_qmr_a<<<1, kVT, 0, st>>>(s, h->d_mvpart, 1, 2, dnb); count_launch();
+      } else {
+        k_dot<R, false><<<nb, kVT, 0, st>>>(v, w, n, part, 0, s); count_launch();
+        k_qmr_a<<<1, kVT, 0, st>>>(s, part, kNB, 1, nb); count_launch();
+      }
       k_qmr_k1<R><<<nb, kVT, 0, st>>>(w, v, vp, n, s, part); count_launch();
       k_qmr_b<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
       k_qmr_k2<R><<<nb, kVT, 0, st>>>(vp, v, w, p1, p2, a1, a2, x, r, n, s, part); count_launch();
@@ -764,6 +841,8 @@ int ensure_solver_mem(dda_t h, size_t bytes) {
   if (!h->d_part) {
     if (cudaMalloc(&h->d_part, kSlots * kNB * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver partials"); }
     if (cudaMalloc(&h->d_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver scalars"); }
+    const size_t mvp = 2 * (size_t)fast_xinv_blocks(h->g.nrows, false);
+    if (cudaMalloc(&h->d_mvpart, mvp * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "product partials"); }
     if (cudaMallocHost(&h->h_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "pinned scalars"); }
   }
   if (h->sv_bytes < bytes) {
@@ -878,7 +957,9 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
         LK(h);
         ru.hist_scale = rn / bn;
         const int it0 = ru.iters;
+        ru.stall_window = 10;
         RK(run_solver<float>(ru, o->solver, b32, x32, vec, target, left));
+        ru.stall_window = 0;
         const int inner_status = ru.hs->status;
         left -= ru.iters - it0;
         outer++;

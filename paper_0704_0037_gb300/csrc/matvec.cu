@@ -291,7 +291,8 @@ cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const Fft
 template <typename R>
 cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, const cpx<R>* beta,
                           int n_mat, const cpx<R>* x, cpx<R>* y, int nrhs, bool adjoint,
-                          cudaStream_t st) {
+                          cudaStream_t st, double* dotp, int* dot_nb) {
+  if (dot_nb) *dot_nb = 0;
   const int logTmax = sizeof(R) == 4 ? 4 : 3;
   const size_t el = sizeof(cpx<R>);
   const cpx<R>* twx = w.tw;
@@ -371,6 +372,10 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
     // P5: inverse x, keep the occupied x, y = x - beta u
     if (fx) {
       fa.in = w.B1; fa.x = xr; fa.out = yr; fa.tw = twx;
+      if (dotp && nrhs == 1 && dot_nb) {
+        fa.dotp = dotp;
+        *dot_nb = fast_xinv_blocks(g.nrows, sizeof(R) == 4);
+      }
       if ((e = fast_pass<R>(g.Mx, FP_XINV, fa)) != cudaSuccess) return e;
     } else if (adjoint) {
       k_p5<R, true><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
@@ -384,10 +389,10 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
 
 template cudaError_t launch_matvec<float>(const Geom&, const LatticeDev&, Work<float>&,
                                           const c64*, int, const c64*, c64*, int, bool,
-                                          cudaStream_t);
+                                          cudaStream_t, double*, int*);
 template cudaError_t launch_matvec<double>(const Geom&, const LatticeDev&, Work<double>&,
                                            const c128*, int, const c128*, c128*, int, bool,
-                                           cudaStream_t);
+                                           cudaStream_t, double*, int*);
 template cudaError_t launch_lines<double>(const Geom&, const c128*, c128*, const FftPlan&,
                                           const c128*, bool, int, int, int, int, int, bool,
                                           long long, long long, long long, long long, long long,

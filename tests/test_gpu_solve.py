@@ -60,6 +60,19 @@ def test_fp32_refined_reaches_fp64_tolerance(sphere16, solver):
     assert rel_l2(P.cpu().numpy(), exact) < 1e-7
 
 
+def test_fp32_inner_floor_is_left_to_refinement(sphere16):
+    """An inner tolerance below the complex64 rounding floor: the inner
+    solves stop on stagnation and the FP64 refinement still reaches tol."""
+    p, prob, exact = sphere16
+    st, info, P, _ = _solve(p, "qmr_cs", "fp32_refined", 1e-9, maxiter=3000, inner_tol=1e-11)
+    assert st == 0, info
+    for r in range(2):
+        assert info[r]["rel_res_true"] < 1e-9
+        assert info[r]["outer"] >= 2
+        assert info[r]["iters"] < 1000
+    assert rel_l2(P.cpu().numpy(), exact) < 1e-7
+
+
 def test_qmr_history_matches_oracle(sphere16):
     """Same algorithm, same arithmetic (FP64): the residual histories agree."""
     p, prob, _ = sphere16
