@@ -6,8 +6,9 @@ conjugation); the stopping rule is the relative residual norm
 ||b - A x||_2 / ||b||_2 < eps with eps = 1e-5 by default (Sec. 2, Sec. 3.1).
 The algorithms are restated from the standard literature as mathematics:
 
-* QMR-CS: Lanczos with the bilinear form, Givens rotations on the tridiagonal
-  matrix, residual kept by r_k = r_{k-1} - tau_k A p_k (no extra product);
+* QMR-CS: Lanczos with the bilinear form and unit-norm Lanczos vectors,
+  quasi-minimal residual iterates, coupled two-term recurrences, residual kept
+  by r_i = r_{i-1} - s_i with s_i built from A p_i (no extra product);
 * Bi-CG-CS (COCG): conjugate gradients with u^T v in place of u^H v;
 * Bi-CGSTAB: van der Vorst's method with Hermitian products, shadow r0;
 * CGNR: CG on A^H A x = A^H b, with A^H y = conj(A conj(y)).
@@ -43,63 +44,70 @@ def _finish(matvec, b, x, status, iters, nmv, hist):
 
 
 def qmr_cs(matvec, b, tol=1e-5, maxiter=10000):
-    """QMR for complex-symmetric A (Lanczos with the bilinear form)."""
+    """QMR for complex-symmetric A (Freund's QMR with the bilinear form).
+
+    Lanczos vectors v_i are scaled to unit Euclidean norm, delta_i = v_i^T v_i
+    carries the bilinear normalisation, and the iteration runs on coupled
+    two-term recurrences (Freund and Nachtigal's implementation of QMR without
+    look-ahead; for A = A^T the left and right Lanczos sequences coincide, so
+    one product per step):
+        p_i = v_i - (rho_i delta_i / eps_{i-1}) p_{i-1},   pt = A p_i,
+        eps_i = p_i^T pt,  beta_i = eps_i / delta_i,  vt = pt - beta_i v_i,
+        rho_{i+1} = ||vt||,  theta_i = rho_{i+1} / (g_{i-1} |beta_i|),
+        g_i = 1 / sqrt(1 + theta_i^2),
+        eta_i = -eta_{i-1} rho_i g_i^2 / (beta_i g_{i-1}^2),
+        d_i = eta_i p_i + (theta_{i-1} g_i)^2 d_{i-1},
+        s_i = eta_i pt + (theta_{i-1} g_i)^2 s_{i-1},
+        x_i = x_{i-1} + d_i,  r_i = r_{i-1} - s_i.
+    The iterate minimises ||rho_1 e_1 - H z|| over the Krylov space, H the
+    (i+1) x i Lanczos matrix in the unit-norm basis (the quasi-minimal
+    residual property).  delta_i = 0, eps_i = 0 or beta_i = 0 is a breakdown
+    (no look-ahead)."""
     bn = norm2(b)
     x = np.zeros_like(b)
     r = b.copy()
-    beta_k = 0.0 + 0.0j                  # beta_1 multiplies v_0 = 0
-    beta_next = np.sqrt(complex(dotu(b, b)))
-    v_prev = np.zeros_like(b)
-    v = b / beta_next
-    p1 = np.zeros_like(b); p2 = np.zeros_like(b)
-    ap1 = np.zeros_like(b); ap2 = np.zeros_like(b)
-    c1, s1 = 1.0, 0.0j                   # G_{k-1}
-    c2, s2 = 1.0, 0.0j                   # G_{k-2}
-    t = beta_next
+    vt = b.copy()
+    rho = bn
+    g_prev, eta_prev, theta_prev, eps_prev = 1.0, -1.0 + 0.0j, 0.0, 1.0 + 0.0j
+    p = np.zeros_like(b)
+    d = np.zeros_like(b)
+    s = np.zeros_like(b)
     hist = [1.0]
     nmv = 0
     status = NOT_CONVERGED
     k = 0
     for k in range(1, maxiter + 1):
-        w = matvec(v); nmv += 1
-        alpha = dotu(v, w)
-        vt = w - alpha * v - beta_k * v_prev
-        vtv = dotu(vt, vt)
-        beta_next = np.sqrt(complex(vtv))
-        # previous rotations applied to column (beta_k, alpha_k, beta_{k+1})
-        eps = s2 * beta_k
-        tmp = c2 * beta_k
-        delta = c1 * tmp + s1 * alpha
-        gt = -np.conj(s1) * tmp + c1 * alpha
-        if gt == 0:
-            c, s = 0.0, 1.0 + 0.0j
-        else:
-            c = abs(gt) / np.sqrt(abs(gt) ** 2 + abs(beta_next) ** 2)
-            s = c * np.conj(beta_next / gt)
-        gamma = c * gt + s * beta_next
-        if gamma == 0:
+        v = vt / rho
+        delta = dotu(v, v)
+        if abs(delta) < 1e-30:
             status = BREAKDOWN
-            hist.append(hist[-1])
             break
-        tau = c * t
-        t = -np.conj(s) * t
-        p = (v - delta * p1 - eps * p2) / gamma
-        ap = (w - delta * ap1 - eps * ap2) / gamma
-        x = x + tau * p
-        r = r - tau * ap
-        p2, p1 = p1, p
-        ap2, ap1 = ap1, ap
-        c2, s2, c1, s1 = c1, s1, c, s
+        p = v if k == 1 else v - (rho * delta / eps_prev) * p
+        pt = matvec(p); nmv += 1
+        eps = dotu(p, pt)
+        beta = eps / delta
+        if eps == 0 or beta == 0:
+            status = BREAKDOWN
+            break
+        vt = pt - beta * v
+        rho_next = norm2(vt)
+        theta = rho_next / (g_prev * abs(beta))
+        g = 1.0 / np.sqrt(1.0 + theta * theta)
+        eta = -eta_prev * rho * g * g / (beta * g_prev * g_prev)
+        c = (theta_prev * g) ** 2
+        d = eta * p + c * d
+        s = eta * pt + c * s
+        x = x + d
+        r = r - s
         res = norm2(r) / bn
         hist.append(res)
         if res < tol:
             status = OK
             break
-        if abs(vtv) < 1e-30 * norm2(vt) ** 2:
-            status = BREAKDOWN
+        if rho_next == 0:            # invariant subspace: the update above is exact
+            status = OK if res < tol else BREAKDOWN
             break
-        v_prev, v = v, vt / beta_next
-        beta_k = beta_next
+        rho, g_prev, eta_prev, theta_prev, eps_prev = rho_next, g, eta, theta, eps
     x, info = _finish(matvec, b, x, status, k, nmv, hist)
     if info["status"] == OK and info["rel_res_true"] >= tol:
         info["status"] = NOT_CONVERGED

@@ -53,6 +53,36 @@ def matvec_bruteforce(pos, beta, kd, x, chunk=512):
     return x - beta * out
 
 
+def matvec_rows(pos, beta, kd, x, rows, chunk=1 << 21):
+    """O6 for selected outputs: (A x)_i = x_i - beta_i sum_j G(r_i - r_j) beta_j x_j
+    (Eq. 3) for the dipoles i in `rows` only, by the direct sum over all j in
+    chunks.  G u is applied as exp(i kappa rho)/rho^3 [(kappa^2 rho^2 - 1 +
+    i kappa rho) u - (kappa^2 rho^2 - 3 + 3 i kappa rho) d (d.u)/rho^2] (O4), so
+    no 3x3 tensors are formed and large lattices fit.  Returns (3, len(rows))."""
+    n = pos.shape[0]
+    u = beta * x
+    out = np.zeros((3, len(rows)), dtype=np.complex128)
+    for k, i in enumerate(rows):
+        acc = np.zeros(3, dtype=np.complex128)
+        for s in range(0, n, chunk):
+            e = min(n, s + chunk)
+            d = pos[i][None, :] - pos[s:e]                # (c, 3)
+            rho2 = np.sum(d * d, axis=1)
+            zero = rho2 == 0.0
+            rho2s = np.where(zero, 1.0, rho2)
+            rho = np.sqrt(rho2s)
+            kr = kd * rho
+            pref = np.exp(1j * kr) / (rho2s * rho)
+            pref[zero] = 0.0                              # G(0) = 0
+            ca = (kr * kr - 1.0 + 1j * kr) * pref
+            cb = (kr * kr - 3.0 + 3j * kr) / rho2s * pref
+            uc = u[:, s:e]
+            du = np.sum(d.T * uc, axis=0)                 # d . u_j
+            acc += uc @ ca - (d.T * (cb * du)[None, :]).sum(axis=1)
+        out[:, k] = x[:, i] - beta[:, i] * acc
+    return out
+
+
 def solve_dense(pos, beta, kd, b):
     """Exact solution of Eq. (3) by LU (numpy.linalg.solve); returns (3, N)."""
     a = dense_matrix(pos, beta, kd)

@@ -27,6 +27,12 @@ constexpr int kNB = 1024;     // max blocks of a vector kernel (partials per slo
 constexpr int kSlots = 8;     // doubles per block in the partials array
 constexpr int kVT = 256;      // threads of vector kernels
 
+// QMR-CS scalars (see the QMR-CS section)
+struct QmrScal {
+  double rho, inv_rho, g, theta, cd;
+  c128 delta, eps, eps_new, beta, eta, cp;
+};
+
 struct Scal {
   double bnorm, res, sres, tol;
   int done, status, half, pad;
@@ -34,6 +40,7 @@ struct Scal {
   double c1, c2;
   c128 rho, rho_prev, omega, bstep;
   double zz, ww;
+  QmrScal q;
 };
 
 // ---------------------------------------------------------------- reductions
@@ -235,57 +242,84 @@ __global__ void k_pfinal(const cpx<R>* __restrict__ x, c128* __restrict__ P, con
 }
 
 // ---------------------------------------------------------------- QMR-CS
+// Freund's QMR for A = A^T without look-ahead, on coupled two-term
+// recurrences (Freund and Nachtigal's implementation; the left and right
+// Lanczos sequences coincide, one product per step).  Lanczos vectors have
+// unit Euclidean norm; delta_i = v_i^T v_i carries the bilinear form.
+//   p_i = v_i - cp p_{i-1},  cp = rho_i delta_i / eps_{i-1};   pt = A p_i
+//   eps_i = p_i^T pt,  beta_i = eps_i / delta_i,  vt = pt - beta_i v_i
+//   rho_{i+1} = ||vt||,  theta_i = rho_{i+1} / (g_{i-1} |beta_i|),
+//   g_i = 1/sqrt(1 + theta_i^2),  eta_i = -eta_{i-1} rho_i g_i^2 / (beta_i g_{i-1}^2)
+//   d = eta_i p_i + (theta_{i-1} g_i)^2 d,  s = eta_i pt + (theta_{i-1} g_i)^2 s
+//   x += d,  r -= s
+// The three-term, bilinear-scaled form of the same Lanczos process loses its
+// convergence rate in complex64 for large size parameters; this form tracks
+// the FP64 iteration.  Scalars live in QmrScal (FP64), vectors in R.
+
+// part: slots 0/1 = b^T b, slot 2 = |b|^2 (k_norms)
 __global__ void k_qmr_init(Scal* s, const double* part, int nb, double tol) {
   const c128 bb = cfin(part, 0, nb);
   const double bn2 = fin(part, 2, nb);
   if (threadIdx.x) return;
+  QmrScal& q = s->q;
   s->tol = tol;
   s->bnorm = sqrt(bn2);
   s->res = 1.0;
   s->done = 0; s->half = 0;
   s->status = DDA_NOT_CONVERGED;
-  const c128 beta1 = csqrt_p(bb);
-  s->t = beta1;
-  s->beta_k = mk<double>(0.0, 0.0);
-  s->inv_beta = cabs2(beta1) > 0 ? cdivd(mk<double>(1.0, 0.0), beta1) : mk<double>(0.0, 0.0);
-  s->c1 = s->c2 = 1.0;
-  s->s1 = s->s2 = mk<double>(0.0, 0.0);
+  q.rho = s->bnorm;
+  q.inv_rho = bn2 > 0.0 ? 1.0 / q.rho : 0.0;
+  q.delta = bn2 > 0.0 ? scale<double>(bb, 1.0 / bn2) : mk<double>(0.0, 0.0);
+  q.g = 1.0; q.theta = 0.0; q.cd = 0.0;
+  q.eta = mk<double>(-1.0, 0.0);
+  q.eps = mk<double>(1.0, 0.0);
+  q.cp = mk<double>(0.0, 0.0);
+  q.beta = mk<double>(0.0, 0.0);
   if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
   else if (!isfinite(bn2) || !cfinite(bb)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
-  else if (cabs2(bb) == 0.0) { s->done = 1; s->status = DDA_BREAKDOWN; }
+  else if (sqrt(cabs2(q.delta)) < 1e-30) { s->done = 1; s->status = DDA_BREAKDOWN; }
 }
 
+// v_1 = b / rho_1, p_1 = v_1, r = b, x = d = s = 0
 template <typename R>
-__global__ void k_qmr_start(const cpx<R>* __restrict__ b, cpx<R>* v, cpx<R>* r, cpx<R>* x,
-                            cpx<R>* vp, cpx<R>* p1, cpx<R>* p2, cpx<R>* a1, cpx<R>* a2, long long n,
+__global__ void k_qmr_start(const cpx<R>* __restrict__ b, cpx<R>* __restrict__ v,
+                            cpx<R>* __restrict__ p, cpx<R>* __restrict__ r, cpx<R>* __restrict__ x,
+                            cpx<R>* __restrict__ d, cpx<R>* __restrict__ sv, long long n,
                             const Scal* s) {
-  const cpx<R> ib = cs<R>(s->inv_beta);
+  const R ir = (R)s->q.inv_rho;
   const cpx<R> z = mk<R>(0, 0);
   VLOOP(n) {
     const cpx<R> bi = b[i];
-    v[i] = bi * ib; r[i] = bi; x[i] = z; vp[i] = z; p1[i] = z; p2[i] = z; a1[i] = z; a2[i] = z;
+    const cpx<R> vi = scale<R>(bi, ir);
+    v[i] = vi; p[i] = vi; r[i] = bi; x[i] = z; d[i] = z; sv[i] = z;
   }
 }
 
-// alpha = v^T w from partials: entry (k, i) at part[k * ks + i * is]
+// eps_i = p^T A p from partials (entry (k, i) at part[k * ks + i * is]); beta_i
 __global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is, int nb) {
   if (s->done) return;
   double a[2];
   fin_k<2>(part, ks, is, nb, a);
-  if (threadIdx.x == 0) s->alpha = mk<double>(a[0], a[1]);
+  if (threadIdx.x) return;
+  QmrScal& q = s->q;
+  const c128 eps = mk<double>(a[0], a[1]);
+  const c128 beta = cdivd(eps, q.delta);
+  if (!cfinite(eps) || !cfinite(beta)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
+  if (cabs2(eps) == 0.0 || cabs2(beta) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  q.eps_new = eps;
+  q.beta = beta;
 }
 
-// vt = w - alpha v - beta_k vprev  (into vprev); partials of vt^T vt and |vt|^2
+// vt = pt - beta v (into v); partials of vt^T vt and |vt|^2
 template <typename R>
-__global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ w, const cpx<R>* __restrict__ v,
-                                                cpx<R>* __restrict__ vp, long long n, const Scal* s,
-                                                double* part) {
+__global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, cpx<R>* __restrict__ v,
+                                                long long n, const Scal* s, double* part) {
   if (s->done) return;
-  const cpx<R> al = cs<R>(s->alpha), bk = cs<R>(s->beta_k);
+  const cpx<R> be = cs<R>(s->q.beta);
   Acc<R> q0, q1, q2;
   VLOOP(n) {
-    const cpx<R> t = w[i] - al * v[i] - bk * vp[i];
-    vp[i] = t;
+    const cpx<R> t = pt[i] - be * v[i];
+    v[i] = t;
     const R x = t.x, y = t.y;
     q0.add(x * x - y * y);
     q1.add((R)2 * x * y);
@@ -295,71 +329,71 @@ __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ w, co
   block_store<3>(acc, part, 0);
 }
 
-// Lanczos coefficient beta_{k+1}, the two previous Givens rotations applied to
-// column (beta_k, alpha_k, beta_{k+1}) of the tridiagonal matrix, the new
-// rotation, and the coefficients of the p / x / Ap / r updates.
+// rho_{i+1}, delta_{i+1}, the quasi-minimisation scalars of step i and the
+// coefficients of the update and of the next direction
 __global__ void k_qmr_b(Scal* s, const double* part, int nb) {
   if (s->done) return;
   double f[3];
   fin_k<3>(part, kNB, 1, nb, f);
-  const c128 vtv = mk<double>(f[0], f[1]);
-  const double vn2 = f[2];
   if (threadIdx.x) return;
-  const c128 bn = csqrt_p(vtv);
-  const c128 bk = s->beta_k, al = s->alpha;
-  const c128 eps = s->s2 * bk;
-  const c128 tmp = scale<double>(bk, s->c2);
-  const c128 delta = scale<double>(tmp, s->c1) + s->s1 * al;
-  const c128 gt = scale<double>(al, s->c1) - conjg(s->s1) * tmp;
-  double c;
-  c128 sn;
-  const double ag = sqrt(cabs2(gt));
-  if (ag == 0.0) { c = 0.0; sn = mk<double>(1.0, 0.0); }
-  else {
-    c = ag / sqrt(cabs2(gt) + cabs2(bn));
-    sn = scale<double>(conjg(cdivd(bn, gt)), c);
+  QmrScal& q = s->q;
+  const c128 vtv = mk<double>(f[0], f[1]);
+  const double rho_n = sqrt(f[2]);
+  const double theta = rho_n / (q.g * sqrt(cabs2(q.beta)));
+  const double g = 1.0 / sqrt(1.0 + theta * theta);
+  const c128 eta = scale<double>(cdivd(q.eta, q.beta), -q.rho * g * g / (q.g * q.g));
+  if (!isfinite(rho_n) || !cfinite(vtv) || !isfinite(theta) || !cfinite(eta)) {
+    s->status = DDA_ERR_NONFINITE; s->done = 1; return;
   }
-  const c128 gamma = scale<double>(gt, c) + sn * bn;
-  if (!cfinite(gamma) || !cfinite(vtv) || !isfinite(vn2)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
-  if (cabs2(gamma) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
-  s->tau = scale<double>(s->t, c);
-  s->t = mk<double>(0.0, 0.0) - conjg(sn) * s->t;
-  s->inv_gamma = cdivd(mk<double>(1.0, 0.0), gamma);
-  s->delta = delta;
-  s->eps = eps;
-  s->c2 = s->c1; s->s2 = s->s1;
-  s->c1 = c; s->s1 = sn;
-  s->beta_next = bn;
-  s->inv_beta = cabs2(bn) > 0.0 ? cdivd(mk<double>(1.0, 0.0), bn) : mk<double>(0.0, 0.0);
-  s->half = (sqrt(cabs2(vtv)) < 1e-30 * vn2) ? 1 : 0;
+  q.cd = (q.theta * g) * (q.theta * g);
+  q.eta = eta;
+  q.g = g;
+  q.theta = theta;
+  s->half = 0;
+  if (rho_n == 0.0) {            // invariant subspace: this step's update is exact
+    q.inv_rho = 0.0;
+    q.cp = mk<double>(0.0, 0.0);
+    s->half = 2;
+  } else {
+    const c128 delta = scale<double>(vtv, 1.0 / (rho_n * rho_n));
+    q.inv_rho = 1.0 / rho_n;
+    q.cp = scale<double>(cdivd(delta, q.eps_new), rho_n);
+    q.delta = delta;
+    if (sqrt(cabs2(delta)) < 1e-30) s->half = 1;   // next v^T v vanishes: breakdown after this step
+  }
+  q.rho = rho_n;
+  q.eps = q.eps_new;
 }
 
-// v_{k+1} = vt / beta_{k+1}; p_k = (v_k - delta p_{k-1} - eps p_{k-2}) / gamma;
-// x += tau p_k; Ap_k likewise from w; r -= tau Ap_k; partial |r|^2.
+// d = eta p + cd d;  s = eta pt + cd s;  x += d;  r -= s (partial |r|^2);
+// then v_{i+1} = vt / rho_{i+1} and p_{i+1} = v_{i+1} - cp p_i
 template <typename R>
-__global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ vp, const cpx<R>* __restrict__ v,
-                                                const cpx<R>* __restrict__ w, const cpx<R>* __restrict__ p1,
-                                                cpx<R>* __restrict__ p2, const cpx<R>* __restrict__ a1,
-                                                cpx<R>* __restrict__ a2, cpx<R>* __restrict__ x,
+__global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* __restrict__ p,
+                                                const cpx<R>* __restrict__ pt, cpx<R>* __restrict__ d,
+                                                cpx<R>* __restrict__ sv, cpx<R>* __restrict__ x,
                                                 cpx<R>* __restrict__ r, long long n, const Scal* s,
                                                 double* part) {
   if (s->done) return;
-  const cpx<R> ib = cs<R>(s->inv_beta), ig = cs<R>(s->inv_gamma);
-  const cpx<R> de = cs<R>(s->delta), ep = cs<R>(s->eps), ta = cs<R>(s->tau);
-  Acc<R> q;
+  const QmrScal& q = s->q;
+  const cpx<R> et = cs<R>(q.eta), cp = cs<R>(q.cp);
+  const R cd = (R)q.cd, ir = (R)q.inv_rho;
+  Acc<R> acc;
   VLOOP(n) {
-    vp[i] = vp[i] * ib;
-    const cpx<R> p = (v[i] - de * p1[i] - ep * p2[i]) * ig;
-    p2[i] = p;
-    x[i] = x[i] + ta * p;
-    const cpx<R> ap = (w[i] - de * a1[i] - ep * a2[i]) * ig;
-    a2[i] = ap;
-    const cpx<R> rr = r[i] - ta * ap;
+    const cpx<R> pi = p[i];
+    const cpx<R> di = fmas<R>(d[i], cd, et * pi);
+    const cpx<R> si = fmas<R>(sv[i], cd, et * pt[i]);
+    d[i] = di;
+    sv[i] = si;
+    x[i] = x[i] + di;
+    const cpx<R> rr = r[i] - si;
     r[i] = rr;
-    q.add(rr.x * rr.x + rr.y * rr.y);
+    acc.add(rr.x * rr.x + rr.y * rr.y);
+    const cpx<R> vn = scale<R>(v[i], ir);
+    v[i] = vn;
+    p[i] = vn - cp * pi;
   }
-  double acc[1] = {q.get()};
-  block_store<1>(acc, part, 0);
+  double a[1] = {acc.get()};
+  block_store<1>(a, part, 0);
 }
 
 __global__ void k_qmr_c(Scal* s, const double* part, int nb) {
@@ -373,7 +407,6 @@ __global__ void k_qmr_c(Scal* s, const double* part, int nb) {
   if (!isfinite(res)) { s->status = DDA_ERR_NONFINITE; s->done = 1; }
   else if (res < s->tol) { s->status = DDA_OK; s->done = 1; }
   else if (s->half) { s->status = DDA_BREAKDOWN; s->done = 1; }
-  else s->beta_k = s->beta_next;
 }
 
 // ---------------------------------------------------------------- Bi-CG-CS (COCG)
@@ -732,28 +765,26 @@ int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, do
   };
   k_norms<R><<<nb, kVT, 0, st>>>(b, n, part, nullptr); count_launch();
   if (solver == DDA_QMR_CS) {
-    cpx<R>*v = vec[0], *vp = vec[1], *w = vec[2], *p1 = vec[3], *p2 = vec[4], *a1 = vec[5],
-          *a2 = vec[6], *r = vec[7];
+    cpx<R>*v = vec[0], *p = vec[1], *pt = vec[2], *d = vec[3], *sv = vec[4], *r = vec[5];
     k_qmr_init<<<1, kVT, 0, st>>>(s, part, nb, tol); count_launch();
-    k_qmr_start<R><<<nb, kVT, 0, st>>>(b, v, r, x, vp, p1, p2, a1, a2, n, s); count_launch();
+    k_qmr_start<R><<<nb, kVT, 0, st>>>(b, v, p, r, x, d, sv, n, s); count_launch();
     LK(h);
     RK(sync_read(ru));
     for (int k = 1; k <= maxiter && !ru.hs->done; ++k) {
-      // w = A v; alpha = v^T w, from the product's last pass when it can
+      // pt = A p; eps = p^T pt, from the product's last pass when it can
       int dnb = 0;
-      RK(matvec<R>(ru, v, w, false, h->d_mvpart, &dnb));
+      RK(matvec<R>(ru, p, pt, false, h->d_mvpart, &dnb));
       if (dnb > 0) {
         k_qmr_a<<<1, kVT, 0, st>>>(s, h->d_mvpart, 1, 2, dnb); count_launch();
       } else {
-        k_dot<R, false><<<nb, kVT, 0, st>>>(v, w, n, part, 0, s); count_launch();
+        k_dot<R, false><<<nb, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
         k_qmr_a<<<1, kVT, 0, st>>>(s, part, kNB, 1, nb); count_launch();
       }
-      k_qmr_k1<R><<<nb, kVT, 0, st>>>(w, v, vp, n, s, part); count_launch();
+      k_qmr_k1<R><<<nb, kVT, 0, st>>>(pt, v, n, s, part); count_launch();
       k_qmr_b<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
-      k_qmr_k2<R><<<nb, kVT, 0, st>>>(vp, v, w, p1, p2, a1, a2, x, r, n, s, part); count_launch();
+      k_qmr_k2<R><<<nb, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part); count_launch();
       k_qmr_c<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
       LK(h);
-      std::swap(v, vp); std::swap(p1, p2); std::swap(a1, a2);
       ru.iters++;
       RK(sync_read(ru));
       rec();

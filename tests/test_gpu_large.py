@@ -1,0 +1,111 @@
+"""Large lattices: the 256^3 sphere (x = 40, m = 2.0; padded 512^3) and the
+536^3 sphere (x = 160, m = 1.05; padded 1080^3, 80,630,200 dipoles), the
+largest case of Table 1 at about 10 dipoles per wavelength.  Sampled outputs
+of both products are checked against the oracle's direct sum (Eq. 3), and the
+x = 160 sphere is solved to 1e-5 and compared with Mie theory (Sec. 3.1)."""
+import numpy as np
+import pytest
+
+from oracle import lattice, mie, observables, system
+from oracle import dda as odda
+from paper_0704_0037_gb300 import inputs
+
+from gpu_util import need_gpu
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _sampled_check(p, occ, m, prec_name, idx_count, seed):
+    torch, dda = need_gpu()
+    prec = dda.PREC[prec_name]
+    dda.dda_set_beta(p.h, dda.DDA_LDR, [(0, 0, 1)], [(1, 0, 0)])
+    x = inputs.random_vectors(seed, 1, p.n_occ)
+    dt = torch.complex128 if prec == dda.DDA_FP64 else torch.complex64
+    xd = torch.from_numpy(x).to("cuda", dt)
+    yd = torch.empty_like(xd)
+    dda.dda_matvec(p.h, prec, xd, yd)
+    idx = np.array([0, p.n_occ - 1] + list(np.random.default_rng(seed).integers(0, p.n_occ,
+                                                                              idx_count - 2)))
+    y = yd[0][:, torch.from_numpy(idx).cuda()].cpu().numpy()
+    del xd, yd
+    prob = odda.Problem(occ, [m], p.kd)
+    beta = prob.beta("ldr", (0, 0, 1), (1, 0, 0))
+    ref = system.matvec_rows(prob.pos, beta, prob.kd, x[0], idx)
+    err = np.abs(y - ref).max() / np.sqrt(np.mean(np.abs(ref) ** 2))
+    assert err <= (1e-12 if prec == dda.DDA_FP64 else 1e-5), err
+    return err
+
+
+@pytest.fixture(scope="module")
+def sphere256():
+    torch, dda = need_gpu()
+    occ = inputs.sphere(256)
+    p = dda.Particle(occ, [2.0], 40.0, volume_corrected=True)
+    assert p.n_occ == 8783848 and p.grid == (512, 512, 512)
+    dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+    yield p, occ
+    p.close()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
+def test_matvec_256_sampled(sphere256, prec_name):
+    p, occ = sphere256
+    _sampled_check(p, occ, 2.0, prec_name, 6, 256)
+
+
+@pytest.fixture(scope="module")
+def sphere536(sphere256):
+    torch, dda = need_gpu()
+    sphere256[0].close()                 # free the 512^3 workspace first
+    torch.cuda.empty_cache()
+    occ = inputs.sphere(536)
+    p = dda.Particle(occ, [1.05], 160.0, volume_corrected=True)
+    assert p.n_occ == 80630200 and p.grid == (1080, 1080, 1080)
+    assert abs(p.kd - lattice.kd_volume_corrected(160.0, 80630200)) < 1e-15
+    dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+    yield p, occ
+    p.close()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
+def test_matvec_536_sampled(sphere536, prec_name):
+    p, occ = sphere536
+    _sampled_check(p, occ, 1.05, prec_name, 3, 536)
+
+
+def test_solve_536_against_mie(sphere536):
+    """x = 160, m = 1.05 (Table 1's largest sphere): FP32-refined QMR-CS to a
+    true residual of 1e-5; Q_ext within 1 % of Mie (the paper's errors for
+    m = 1.05 are far below that, Sec. 4) and S11 in the xz plane with the RMS
+    relative error inside the paper's range (Sec. 4: 0.04 to 1).  The
+    y-polarised far field comes from the x-polarised solution rotated by 90
+    degrees about z (the sphere's lattice is invariant under that rotation)."""
+    torch, dda = need_gpu()
+    p, occ = sphere536
+    prop = np.array([[0.0, 0.0, 1.0]])
+    pol = np.array([[1.0, 0.0, 0.0]])
+    P = torch.zeros((1, 3, p.n_occ), dtype=torch.complex128, device="cuda")
+    st, info, _ = dda.dda_solve(p.h, dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_LDR,
+                                          prec=dda.DDA_FP32_REFINED, tol=1e-5, maxiter=3000,
+                                          inner_tol=8e-6), prop, pol, P)
+    assert st == 0 and info[0]["rel_res_true"] < 1e-5, info
+    th = inputs.angles_deg(181)
+    t = np.deg2rad(th)
+    d_xz = np.stack([np.sin(t), np.zeros_like(t), np.cos(t)], axis=1)
+    d_yz = np.stack([np.zeros_like(t), -np.sin(t), np.cos(t)], axis=1)
+    F, q = dda.dda_scatter(p.h, dda.DDA_LDR, P, prop, pol, np.concatenate([d_xz, d_yz]))
+    Fx = F[0, :181]
+    Fr = F[0, 181:]
+    Fy = np.stack([-Fr[:, 1], Fr[:, 0], Fr[:, 2]], axis=1)     # R_z(90 deg) applied
+    s11 = dda.dda_mueller_plane(th, Fx, Fy)
+    qm = mie.efficiencies(160.0, 1.05)[0]
+    s11m = mie.s11(160.0, 1.05, th)
+    rel = np.abs(s11 - s11m) / s11m
+    print(f"536^3: iters {info[0]['iters']} outer {info[0]['outer']} "
+          f"res {info[0]['rel_res_true']:.3e} Qext {q[0, 0]:.6f} Mie {qm:.6f} "
+          f"S11 max {rel.max():.3f} rms {np.sqrt(np.mean(rel ** 2)):.3f}")
+    assert abs(q[0, 0] / qm - 1) < 0.01
+    assert abs(q[0, 1]) < 1e-6 * q[0, 0]                     # real m: Q_abs = 0
+    assert np.sqrt(np.mean(rel ** 2)) < 1.0

@@ -127,6 +127,38 @@ def test_qmr_recurrence_tracks_true_residual():
     assert info["hist"][0] == 1.0 and info["hist"][-1] < 1e-9
 
 
+def test_qmr_iterates_are_quasi_minimal():
+    """QMR by its definition: after k steps x_k = V_k z, z minimising
+    ||rho_1 e_1 - H z||_2, where A V_k = V_{k+1} H is the complex-symmetric
+    Lanczos relation in a unit-Euclidean-norm basis.  The basis here comes
+    from explicit Gram-Schmidt with the bilinear form against every earlier
+    vector and a least-squares solve, independent of the solver's
+    recurrences."""
+    prob, beta, b, _ = _solver_problem(1.8)
+    mv = prob.matvec(beta, "brute")
+    kmax = 8
+    rho1 = np.linalg.norm(b)
+    V = [b / rho1]
+    H = np.zeros((kmax + 1, kmax), dtype=np.complex128)
+    for j in range(kmax):
+        w = mv(V[j])
+        for i in range(j + 1):
+            h = np.sum(V[i] * w) / np.sum(V[i] * V[i])
+            H[i, j] += h
+            w = w - h * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        V.append(w / H[j + 1, j])
+    assert np.abs(np.triu(H[:kmax, :kmax], 2)).max() < 1e-10 * np.abs(H).max()   # tridiagonal
+    for k in (1, 3, 8):
+        rhs = np.zeros(k + 1, dtype=np.complex128)
+        rhs[0] = rho1
+        z = np.linalg.lstsq(H[:k + 1, :k], rhs, rcond=None)[0]
+        xk = sum(V[j] * z[j] for j in range(k))
+        xq, info = solvers.qmr_cs(mv, b, tol=0.0, maxiter=k)
+        assert info["iters"] == k
+        assert np.linalg.norm(xq - xk) / np.linalg.norm(xk) < 1e-10
+
+
 def test_matvec_counts():
     prob, beta, b, _ = _solver_problem(1.5)
     mv = prob.matvec(beta, "brute")
