@@ -212,6 +212,92 @@ int dda_mueller_plane(int n_theta, const double* theta_deg_host, const double* F
                       const double* F_ypol_host, double* s11_out_host);
 
 /*
+ * dda_mueller_plane_full -- all 16 Mueller elements in the xz scattering
+ * plane (Sec. 3.1: "all Mueller matrix elements in one scattering plane"),
+ * from the same amplitudes as dda_mueller_plane.  With the amplitude matrix
+ * [[S2, S3], [S4, S1]] acting on (E_par, E_perp) and Stokes vectors
+ * (I, Q, U, V) = (|E_par|^2+|E_perp|^2, |E_par|^2-|E_perp|^2,
+ * 2 Re(E_par E_perp^*), -2 Im(E_par E_perp^*)) (Bohren-Huffman), the scattered
+ * Stokes vector is M times the incident one.
+ *   M_out_host : n_theta x 16 doubles, row-major M[i][j] (M11 first).
+ * Host-only arithmetic; no device work.  DDA_ERR_ARG on a null pointer.
+ */
+int dda_mueller_plane_full(int n_theta, const double* theta_deg_host, const double* F_xpol_host,
+                           const double* F_ypol_host, double* M_out_host);
+
+/*
+ * dda_asymmetry -- the asymmetry parameter <cos theta> (Sec. 3.1) from the
+ * amplitudes F (as dda_scatter returns them) at n_dir quadrature directions:
+ *   g_vec = sum_k w_k |F_k|^2 n_k / sum_k w_k |F_k|^2,  <cos theta> = g_vec . a.
+ *   dirs_host : n_dir x 3 unit directions;  weights_host : n_dir weights;
+ *   F_host : n_dir x 3 complex (re, im);  prop_host : the incidence direction a.
+ *   g_out_host : 4 doubles = (<cos theta>, g_x, g_y, g_z).
+ * Host-only arithmetic.  DDA_ERR_ARG on a null pointer, n_dir < 1 or a zero
+ * total scattered power.
+ */
+int dda_asymmetry(int n_dir, const double* dirs_host, const double* weights_host,
+                  const double* F_host, const double* prop_host, double* g_out_host);
+
+/*
+ * dda_symmetry -- symmetries of the lattice found at dda_init_lattice.
+ *   flags_out : bit 0 (DDA_SYM_ROT90_Z) set when the occupancy, materials
+ *   included, is invariant under the rotation by +90 degrees about z
+ *   ((x, y) -> (-y, x); needs nx = ny), e.g. every sphere lattice.
+ */
+#define DDA_SYM_ROT90_Z 1
+int dda_symmetry(dda_t h, int* flags_out);
+
+/*
+ * dda_mueller_plane_sym -- the 16 Mueller elements in the xz plane from ONE
+ * solution, the x-polarised one for incidence along +z (Sec. 3.1 uses the
+ * symmetry of the sphere to get all results from one polarisation state).
+ * For a lattice invariant under R = rotation by +90 degrees about z, the
+ * y-polarised solution is P_y(r) = R P_x(R^-1 r), so its amplitude is
+ * F_y(n) = R F_x(R^-1 n); the library evaluates F_x at n = (sin t, 0, cos t)
+ * and at R^-1 n = (0, -sin t, cos t) on the device and proceeds as
+ * dda_mueller_plane_full.  Holds for every polarizability prescription here
+ * (for incidence along z both polarisations have the same alpha).
+ *   P_dev : device [3][N_occ] complex128, the x-polarised solution.
+ *   M_out_host : n_theta x 16.   F_out_host : optional, n_theta x 2 x 3
+ *   complex (F_x then F_y per angle) or NULL.
+ * DDA_ERR_ARG when the lattice lacks the symmetry (dda_symmetry) or on bad
+ * arguments.  Synchronises the stream.
+ */
+int dda_mueller_plane_sym(dda_t h, int pol_prescription, const void* P_dev, int n_theta,
+                          const double* theta_deg_host, double* M_out_host, double* F_out_host);
+
+/*
+ * dda_orientation_average -- scattering averaged over particle orientations
+ * (Sec. 2: averaging over the Euler angles alpha, beta, gamma; alpha by
+ * scattering planes of one solution, beta and gamma by independent
+ * solutions).  Orientation R = Rz(alpha) Ry(beta) Rz(gamma) (z-y-z) takes the
+ * particle frame to the laboratory, incidence along laboratory z.  For each
+ * (beta, gamma) node the library solves the two polarisations (incidence
+ * R^T z, polarisations R^T x and R^T y) as two right-hand sides, evaluates
+ * the far field in n_alpha scattering planes of azimuth 2 pi k / n_alpha
+ * (amplitudes along theta_hat and phi_hat of each plane, polarisations
+ * combined as cos(phi) e_x + sin(phi) e_y and -sin(phi) e_x + cos(phi) e_y)
+ * and accumulates the Mueller matrix and the cross sections for unpolarised
+ * light.  Quadrature, fixed: Gauss-Legendre in cos(beta) (n_beta nodes),
+ * uniform gamma (n_gamma) and alpha (n_alpha) nodes; no Romberg adaptivity.
+ *   opts : solver options as in dda_solve; opts->pol must not be DDA_LDR
+ *          (its polarizability depends on the incident polarisation, so the
+ *          field of a rotated polarisation is not a combination of the two
+ *          solutions): DDA_ERR_ARG.
+ *   theta_deg_host : n_theta scattering angles.
+ *   q_avg_host : 2 doubles = <Q_ext>, <Q_abs>.
+ *   M_avg_host : n_theta x 16 doubles, the averaged Mueller matrix.
+ *   info_host  : optional, 2 * n_beta * n_gamma entries (node (ib, ig),
+ *                polarisation r at 2 (ib n_gamma + ig) + r).
+ * The D-matrix must be built for opts->prec.  Allocates 2 x 3 N_occ
+ * complex128 of device memory for the duration of the call.  Returns DDA_OK,
+ * or the first non-OK solver status (the averages are still written).
+ */
+int dda_orientation_average(dda_t h, const dda_solve_opts* opts, int n_alpha, int n_beta,
+                            int n_gamma, int n_theta, const double* theta_deg_host,
+                            double* q_avg_host, double* M_avg_host, dda_solve_info* info_host);
+
+/*
  * dda_farfield_noalloc -- the scattering amplitude F(n) of dda_scatter for
  * one polarization vector, computed without allocating any device memory.
  * (The paper has no counterpart: this is an interface for callers that cannot

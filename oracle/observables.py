@@ -16,6 +16,12 @@ plane (n = (sin t, 0, cos t), theta_hat = (cos t, 0, -sin t)):
   x-polarised incidence: S2 = theta_hat . F, S4 = -y_hat . F
   y-polarised incidence: S3 = -theta_hat . F, S1 = y_hat . F
   S11 = (|S1|^2 + |S2|^2 + |S3|^2 + |S4|^2) / 2
+The full 4x4 Mueller matrix follows from its definition: Stokes vectors
+(I, Q, U, V) = (|E_par|^2 + |E_perp|^2, |E_par|^2 - |E_perp|^2,
+2 Re(E_par E_perp^*), -2 Im(E_par E_perp^*)) of the scattered field
+(E_par, E_perp)_s = [[S2, S3], [S4, S1]] (E_par, E_perp)_inc for four incident
+states whose Stokes vectors span R^4.  The asymmetry parameter is
+<cos theta> = \\oint |F|^2 (n . a) dOmega / \\oint |F|^2 dOmega.
 """
 import math
 
@@ -95,3 +101,49 @@ def q_sca_quadrature(P, pos, kd, x_size, n_theta, n_phi):
     dirs, w = sphere_quadrature(n_theta, n_phi)
     F = farfield(P, pos, kd, dirs)
     return float(np.sum(w * np.sum(np.abs(F) ** 2, axis=1))) / (math.pi * x_size ** 2)
+
+
+def stokes(e_par, e_perp):
+    """Stokes vectors (..., 4) of fields with components (E_par, E_perp)."""
+    z = e_par * np.conj(e_perp)
+    return np.stack([np.abs(e_par) ** 2 + np.abs(e_perp) ** 2,
+                     np.abs(e_par) ** 2 - np.abs(e_perp) ** 2,
+                     2.0 * z.real, -2.0 * z.imag], axis=-1)
+
+
+def mueller_from_amplitudes(S1, S2, S3, S4):
+    """(n, 4, 4) Mueller matrices by the definition: the scattered Stokes
+    vectors of four incident states (parallel, perpendicular, +45 degree and
+    circular) against their incident Stokes vectors."""
+    S1, S2, S3, S4 = (np.atleast_1d(np.asarray(v, dtype=np.complex128)) for v in (S1, S2, S3, S4))
+    r = 1.0 / math.sqrt(2.0)
+    states = [(1.0, 0.0), (0.0, 1.0), (r, r), (r, 1j * r)]
+    s_in = np.stack([stokes(np.complex128(a), np.complex128(b)) for a, b in states], axis=1)
+    s_out = np.stack([stokes(S2 * a + S3 * b, S4 * a + S1 * b) for a, b in states], axis=2)
+    return s_out @ np.linalg.inv(s_in)
+
+
+def mueller_plane(F_xpol, F_ypol, thetas_deg):
+    """Mueller matrix in the xz plane, (n, 4, 4)."""
+    return mueller_from_amplitudes(*amplitude_plane(F_xpol, F_ypol, thetas_deg))
+
+
+def asymmetry_from_farfield(F, dirs, weights, prop):
+    """<cos theta> and the vector <n> from far fields F (K, 3) at quadrature
+    directions dirs (K, 3) with weights (K,): (g, g_vec)."""
+    f2 = np.asarray(weights) * np.sum(np.abs(F) ** 2, axis=1)
+    gvec = (f2[:, None] * np.asarray(dirs)).sum(axis=0) / f2.sum()
+    return float(gvec @ np.asarray(prop, dtype=np.float64)), gvec
+
+
+def rotate_z90(v):
+    """R v for the rotation by +90 degrees about z: (x, y, z) -> (-y, x, z)."""
+    v = np.asarray(v)
+    return np.stack([-v[..., 1], v[..., 0], v[..., 2]], axis=-1)
+
+
+def ypol_farfield_by_symmetry(F_xpol_rotdirs):
+    """For a lattice invariant under the +90 degree rotation about the
+    incidence axis z, the y-polarised amplitude at n equals R F_xpol(R^-1 n).
+    Given F_xpol at the directions R^-1 n, return F_ypol at n."""
+    return rotate_z90(F_xpol_rotdirs)

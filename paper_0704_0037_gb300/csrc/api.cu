@@ -215,6 +215,17 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   }
   g.n_occ = (long long)h->xi_h.size();
   if (g.n_occ == 0) { delete h; return DDA_ERR_ARG; }
+  // rotation by +90 degrees about z maps cell (x=i, y=j) to (x=n-1-j, y=i)
+  if (nx == ny) {
+    bool sym = true;
+    for (int iz = 0; iz < nz && sym; ++iz) {
+      const uint8_t* pl = occ + (size_t)iz * nx * ny;
+      for (int j = 0; j < ny && sym; ++j)
+        for (int i = 0; i < nx; ++i)
+          if (pl[(size_t)i * nx + (nx - 1 - j)] != pl[(size_t)j * nx + i]) { sym = false; break; }
+    }
+    if (sym) h->sym_flags |= DDA_SYM_ROT90_Z;
+  }
   g.Mx = smooth_size(2 * nx - 1);
   g.My = smooth_size(2 * ny - 1);
   g.Mz = smooth_size(2 * nz - 1);
@@ -340,6 +351,112 @@ extern "C" int dda_mueller_plane(int n_theta, const double* th, const double* Fx
                     s4r * s4r + s4i * s4i);
   }
   return DDA_OK;
+}
+
+static inline double cabs2h(c128 a) { return a.x * a.x + a.y * a.y; }
+
+// Amplitude matrix in the xz plane from F_x, F_y at n = (sin t, 0, cos t):
+// S2 = theta.F_x, S4 = -y.F_x, S3 = -theta.F_y, S1 = y.F_y (theta = (cos t, 0, -sin t))
+static void plane_amplitudes(double t_deg, const double* fx, const double* fy, c128 S[4]) {
+  const double t = t_deg * (M_PI / 180.0);
+  const double ct = std::cos(t), st = std::sin(t);
+  S[1] = mk<double>(ct * fx[0] - st * fx[4], ct * fx[1] - st * fx[5]);        // S2
+  S[3] = mk<double>(-fx[2], -fx[3]);                                          // S4
+  S[2] = mk<double>(-(ct * fy[0] - st * fy[4]), -(ct * fy[1] - st * fy[5]));  // S3
+  S[0] = mk<double>(fy[2], fy[3]);                                            // S1
+}
+
+// The 16 Mueller elements of the amplitude matrix [[S2, S3], [S4, S1]] acting
+// on (E_par, E_perp), Stokes (I, Q, U, V) = (|E_par|^2+|E_perp|^2,
+// |E_par|^2-|E_perp|^2, 2 Re(E_par E_perp^*), -2 Im(E_par E_perp^*)):
+// with a = S2, b = S3, c = S4, d = S1, expand the Stokes vector of
+// (a E_par + b E_perp, c E_par + d E_perp).  S[] = {S1, S2, S3, S4}.
+void mueller_from_S(const c128 S[4], double* m) {
+  const c128 a = S[1], b = S[2], c = S[3], d = S[0];
+  const double A = cabs2h(a), B = cabs2h(b), C = cabs2h(c), D = cabs2h(d);
+  const c128 ab = a * conjg(b), cd = c * conjg(d), ac = a * conjg(c), bd = b * conjg(d);
+  const c128 ad = a * conjg(d), bc = b * conjg(c);
+  m[0] = 0.5 * (A + B + C + D);  m[1] = 0.5 * (A - B + C - D);
+  m[2] = ab.x + cd.x;            m[3] = ab.y + cd.y;
+  m[4] = 0.5 * (A + B - C - D);  m[5] = 0.5 * (A - B - C + D);
+  m[6] = ab.x - cd.x;            m[7] = ab.y - cd.y;
+  m[8] = ac.x + bd.x;            m[9] = ac.x - bd.x;
+  m[10] = ad.x + bc.x;           m[11] = ad.y - bc.y;
+  m[12] = -(ac.y + bd.y);        m[13] = -(ac.y - bd.y);
+  m[14] = -(ad.y + bc.y);        m[15] = ad.x - bc.x;
+}
+
+extern "C" int dda_mueller_plane_full(int n_theta, const double* th, const double* Fx,
+                                      const double* Fy, double* M) {
+  if (n_theta < 0 || (n_theta > 0 && (!th || !Fx || !Fy || !M))) return DDA_ERR_ARG;
+  for (int i = 0; i < n_theta; ++i) {
+    c128 S[4];
+    plane_amplitudes(th[i], Fx + 6 * i, Fy + 6 * i, S);
+    mueller_from_S(S, M + 16 * i);
+  }
+  return DDA_OK;
+}
+
+extern "C" int dda_asymmetry(int n_dir, const double* dirs, const double* w, const double* F,
+                             const double* prop, double* g) {
+  if (n_dir < 1 || !dirs || !w || !F || !prop || !g) return DDA_ERR_ARG;
+  double s = 0.0, v[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < n_dir; ++k) {
+    double f2 = 0.0;
+    for (int q = 0; q < 6; ++q) f2 += F[6 * k + q] * F[6 * k + q];
+    const double wf = w[k] * f2;
+    s += wf;
+    for (int q = 0; q < 3; ++q) v[q] += wf * dirs[3 * k + q];
+  }
+  if (!(s > 0.0) || !std::isfinite(s)) return DDA_ERR_ARG;
+  for (int q = 0; q < 3; ++q) g[1 + q] = v[q] / s;
+  g[0] = g[1] * prop[0] + g[2] * prop[1] + g[3] * prop[2];
+  return DDA_OK;
+}
+
+extern "C" int dda_symmetry(dda_t h, int* flags) {
+  if (!h || !flags) return DDA_ERR_ARG;
+  *flags = h->sym_flags;
+  return DDA_OK;
+}
+
+extern "C" int dda_mueller_plane_sym(dda_t h, int presc, const void* P_dev, int n_theta,
+                                     const double* th, double* M, double* F_out) {
+  if (!h) return DDA_ERR_ARG;
+  if (!(h->sym_flags & DDA_SYM_ROT90_Z))
+    return dda_fail(h, DDA_ERR_ARG, "lattice is not invariant under the 90 degree rotation about z");
+  if (n_theta < 1 || !th || !M || !P_dev) return dda_fail(h, DDA_ERR_ARG, "bad arguments");
+  std::vector<double> dirs((size_t)6 * n_theta), F((size_t)12 * n_theta);
+  for (int i = 0; i < n_theta; ++i) {
+    const double t = th[i] * (M_PI / 180.0);
+    double* a = dirs.data() + 3 * i;
+    double* b = dirs.data() + 3 * (n_theta + i);
+    a[0] = std::sin(t); a[1] = 0.0; a[2] = std::cos(t);      // n
+    b[0] = 0.0; b[1] = -std::sin(t); b[2] = std::cos(t);     // R^-1 n
+  }
+  const double prop[3] = {0.0, 0.0, 1.0};
+  const double pol[6] = {1.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double q[3];
+  const int rc = dda_scatter_internal(h, presc, P_dev, 1, prop, pol, 2 * n_theta, dirs.data(),
+                                      nullptr, F.data(), q);
+  if (rc != DDA_OK) return rc;
+  std::vector<double> Fy((size_t)6 * n_theta);
+  for (int i = 0; i < n_theta; ++i) {
+    const double* fr = F.data() + 6 * (n_theta + i);     // F_x at R^-1 n
+    double* fy = Fy.data() + 6 * i;                      // R applied: (x, y, z) -> (-y, x, z)
+    fy[0] = -fr[2]; fy[1] = -fr[3];
+    fy[2] = fr[0];  fy[3] = fr[1];
+    fy[4] = fr[4];  fy[5] = fr[5];
+  }
+  if (F_out) {
+    for (int i = 0; i < n_theta; ++i) {
+      for (int q2 = 0; q2 < 6; ++q2) {
+        F_out[12 * i + q2] = F[6 * i + q2];
+        F_out[12 * i + 6 + q2] = Fy[6 * i + q2];
+      }
+    }
+  }
+  return dda_mueller_plane_full(n_theta, th, F.data(), Fy.data(), M);
 }
 
 extern "C" int dda_n_occ(dda_t h, long long* n) {

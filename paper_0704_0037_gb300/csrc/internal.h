@@ -92,6 +92,7 @@ int smooth_size(int lo);
 
 // The handle.
 struct dda_ctx {
+  int sym_flags = 0;        // DDA_SYM_* found at init
   dda::Geom g{};
   int n_mat = 0;
   std::vector<double> m;          // 2*n_mat
@@ -143,6 +144,8 @@ int dda_build_D_internal(dda_t h, bool want32);
 int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                        const double* pol, void* P_dev, double* hist, int hist_len,
                        dda_solve_info* info);
+// the 16 Mueller elements (row-major) of amplitudes S = {S1, S2, S3, S4} (api.cu)
+void mueller_from_S(const dda::c128 S[4], double* m);
 // scatter (scatter.cu)
 int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const double* prop,
                          const double* pol, int n_dir, const double* dirs, const double* w,

@@ -34,6 +34,8 @@ PREC = {"fp64": DDA_FP64, "fp32_refined": DDA_FP32_REFINED}
 # every entry point declared in include/dda.h
 EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec",
            "dda_matvec_adjoint", "dda_solve", "dda_scatter", "dda_mueller_plane",
+           "dda_mueller_plane_full", "dda_asymmetry", "dda_symmetry", "dda_mueller_plane_sym",
+           "dda_orientation_average",
            "dda_farfield_noalloc", "dda_trace",
            "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
            "dda_free")
@@ -89,6 +91,12 @@ def lib():
                        ctypes.POINTER(SolveInfo)], _ip),
         "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
+        "dda_mueller_plane_full": ([_ip, _dp, _dp, _dp, _dp], _ip),
+        "dda_asymmetry": ([_ip, _dp, _dp, _dp, _dp, _dp], _ip),
+        "dda_symmetry": ([_vp, ctypes.POINTER(ctypes.c_int)], _ip),
+        "dda_mueller_plane_sym": ([_vp, _ip, _vp, _ip, _dp, _dp, _dp], _ip),
+        "dda_orientation_average": ([_vp, ctypes.POINTER(SolveOpts), _ip, _ip, _ip, _ip, _dp, _dp,
+                                     _dp, ctypes.POINTER(SolveInfo)], _ip),
         "dda_farfield_noalloc": ([_vp, _vp, _ip, _vp, _vp], _ip),
         "dda_trace": ([_vp, _ip], _ip),
         "dda_trace_read": ([_vp, _ip, ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_longlong),
@@ -184,16 +192,19 @@ def dda_matvec_adjoint(h, prec, x, y, nrhs=1):
                                               int(nrhs)))
 
 
+def _opts(opts):
+    if isinstance(opts, dict):
+        return SolveOpts(solver=opts.get("solver", DDA_QMR_CS), pol=opts.get("pol", DDA_LDR),
+                         prec=opts.get("prec", DDA_FP64), tol=opts.get("tol", 1e-5),
+                         maxiter=opts.get("maxiter", 10000), inner_tol=opts.get("inner_tol", 1e-3),
+                         checkpoint_every=0)
+    return opts
+
+
 def dda_solve(h, opts, prop, pol, P, hist_len=0):
     """opts: SolveOpts or dict.  Returns (status, [info dicts], hist or None)."""
     import torch
-    if isinstance(opts, dict):
-        o = SolveOpts(solver=opts.get("solver", DDA_QMR_CS), pol=opts.get("pol", DDA_LDR),
-                      prec=opts.get("prec", DDA_FP64), tol=opts.get("tol", 1e-5),
-                      maxiter=opts.get("maxiter", 10000), inner_tol=opts.get("inner_tol", 1e-3),
-                      checkpoint_every=0)
-    else:
-        o = opts
+    o = _opts(opts)
     nrhs = int(np.asarray(prop).size // 3)
     a, e = _vecs(prop, pol, nrhs)
     info = (SolveInfo * nrhs)()
@@ -221,6 +232,72 @@ def dda_scatter(h, pol_prescription, P, prop, pol, dirs=None, weights=None):
     _check(h, rc)
     Fc = (F[..., 0::2] + 1j * F[..., 1::2])[:, :n_dir, :]
     return Fc, q
+
+
+def _cplx_pairs(F):
+    f = np.asarray(F, dtype=np.complex128).reshape(-1, 3)
+    return np.ascontiguousarray(np.stack([f.real, f.imag], axis=-1).reshape(-1))
+
+
+def dda_mueller_plane_full(theta_deg, F_xpol, F_ypol):
+    """(n_theta, 4, 4) Mueller matrices in the xz plane."""
+    th = np.ascontiguousarray(np.asarray(theta_deg, dtype=np.float64))
+    out = np.zeros(th.size * 16)
+    rc = lib().dda_mueller_plane_full(th.size, _dptr(th), _dptr(_cplx_pairs(F_xpol)),
+                                      _dptr(_cplx_pairs(F_ypol)), _dptr(out))
+    if rc < 0:
+        raise DDAError(rc, "dda_mueller_plane_full")
+    return out.reshape(-1, 4, 4)
+
+
+def dda_asymmetry(dirs, weights, F, prop):
+    """(<cos theta>, g_vec) from amplitudes at quadrature directions."""
+    d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    a = np.ascontiguousarray(np.asarray(prop, dtype=np.float64).reshape(3))
+    g = np.zeros(4)
+    rc = lib().dda_asymmetry(d.shape[0], _dptr(d), _dptr(w), _dptr(_cplx_pairs(F)), _dptr(a),
+                             _dptr(g))
+    if rc < 0:
+        raise DDAError(rc, "dda_asymmetry")
+    return float(g[0]), g[1:].copy()
+
+
+DDA_SYM_ROT90_Z = 1
+
+
+def dda_symmetry(h):
+    f = ctypes.c_int(0)
+    _check(h, lib().dda_symmetry(h, ctypes.byref(f)))
+    return f.value
+
+
+def dda_mueller_plane_sym(h, pol_prescription, P, theta_deg):
+    """Mueller matrices (n, 4, 4) in the xz plane from the x-polarised
+    solution alone (lattice invariant under the 90 degree rotation about z);
+    also returns (F_x, F_y), each (n, 3) complex."""
+    import torch
+    th = np.ascontiguousarray(np.asarray(theta_deg, dtype=np.float64))
+    M = np.zeros(th.size * 16)
+    F = np.zeros(th.size * 12)
+    _check(h, lib().dda_mueller_plane_sym(h, int(pol_prescription), _dev_ptr(P, torch.complex128),
+                                          th.size, _dptr(th), _dptr(M), _dptr(F)))
+    Fc = F[0::2] + 1j * F[1::2]
+    Fc = Fc.reshape(-1, 2, 3)
+    return M.reshape(-1, 4, 4), Fc[:, 0], Fc[:, 1]
+
+
+def dda_orientation_average(h, opts, n_alpha, n_beta, n_gamma, theta_deg):
+    """Returns (status, (<Q_ext>, <Q_abs>), M (n, 4, 4), [info dicts])."""
+    o = _opts(opts)
+    th = np.ascontiguousarray(np.asarray(theta_deg, dtype=np.float64))
+    q = np.zeros(2)
+    M = np.zeros(th.size * 16)
+    infos = (SolveInfo * (2 * n_beta * n_gamma))()
+    rc = _check(h, lib().dda_orientation_average(h, ctypes.byref(o), int(n_alpha), int(n_beta),
+                                                 int(n_gamma), th.size, _dptr(th), _dptr(q),
+                                                 _dptr(M), infos))
+    return rc, (float(q[0]), float(q[1])), M.reshape(-1, 4, 4), [i.as_dict() for i in infos]
 
 
 def dda_mueller_plane(theta_deg, F_xpol, F_ypol):

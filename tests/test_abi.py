@@ -69,3 +69,28 @@ def test_mueller_plane_host_logic(L):
     s11 = dda.dda_mueller_plane(th, Fx, Fy)
     ref = observables.s11_plane(Fx, Fy, th)
     assert np.allclose(s11, ref, rtol=1e-14, atol=0)
+
+
+def test_mueller_full_host_logic(L):
+    """All 16 elements from the closed forms equal the oracle's Mueller matrix
+    by the Stokes-vector definition, on random amplitudes."""
+    rng = np.random.default_rng(1)
+    th = inputs.angles_deg(29)
+    Fx = rng.standard_normal((29, 3)) + 1j * rng.standard_normal((29, 3))
+    Fy = rng.standard_normal((29, 3)) + 1j * rng.standard_normal((29, 3))
+    M = dda.dda_mueller_plane_full(th, Fx, Fy)
+    ref = observables.mueller_plane(Fx, Fy, th)
+    assert np.abs(M - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.allclose(M[:, 0, 0], dda.dda_mueller_plane(th, Fx, Fy), rtol=1e-14)
+
+
+def test_asymmetry_host_logic(L):
+    rng = np.random.default_rng(2)
+    dirs, w = observables.sphere_quadrature(8, 12)
+    F = rng.standard_normal((dirs.shape[0], 3)) + 1j * rng.standard_normal((dirs.shape[0], 3))
+    a = np.array([0.6, 0.0, 0.8])
+    g, gv = dda.dda_asymmetry(dirs, w, F, a)
+    g0, gv0 = observables.asymmetry_from_farfield(F, dirs, w, a)
+    assert abs(g - g0) < 1e-14 and np.allclose(gv, gv0, rtol=0, atol=1e-14)
+    with pytest.raises(dda.DDAError):
+        dda.dda_asymmetry(dirs, w, 0 * F, a)          # no scattered power

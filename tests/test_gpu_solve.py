@@ -133,6 +133,69 @@ def test_qsca_quadrature_matches_oracle(sphere16):
         assert abs(q[r, 0] - q[r, 1] - q[r, 2]) <= 1e-5 * q[r, 0]
 
 
+def test_mueller_full_and_single_polarisation_symmetry(sphere16):
+    """All 16 in-plane Mueller elements against the oracle (exact solutions);
+    the single-polarisation route (x-polarised solution + the 90 degree
+    rotation symmetry of the sphere lattice, Sec. 3.1) gives the same matrix."""
+    torch, dda = need_gpu()
+    p, prob, exact = sphere16
+    st, info, P, _ = _solve(p, "qmr_cs", "fp64", 1e-10)
+    th = inputs.angles_deg(91)
+    dirs = observables.plane_dirs(th)
+    F, _ = dda.dda_scatter(p.h, dda.DDA_LDR, P, PROP, POLS, dirs)
+    M = dda.dda_mueller_plane_full(th, F[0], F[1])
+    Fo = [observables.farfield(exact[r], prob.pos, prob.kd, dirs) for r in range(2)]
+    Mo = observables.mueller_plane(Fo[0], Fo[1], th)
+    assert np.abs(M - Mo).max() <= 1e-7 * np.abs(Mo).max()
+    assert dda.dda_symmetry(p.h) == dda.DDA_SYM_ROT90_Z
+    Ms, Fx, Fy = dda.dda_mueller_plane_sym(p.h, dda.DDA_LDR, P[0], th)
+    assert np.abs(Fx - F[0]).max() <= 1e-12 * np.abs(F[0]).max()
+    assert np.abs(Ms - M).max() <= 1e-7 * np.abs(M).max()     # the two solves differ by ~tol
+    # the cross-polarised elements vanish in this symmetry plane
+    for (i, j) in ((0, 2), (0, 3), (2, 0), (3, 0), (1, 2), (1, 3)):
+        assert np.abs(M[:, i, j]).max() <= 1e-8 * M[:, 0, 0].max()
+
+
+def test_symmetry_flag_and_refusal():
+    torch, dda = need_gpu()
+    occ = inputs.ellipsoid(10, 8, 6)
+    p, prob = twin(occ, [1.5], 0.5)
+    with p:
+        assert dda.dda_symmetry(p.h) == 0
+        P = torch.zeros((3, p.n_occ), dtype=torch.complex128, device="cuda")
+        with pytest.raises(dda.DDAError) as ei:
+            dda.dda_mueller_plane_sym(p.h, dda.DDA_LDR, P, [0.0, 90.0])
+        assert ei.value.status == dda.DDA_ERR_ARG
+    # a cube with two materials arranged without the rotation symmetry
+    occ = inputs.cube(6, 6, 4)
+    occ[:, :, :3] = 2
+    p, prob = twin(occ, [1.5, 1.3], 0.5)
+    with p:
+        assert dda.dda_symmetry(p.h) == 0
+    occ = inputs.cube(6, 6, 4)
+    p, prob = twin(occ, [1.5], 0.5)
+    with p:
+        assert dda.dda_symmetry(p.h) == dda.DDA_SYM_ROT90_Z
+
+
+def test_asymmetry_parameter(sphere16):
+    """<cos theta> from the library's amplitudes on a sphere quadrature against
+    the oracle's, and against Mie within the paper's regime (Sec. 4)."""
+    torch, dda = need_gpu()
+    p, prob, exact = sphere16
+    st, info, P, _ = _solve(p, "qmr_cs", "fp64", 1e-10)
+    dirs, w = observables.sphere_quadrature(32, 64)
+    F, q = dda.dda_scatter(p.h, dda.DDA_LDR, P, PROP, POLS, dirs, w)
+    for r in range(2):
+        g, gv = dda.dda_asymmetry(dirs, w, F[r], PROP[r])
+        Fo = observables.farfield(exact[r], prob.pos, prob.kd, dirs)
+        go, gvo = observables.asymmetry_from_farfield(Fo, dirs, w, PROP[r])
+        assert abs(g - go) <= 1e-7 * abs(go)
+        assert np.abs(gv[:2]).max() < 1e-6
+        gm = mie.efficiencies(3.0, 1.5)[3]
+        assert abs(g / gm - 1) < 0.03
+
+
 def test_status_codes_and_edge_cases():
     torch, dda = need_gpu()
     occ = inputs.sphere(6)

@@ -198,3 +198,80 @@ def test_dda_converges_to_mie_config_sphere16():
         assert abs(res["qabs"][0]) < 1e-10
     assert errs[0][0] < 0.03 and errs[0][1] < 0.4
     assert errs[1][0] < errs[0][0] and errs[1][2] < errs[0][2]
+
+
+# ---------------------------------------------------------------- full Mueller matrix, <cos theta>
+def test_mueller_sphere_form_from_mie():
+    """Sphere amplitudes (S3 = S4 = 0): the Mueller matrix by its Stokes
+    definition has the textbook block form M11 = M22 = (|S1|^2 + |S2|^2)/2,
+    M12 = M21 = (|S2|^2 - |S1|^2)/2, M33 = M44 = Re(S1 S2^*),
+    M34 = -M43 = Im(S2 S1^*), all other elements 0."""
+    th = inputs.angles_deg(37)
+    S1, S2 = mie.amplitudes(3.0, 1.5 + 0.1j, th)
+    z = np.zeros_like(S1)
+    M = observables.mueller_from_amplitudes(S1, S2, z, z)
+    a, b = np.abs(S1) ** 2, np.abs(S2) ** 2
+    ref = np.zeros_like(M)
+    ref[:, 0, 0] = ref[:, 1, 1] = 0.5 * (a + b)
+    ref[:, 0, 1] = ref[:, 1, 0] = 0.5 * (b - a)
+    ref[:, 2, 2] = ref[:, 3, 3] = (S1 * np.conj(S2)).real
+    ref[:, 2, 3] = (S2 * np.conj(S1)).imag
+    ref[:, 3, 2] = -ref[:, 2, 3]
+    assert np.abs(M - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_mueller_pure_matrix_identities():
+    """Any single amplitude matrix gives a non-depolarising Mueller matrix:
+    sum_ij M_ij^2 = 4 M11^2, and M11 >= |M_ij|; J = I gives M = I; swapping
+    the two field components (S2 = S1 = 0, S3 = S4 = 1) flips Q and V."""
+    rng = np.random.default_rng(11)
+    S = rng.standard_normal((4, 50)) + 1j * rng.standard_normal((4, 50))
+    M = observables.mueller_from_amplitudes(*S)
+    assert np.allclose(np.sum(M ** 2, axis=(1, 2)), 4 * M[:, 0, 0] ** 2, rtol=1e-12)
+    assert np.all(M[:, :1, :1] >= np.abs(M).max(axis=(1, 2))[:, None, None] - 1e-12)
+    one, zero = np.ones(1), np.zeros(1)
+    assert np.allclose(observables.mueller_from_amplitudes(one, one, zero, zero)[0], np.eye(4),
+                       atol=1e-14)
+    swap = observables.mueller_from_amplitudes(zero, zero, one, one)[0]
+    assert np.allclose(swap, np.diag([1.0, -1.0, 1.0, -1.0]), atol=1e-14)
+
+
+def test_asymmetry_quadrature_against_mie_series():
+    """<cos theta> from the far field on the sphere quadrature, with the Mie
+    amplitudes as the far field (x-polarised incidence:
+    |F|^2 = |S2|^2 cos^2 phi + |S1|^2 sin^2 phi), equals the Mie series g."""
+    x, m = 4.0, 1.5 + 0.05j
+    dirs, w = observables.sphere_quadrature(64, 16)
+    th = np.rad2deg(np.arccos(np.clip(dirs[:, 2], -1, 1)))
+    phi = np.arctan2(dirs[:, 1], dirs[:, 0])
+    S1, S2 = mie.amplitudes(x, m, th)
+    # a field with the right |F|^2: components along theta_hat and phi_hat
+    F = np.stack([S2 * np.cos(phi), S1 * np.sin(phi), np.zeros_like(S1)], axis=1)
+    g, gvec = observables.asymmetry_from_farfield(F, dirs, w, (0, 0, 1))
+    assert abs(g - mie.efficiencies(x, m)[3]) < 1e-10
+    assert abs(gvec[0]) < 1e-12 and abs(gvec[1]) < 1e-12
+    # a single dipole scatters symmetrically: g = 0
+    P = np.array([[1.0 + 0.5j], [0.0], [0.0]])
+    Fd = observables.farfield(P, np.zeros((1, 3)), 0.4, dirs)
+    assert abs(observables.asymmetry_from_farfield(Fd, dirs, w, (0, 0, 1))[0]) < 1e-14
+
+
+def test_ypol_from_xpol_by_rotation_symmetry():
+    """Sphere lattice (invariant under the 90 degree rotation about z): the
+    y-polarised far field equals the rotated x-polarised one (Sec. 3.1's use
+    of the spherical symmetry), to round-off with the exact solutions."""
+    occ = inputs.sphere(6)
+    xs = 1.5
+    prob = dda.Problem(occ, [1.5 + 0.1j], lattice.kd_volume_corrected(xs, int((occ > 0).sum())))
+    th = inputs.angles_deg(19)
+    res = dda.simulate(prob, xs, "ldr", method="dense")
+    Px, Py = res["P"]
+    d = observables.plane_dirs(th)
+    Fy = observables.farfield(Py, prob.pos, prob.kd, d)
+    d_rot = np.stack([d[:, 1], -d[:, 0], d[:, 2]], axis=1)      # R^-1 n
+    Fy_sym = observables.ypol_farfield_by_symmetry(observables.farfield(Px, prob.pos, prob.kd, d_rot))
+    assert np.abs(Fy_sym - Fy).max() < 1e-12 * np.abs(Fy).max()
+    Fx = observables.farfield(Px, prob.pos, prob.kd, d)
+    M2 = observables.mueller_plane(Fx, Fy, th)
+    Ms = observables.mueller_plane(Fx, Fy_sym, th)
+    assert np.abs(M2 - Ms).max() < 1e-12 * np.abs(M2).max()
