@@ -180,6 +180,26 @@ int dda_solve(dda_t h, const dda_solve_opts* opts, int nrhs, const double* prop_
               dda_solve_info* info);
 
 /*
+ * dda_solve_batch -- dda_solve for all nrhs right-hand sides at once (QMR-CS
+ * only; no counterpart in the paper, which solves one right-hand side at a
+ * time): every QMR step is one launch per product pass and per solver kernel
+ * for all right-hand sides (the products of converged ones are skipped), and
+ * the host reads the solver scalars every 8 steps instead of every step.  The
+ * arithmetic per right-hand side is that of dda_solve with QMR-CS (the
+ * iterates agree to rounding), and FP32_REFINED runs the same refinement per
+ * right-hand side (inner complex64 solves of all unfinished right-hand sides
+ * together, then one batched FP64 residual product).  Arguments as dda_solve
+ * (no history); opts->solver must be DDA_QMR_CS (else DDA_ERR_ARG).
+ * info[r].seconds is the wall time of the whole call.  Allocates per call
+ * about nrhs x (8 complex64 + 4 complex128) x 3 N_occ (FP32_REFINED) or
+ * nrhs x 8 complex128 x 3 N_occ (FP64) of device memory, kept by the handle,
+ * and grows the product buffers to up to 64 right-hand sides.
+ * Synchronises the stream.
+ */
+int dda_solve_batch(dda_t h, const dda_solve_opts* opts, int nrhs, const double* prop_host,
+                    const double* pol_host, void* P_dev, dda_solve_info* info);
+
+/*
  * dda_scatter -- scattering quantities of Sec. 3.1 from P (FP64 sums).
  *   pol_prescription : the prescription P was computed with (Q_abs needs alpha).
  *   P_dev     : device [nrhs][3][N_occ] complex128.

@@ -62,8 +62,10 @@ int ensure_work(dda_t h, Work<R>& w) {
       return dda_fail(h, DDA_ERR_OOM, "cannot allocate FFT work buffer B2");
     }
   }
+  if (w.cap < 1) w.cap = 1;
   return DDA_OK;
 }
+
 
 template <typename R>
 void free_work(Work<R>& w) {
@@ -139,6 +141,43 @@ bool finite_all(const double* p, int n) {
 }
 
 }  // namespace
+
+namespace dda {
+
+// Several right-hand sides per launch need B1/B2 for each: grow to
+// min(want, 64, what a quarter of the free device memory holds).
+template <typename R>
+int ensure_work_cap(dda_t h, Work<R>& w, int want) {
+  int rc = ensure_work<R>(h, w);
+  if (rc != DDA_OK) return rc;
+  if (want <= w.cap) return DDA_OK;
+  const Geom& g = h->g;
+  const size_t per = (size_t)(g.b1() + g.b2()) * sizeof(cpx<R>);
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
+  long long fit = (long long)((fr / 4 + (size_t)w.cap * per) / per);
+  int target = want < 64 ? want : 64;
+  if (fit < target) target = (int)(fit > 1 ? fit : 1);
+  if (target <= w.cap) return DDA_OK;
+  cpx<R>* b1 = nullptr;
+  cpx<R>* b2 = nullptr;
+  if (cudaMalloc(&b1, (size_t)target * g.b1() * sizeof(cpx<R>)) != cudaSuccess ||
+      cudaMalloc(&b2, (size_t)target * g.b2() * sizeof(cpx<R>)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b1);
+    return DDA_OK;            // keep the current capacity: the product runs in more chunks
+  }
+  cudaFree(w.B1);
+  cudaFree(w.B2);
+  w.B1 = b1;
+  w.B2 = b2;
+  w.cap = target;
+  return DDA_OK;
+}
+template int ensure_work_cap<float>(dda_t, Work<float>&, int);
+template int ensure_work_cap<double>(dda_t, Work<double>&, int);
+
+}  // namespace dda
 
 int dda_beta_internal(dda_t h, int presc, int nrhs, const double* prop, const double* pol) {
   if (presc < DDA_CM || presc > DDA_CLDR) return dda_fail(h, DDA_ERR_ARG, "unknown polarizability prescription");
@@ -285,10 +324,14 @@ static int matvec_common(dda_t h, int prec, const void* x, void* y, int nrhs, bo
   cudaError_t e;
   if (prec == DDA_FP64) {
     if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "FP64 D-matrix not built");
+    const int rc = ensure_work_cap<double>(h, h->w64, nrhs);
+    if (rc != DDA_OK) return rc;
     e = launch_matvec<double>(h->g, h->lat(), h->w64, h->w64.beta, h->n_mat, (const c128*)x,
                               (c128*)y, nrhs, adjoint, h->stream);
   } else if (prec == DDA_FP32_REFINED) {
     if (!h->w32.have_D) return dda_fail(h, DDA_ERR_STATE, "FP32 D-matrix not built");
+    const int rc = ensure_work_cap<float>(h, h->w32, nrhs);
+    if (rc != DDA_OK) return rc;
     e = launch_matvec<float>(h->g, h->lat(), h->w32, h->w32.beta, h->n_mat, (const c64*)x,
                              (c64*)y, nrhs, adjoint, h->stream);
   } else {
@@ -321,6 +364,22 @@ extern "C" int dda_solve(dda_t h, const dda_solve_opts* o, int nrhs, const doubl
   if (o->prec == DDA_FP32_REFINED && !h->w32.have_D)
     return dda_fail(h, DDA_ERR_STATE, "FP32 D-matrix not built");
   return dda_solve_internal(h, o, nrhs, prop, pol, P_dev, hist, hist_len, info);
+}
+
+extern "C" int dda_solve_batch(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
+                               const double* pol, void* P_dev, dda_solve_info* info) {
+  if (!h) return DDA_ERR_ARG;
+  if (!o || !prop || !pol || !P_dev || !info || nrhs < 1)
+    return dda_fail(h, DDA_ERR_ARG, "bad dda_solve_batch arguments");
+  if (o->solver != DDA_QMR_CS) return dda_fail(h, DDA_ERR_ARG, "dda_solve_batch runs QMR-CS only");
+  if (o->prec != DDA_FP64 && o->prec != DDA_FP32_REFINED) return dda_fail(h, DDA_ERR_ARG, "unknown precision");
+  if (!(o->tol > 0.0) || o->maxiter < 1) return dda_fail(h, DDA_ERR_ARG, "tol must be > 0 and maxiter >= 1");
+  if (o->prec == DDA_FP32_REFINED && !(o->inner_tol > 0.0 && o->inner_tol < 1.0))
+    return dda_fail(h, DDA_ERR_ARG, "inner_tol must be in (0, 1)");
+  if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "FP64 D-matrix not built");
+  if (o->prec == DDA_FP32_REFINED && !h->w32.have_D)
+    return dda_fail(h, DDA_ERR_STATE, "FP32 D-matrix not built");
+  return dda_solve_batch_internal(h, o, nrhs, prop, pol, P_dev, info);
 }
 
 extern "C" int dda_scatter(dda_t h, int presc, const void* P_dev, int nrhs, const double* prop,
@@ -504,6 +563,7 @@ extern "C" int dda_free(dda_t h) {
   free_work(h->w32);
   cudaFree(h->d_row_off); cudaFree(h->d_xi); cudaFree(h->d_mat);
   cudaFree(h->sv); cudaFree(h->d_part); cudaFree(h->d_mvpart); cudaFree(h->d_scal); cudaFreeHost(h->h_scal);
+  batch_free(h);
   cudaFree(h->d_tab); cudaFree(h->d_fpart); cudaFree(h->d_coll);
   cudaGetLastError();
   delete h;

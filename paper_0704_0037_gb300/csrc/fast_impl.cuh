@@ -13,16 +13,18 @@ cudaError_t run_pass(int pass, const FastArgs& a) {
   switch (pass) {
     case FP_XFWD:
       return P::xfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.lat, (const cpx<R>*)a.beta, a.n_occ,
-                     a.nrows, tw, a.adj, a.st);
+                     a.nrows, tw, a.adj, a.nrhs, a.bstride, a.skip, a.st);
     case FP_YFWD:
-      return P::yfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.st);
+      return P::yfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.nrhs, a.skip, a.st);
     case FP_ZCONV:
-      return P::zconv((cpx<R>*)a.out, (const cpx<R>*)a.D, a.nz, a.Mx, a.My, tw, a.st);
+      return P::zconv((cpx<R>*)a.out, (const cpx<R>*)a.D, a.nz, a.Mx, a.My, tw, a.nrhs, a.skip,
+                      a.st);
     case FP_YINV:
-      return P::yinv((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.st);
+      return P::yinv((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.nrhs, a.skip, a.st);
     case FP_XINV:
       return P::xinv((const cpx<R>*)a.in, (const cpx<R>*)a.x, (cpx<R>*)a.out, a.lat,
-                     (const cpx<R>*)a.beta, a.n_occ, a.nrows, tw, a.adj, a.dotp, a.st);
+                     (const cpx<R>*)a.beta, a.n_occ, a.nrows, tw, a.adj, a.dotp, a.nrhs, a.bstride,
+                     a.skip, a.st);
     case FP_XFULL:
       return P::xfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.ny, a.My, tw, a.st);
     case FP_SFULL:

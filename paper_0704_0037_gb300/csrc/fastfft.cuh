@@ -43,8 +43,9 @@ template <typename R, int M1, int M2, int T>
 __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restrict__ in,
                                                           cpx<R>* __restrict__ out, int ny, int nz,
                                                           int Mx, const cpx<R>* __restrict__ tw,
-                                                          int msign) {
+                                                          int msign, const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  if (skip && skip[blockIdx.z / 3]) return;     // right-hand side already converged
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* s = s_tw + M;
@@ -97,8 +98,10 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
 template <typename R, int M1, int M2, int T>
 __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yinv(const cpx<R>* __restrict__ in,
                                                           cpx<R>* __restrict__ out, int ny, int nz,
-                                                          int Mx, const cpx<R>* __restrict__ tw) {
+                                                          int Mx, const cpx<R>* __restrict__ tw,
+                                                          const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  if (skip && skip[blockIdx.z / 3]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* s = s_tw + M;
@@ -149,8 +152,11 @@ template <typename R, int M1, int M2, int T>
 __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict__ B2,
                                                            const cpx<R>* __restrict__ D, int nz,
                                                            int Mx, int My,
-                                                           const cpx<R>* __restrict__ tw) {
+                                                           const cpx<R>* __restrict__ tw,
+                                                           const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  if (skip && skip[blockIdx.z]) return;
+  B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* s = s_tw + M;                      // [3][M][T]
@@ -278,17 +284,21 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const cpx<R>* __res
                                                           cpx<R>* __restrict__ B1, LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
-                                                          const cpx<R>* __restrict__ tw) {
+                                                          const cpx<R>* __restrict__ tw,
+                                                          int bstride, const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* a = s_tw + M;                      // [T][LD]
-  const int c = blockIdx.y;
+  // blockIdx.y = 3 * (right-hand side) + component; vectors [rhs][3][n_occ]
+  const int cc = blockIdx.y, c = cc % 3;
+  if (skip && skip[cc / 3]) return;
+  beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
   load_tw(s_tw, tw, M, NT);
   for (int i = threadIdx.x; i < T * LD; i += NT) a[i] = zero<R>();
   __syncthreads();
-  const cpx<R>* xc = x + (long long)c * n_occ;
+  const cpx<R>* xc = x + (long long)cc * n_occ;
   {
     // one warp per row: the dipoles of a row are contiguous in x
     constexpr int NW = NT / 32;
@@ -333,7 +343,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const cpx<R>* __res
     for (int k2 = 0; k2 < M2; ++k2) at[k1 + M1 * k2] = u[k2];
   }
   __syncthreads();
-  cpx<R>* out = B1 + (long long)c * nrows * M;
+  cpx<R>* out = B1 + (long long)cc * nrows * M;
   for (int idx = threadIdx.x; idx < T * M; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
     const int row = r0 + tt;
@@ -351,15 +361,18 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
                                                           const cpx<R>* __restrict__ tw,
-                                                          double* __restrict__ dotp) {
+                                                          double* __restrict__ dotp, int bstride,
+                                                          const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* a = s_tw + M;                      // [T][LD]
-  const int c = blockIdx.y;
+  const int cc = blockIdx.y, c = cc % 3;     // 3 * (right-hand side) + component
+  if (skip && skip[cc / 3]) return;
+  beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
   load_tw(s_tw, tw, M, NT);
-  const cpx<R>* in = B1 + (long long)c * nrows * M;
+  const cpx<R>* in = B1 + (long long)cc * nrows * M;
   for (int idx = threadIdx.x; idx < T * M; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
     const int row = r0 + tt;
@@ -394,8 +407,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
     for (int i = 0; i < M1; ++i) at[j + M2 * i] = v[i];
   }
   __syncthreads();
-  const cpx<R>* xc = x + (long long)c * n_occ;
-  cpx<R>* yc = y + (long long)c * n_occ;
+  const cpx<R>* xc = x + (long long)cc * n_occ;
+  cpx<R>* yc = y + (long long)cc * n_occ;
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double dre = 0.0, dim = 0.0;       // partial x^T y (bilinear) when dotp is set
@@ -513,47 +526,52 @@ template <typename R, int M1, int M2>
 struct Passes {
   static constexpr int M = M1 * M2, T = kT<R>, NT = T * kQ<M1, M2>;
   static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                          const cpx<R>* tw, cudaStream_t st) {
+                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
-    fk_yfwd<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3), NT, sm, st>>>(in, out, ny, nz, Mx, tw,
-                                                                         0);
+    fk_yfwd<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3 * nrhs), NT, sm, st>>>(in, out, ny, nz,
+                                                                                Mx, tw, 0, skip);
     count_launch();
     return cudaGetLastError();
   }
   static cudaError_t yinv(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                          const cpx<R>* tw, cudaStream_t st) {
+                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yinv<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
-    fk_yinv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3), NT, sm, st>>>(in, out, ny, nz, Mx, tw);
+    fk_yinv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3 * nrhs), NT, sm, st>>>(in, out, ny, nz,
+                                                                                Mx, tw, skip);
     count_launch();
     return cudaGetLastError();
   }
   static cudaError_t zconv(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
-                           cudaStream_t st) {
+                           int nrhs, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + 3 * M * T) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_zconv<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
     // two ~106 KB blocks per SM need the largest shared-memory carveout
     e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, T>);
     if (e != cudaSuccess) return e;
-    fk_zconv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, My), NT, sm, st>>>(B2, D, nz, Mx, My, tw);
+    fk_zconv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, My, nrhs), NT, sm, st>>>(B2, D, nz, Mx, My, tw,
+                                                                              skip);
     count_launch();
     return cudaGetLastError();
   }
   static cudaError_t xfwd(const cpx<R>* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,
-                          long long n_occ, int nrows, const cpx<R>* tw, bool adj, cudaStream_t st) {
+                          long long n_occ, int nrows, const cpx<R>* tw, bool adj, int nrhs,
+                          int bstride, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
-    const dim3 grid((nrows + T - 1) / T, 3);
+    const dim3 grid((nrows + T - 1) / T, 3 * nrhs);
     cudaError_t e;
     if (adj) {
       if ((e = set_smem(fk_xfwd<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
-      fk_xfwd<R, M1, M2, T, true><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw);
+      fk_xfwd<R, M1, M2, T, true><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
+                                                        bstride, skip);
     } else {
       if ((e = set_smem(fk_xfwd<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
-      fk_xfwd<R, M1, M2, T, false><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw);
+      fk_xfwd<R, M1, M2, T, false><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
+                                                         bstride, skip);
     }
     count_launch();
     return cudaGetLastError();
@@ -579,29 +597,31 @@ struct Passes {
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
     fk_yfwd<R, M1, M2, T><<<dim3((nlines + T - 1) / T, n_outer, 1), NT, sm, st>>>(in, out, M, n_outer,
-                                                                                 stride, tw, msign);
+                                                                                 stride, tw, msign,
+                                                                                 nullptr);
     count_launch();
     return cudaGetLastError();
   }
   static cudaError_t xinv(const cpx<R>* B1, const cpx<R>* x, cpx<R>* y, const LatticeDev& lat,
                           const cpx<R>* beta, long long n_occ, int nrows, const cpx<R>* tw, bool adj,
-                          double* dotp, cudaStream_t st) {
+                          double* dotp, int nrhs, int bstride, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
-    const dim3 grid((nrows + T - 1) / T, 3);
+    const dim3 grid((nrows + T - 1) / T, 3 * nrhs);
     cudaError_t e;
     if (adj) {
       if ((e = set_smem(fk_xinv<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
       fk_xinv<R, M1, M2, T, true><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
-                                                        dotp);
+                                                        dotp, bstride, skip);
     } else {
       if ((e = set_smem(fk_xinv<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
       fk_xinv<R, M1, M2, T, false><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
-                                                         dotp);
+                                                         dotp, bstride, skip);
     }
     count_launch();
     return cudaGetLastError();
   }
-  // number of blocks (partials written to dotp) of xinv for nrows rows
+  // number of blocks (partials written to dotp) of xinv for nrows rows, per
+  // right-hand side (the partials of right-hand side r follow those of r - 1)
   static int xinv_blocks(int nrows) { return 3 * ((nrows + T - 1) / T); }
 };
 

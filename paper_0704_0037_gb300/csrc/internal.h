@@ -68,22 +68,33 @@ struct Work {
   cpx<R>* D = nullptr;      // octant of FFT(G)/(Mx My Mz): [6][Mz/2+1][My/2+1][Mx/2+1]
   cpx<R>* beta = nullptr;   // [nrhs][n_mat][3]
   bool have_D = false;
+  int cap = 0;              // right-hand sides B1 and B2 hold
 };
 
+// Grow the product buffers of w to hold min(want, what fits) right-hand
+// sides (api.cu); at least one.
+template <typename R> int ensure_work_cap(dda_t h, Work<R>& w, int want);
+
 // Launch helpers (matvec.cu)
-// With dotp != null (nrhs == 1), the last pass also writes per-block partials
-// of x^T y to dotp when it can (*dot_nb = their count, else 0).
+// y = A x for nrhs right-hand sides ([nrhs][3][n_occ]), in chunks of w.cap
+// right-hand sides per launch.  With dotp != null the last pass also writes
+// per-block partials of x^T y when it can: *dot_nb = their count per
+// right-hand side (those of right-hand side r start at dotp + 2 r *dot_nb),
+// else 0.  skip (device, nrhs ints, or null): right-hand sides with a nonzero
+// entry are left untouched.
 template <typename R>
 cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, const cpx<R>* beta,
                           int n_mat, const cpx<R>* x, cpx<R>* y, int nrhs, bool adjoint,
-                          cudaStream_t st, double* dotp = nullptr, int* dot_nb = nullptr);
+                          cudaStream_t st, double* dotp = nullptr, int* dot_nb = nullptr,
+                          const int* skip = nullptr);
 
 template <typename R>
 cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const FftPlan& p,
                          const cpx<R>* tw, bool inverse, int n_in, int n_out, int nt, int n_outer,
                          int n_batch, bool contig, long long in_sm, long long in_st,
                          long long in_so, long long in_sb, long long out_sm, long long out_st,
-                         long long out_so, long long out_sb, cudaStream_t st);
+                         long long out_so, long long out_sb, cudaStream_t st,
+                         const int* skip = nullptr);
 
 FftPlan make_plan(int M);
 int smooth_size(int lo);
@@ -115,6 +126,7 @@ struct dda_ctx {
   size_t sv_bytes = 0;
   double* d_part = nullptr;       // reduction partials
   double* d_mvpart = nullptr;     // per-block x^T y partials of the product's last pass
+  void* bm = nullptr;             // batched-solver state (krylov.cu)
   void* d_scal = nullptr;         // device scalar state
   void* h_scal = nullptr;         // pinned host mirror
   // scatter scratch
@@ -141,6 +153,10 @@ int dda_beta_internal(dda_t h, int presc, int nrhs, const double* prop, const do
 // D-matrix (dmatrix.cu)
 int dda_build_D_internal(dda_t h, bool want32);
 // solvers (krylov.cu)
+// all right-hand sides at once (QMR-CS only); frees with batch_free (krylov.cu)
+int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
+                             const double* pol, void* P_dev, dda_solve_info* info);
+void batch_free(dda_t h);
 int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                        const double* pol, void* P_dev, double* hist, int hist_len,
                        dda_solve_info* info);
@@ -193,6 +209,12 @@ struct FastArgs {
   int msign;
   double* dotp;          // FP_XINV: per-block partials of x^T y (re, im), or null
   cudaStream_t st;
+  // right-hand sides in one launch: vectors [nrhs][3][n_occ], buffers
+  // [nrhs][3][...], beta of right-hand side r at beta + r * bstride; a
+  // right-hand side with skip[r] != 0 is left untouched (null: none skipped)
+  int nrhs = 1;
+  int bstride = 0;
+  const int* skip = nullptr;
 };
 // number of (re, im) partials FP_XINV writes to dotp for nrows rows
 inline int fast_xinv_blocks(int nrows, bool fp32) { return 3 * ((nrows + (fp32 ? 16 : 8) - 1) / (fp32 ? 16 : 8)); }

@@ -26,6 +26,11 @@ namespace dda {
 constexpr int kNB = 1024;     // max blocks of a vector kernel (partials per slot)
 constexpr int kSlots = 8;     // doubles per block in the partials array
 constexpr int kVT = 256;      // threads of vector kernels
+constexpr long long kPS = (long long)kSlots * kNB;   // partials per right-hand side
+// Batched launches: vector kernels take right-hand side blockIdx.y (vectors
+// [nrhs][n], partials at part + r * kPS, scalars at s + r), scalar kernels
+// take right-hand side blockIdx.x (one block each).  Single right-hand-side
+// launches have gridDim.y = 1 and one block, i.e. r = 0.
 
 // QMR-CS scalars (see the QMR-CS section)
 struct QmrScal {
@@ -35,7 +40,7 @@ struct QmrScal {
 
 struct Scal {
   double bnorm, res, sres, tol;
-  int done, status, half, pad;
+  int done, status, half, iters;   // iters: steps taken (batched QMR)
   c128 alpha, beta_k, beta_next, inv_beta, t, tau, delta, eps, inv_gamma, s1, s2;
   double c1, c2;
   c128 rho, rho_prev, omega, bstep;
@@ -168,6 +173,8 @@ template <typename R> __device__ __forceinline__ cpx<R> cs(c128 a) { return mk<R
 template <typename R, bool HERM>
 __global__ void __launch_bounds__(kVT) k_dot(const cpx<R>* __restrict__ a, const cpx<R>* __restrict__ b,
                                              long long n, double* part, int slot, const Scal* s) {
+  a += blockIdx.y * n; b += blockIdx.y * n; part += blockIdx.y * kPS;
+  if (s) s += blockIdx.y;
   if (s && s->done) return;
   Acc<R> a0, a1;
   VLOOP(n) {
@@ -184,6 +191,8 @@ __global__ void __launch_bounds__(kVT) k_dot(const cpx<R>* __restrict__ a, const
 template <typename R>
 __global__ void __launch_bounds__(kVT) k_norms(const cpx<R>* __restrict__ a, long long n, double* part,
                                                const Scal* s) {
+  a += blockIdx.y * n; part += blockIdx.y * kPS;
+  if (s) s += blockIdx.y;
   if (s && s->done) return;
   double v[3] = {0.0, 0.0, 0.0};
   VLOOP(n) {
@@ -256,13 +265,19 @@ __global__ void k_pfinal(const cpx<R>* __restrict__ x, c128* __restrict__ P, con
 // convergence rate in complex64 for large size parameters; this form tracks
 // the FP64 iteration.  Scalars live in QmrScal (FP64), vectors in R.
 
-// part: slots 0/1 = b^T b, slot 2 = |b|^2 (k_norms)
-__global__ void k_qmr_init(Scal* s, const double* part, int nb, double tol) {
+// part: slots 0/1 = b^T b, slot 2 = |b|^2 (k_norms).  tols (device, or null:
+// tol for all) per right-hand side; off (device, or null) marks right-hand
+// sides that start done; mask (device, or null) mirrors the done flags.
+__global__ void k_qmr_init(Scal* s, const double* part, int nb, double tol, const double* tols,
+                           const int* off, int* mask) {
+  const int rr = blockIdx.x;
+  s += rr; part += rr * kPS;
   const c128 bb = cfin(part, 0, nb);
   const double bn2 = fin(part, 2, nb);
   if (threadIdx.x) return;
   QmrScal& q = s->q;
-  s->tol = tol;
+  s->tol = tols ? tols[rr] : tol;
+  s->iters = 0;
   s->bnorm = sqrt(bn2);
   s->res = 1.0;
   s->done = 0; s->half = 0;
@@ -278,6 +293,8 @@ __global__ void k_qmr_init(Scal* s, const double* part, int nb, double tol) {
   if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
   else if (!isfinite(bn2) || !cfinite(bb)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
   else if (sqrt(cabs2(q.delta)) < 1e-30) { s->done = 1; s->status = DDA_BREAKDOWN; }
+  if (off && off[rr]) { s->done = 1; s->status = DDA_OK; }
+  if (mask) mask[rr] = s->done;
 }
 
 // v_1 = b / rho_1, p_1 = v_1, r = b, x = d = s = 0
@@ -286,6 +303,9 @@ __global__ void k_qmr_start(const cpx<R>* __restrict__ b, cpx<R>* __restrict__ v
                             cpx<R>* __restrict__ p, cpx<R>* __restrict__ r, cpx<R>* __restrict__ x,
                             cpx<R>* __restrict__ d, cpx<R>* __restrict__ sv, long long n,
                             const Scal* s) {
+  const long long o = blockIdx.y * n;
+  b += o; v += o; p += o; r += o; x += o; d += o; sv += o;
+  s += blockIdx.y;
   const R ir = (R)s->q.inv_rho;
   const cpx<R> z = mk<R>(0, 0);
   VLOOP(n) {
@@ -295,8 +315,11 @@ __global__ void k_qmr_start(const cpx<R>* __restrict__ b, cpx<R>* __restrict__ v
   }
 }
 
-// eps_i = p^T A p from partials (entry (k, i) at part[k * ks + i * is]); beta_i
-__global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is, int nb) {
+// eps_i = p^T A p from partials (entry (k, i) at part[k * ks + i * is],
+// right-hand side r's partials at part + r * rs); beta_i
+__global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is, long long rs,
+                        int nb) {
+  s += blockIdx.x; part += blockIdx.x * rs;
   if (s->done) return;
   double a[2];
   fin_k<2>(part, ks, is, nb, a);
@@ -314,6 +337,7 @@ __global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is,
 template <typename R>
 __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, cpx<R>* __restrict__ v,
                                                 long long n, const Scal* s, double* part) {
+  pt += blockIdx.y * n; v += blockIdx.y * n; part += blockIdx.y * kPS; s += blockIdx.y;
   if (s->done) return;
   const cpx<R> be = cs<R>(s->q.beta);
   Acc<R> q0, q1, q2;
@@ -332,6 +356,7 @@ __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, c
 // rho_{i+1}, delta_{i+1}, the quasi-minimisation scalars of step i and the
 // coefficients of the update and of the next direction
 __global__ void k_qmr_b(Scal* s, const double* part, int nb) {
+  s += blockIdx.x; part += blockIdx.x * kPS;
   if (s->done) return;
   double f[3];
   fin_k<3>(part, kNB, 1, nb, f);
@@ -373,6 +398,9 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* 
                                                 cpx<R>* __restrict__ sv, cpx<R>* __restrict__ x,
                                                 cpx<R>* __restrict__ r, long long n, const Scal* s,
                                                 double* part) {
+  const long long o = blockIdx.y * n;
+  v += o; p += o; pt += o; d += o; sv += o; x += o; r += o;
+  part += blockIdx.y * kPS; s += blockIdx.y;
   if (s->done) return;
   const QmrScal& q = s->q;
   const cpx<R> et = cs<R>(q.eta), cp = cs<R>(q.cp);
@@ -396,17 +424,24 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* 
   block_store<1>(a, part, 0);
 }
 
-__global__ void k_qmr_c(Scal* s, const double* part, int nb) {
-  if (s->done) return;
+__global__ void k_qmr_c(Scal* s, const double* part, int nb, int* mask) {
+  const int rr = blockIdx.x;
+  s += rr; part += rr * kPS;
+  if (s->done) {
+    if (mask && threadIdx.x == 0) mask[rr] = 1;
+    return;
+  }
   double f[1];
   fin_k<1>(part, kNB, 1, nb, f);
   const double rn2 = f[0];
   if (threadIdx.x) return;
   const double res = sqrt(rn2) / s->bnorm;
   s->res = res;
+  s->iters++;
   if (!isfinite(res)) { s->status = DDA_ERR_NONFINITE; s->done = 1; }
   else if (res < s->tol) { s->status = DDA_OK; s->done = 1; }
   else if (s->half) { s->status = DDA_BREAKDOWN; s->done = 1; }
+  if (mask) mask[rr] = s->done;
 }
 
 // ---------------------------------------------------------------- Bi-CG-CS (COCG)
@@ -766,7 +801,7 @@ int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, do
   k_norms<R><<<nb, kVT, 0, st>>>(b, n, part, nullptr); count_launch();
   if (solver == DDA_QMR_CS) {
     cpx<R>*v = vec[0], *p = vec[1], *pt = vec[2], *d = vec[3], *sv = vec[4], *r = vec[5];
-    k_qmr_init<<<1, kVT, 0, st>>>(s, part, nb, tol); count_launch();
+    k_qmr_init<<<1, kVT, 0, st>>>(s, part, nb, tol, nullptr, nullptr, nullptr); count_launch();
     k_qmr_start<R><<<nb, kVT, 0, st>>>(b, v, p, r, x, d, sv, n, s); count_launch();
     LK(h);
     RK(sync_read(ru));
@@ -775,15 +810,15 @@ int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, do
       int dnb = 0;
       RK(matvec<R>(ru, p, pt, false, h->d_mvpart, &dnb));
       if (dnb > 0) {
-        k_qmr_a<<<1, kVT, 0, st>>>(s, h->d_mvpart, 1, 2, dnb); count_launch();
+        k_qmr_a<<<1, kVT, 0, st>>>(s, h->d_mvpart, 1, 2, 0, dnb); count_launch();
       } else {
         k_dot<R, false><<<nb, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
-        k_qmr_a<<<1, kVT, 0, st>>>(s, part, kNB, 1, nb); count_launch();
+        k_qmr_a<<<1, kVT, 0, st>>>(s, part, kNB, 1, 0, nb); count_launch();
       }
       k_qmr_k1<R><<<nb, kVT, 0, st>>>(pt, v, n, s, part); count_launch();
       k_qmr_b<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
       k_qmr_k2<R><<<nb, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part); count_launch();
-      k_qmr_c<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_qmr_c<<<1, kVT, 0, st>>>(s, part, nb, nullptr); count_launch();
       LK(h);
       ru.iters++;
       RK(sync_read(ru));
@@ -1028,6 +1063,409 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
       for (int i = 0; i < hist_len; ++i) hr[i] = i < (int)hv.size() ? hv[i] : -1.0;
     }
     if (status_rank(st_rhs) > status_rank(worst)) worst = st_rhs;
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------- batched QMR-CS
+// All right-hand sides of one particle advance together: every QMR step is
+// one launch per product pass and per solver kernel for all of them (the
+// right-hand side is the grid's y index), converged ones are skipped through
+// a device mask, and the host reads the scalars every kSyncEvery steps only
+// (a converged right-hand side's kernels are no-ops in between).
+namespace dda {
+namespace {
+
+constexpr int kSyncEvery = 8;
+
+// b32[r] = (complex64)(a64[r] * scl[r]) for right-hand sides with off[r] == 0
+__global__ void k_to32s_b(const c128* __restrict__ a, c64* __restrict__ b, long long n,
+                          const double* __restrict__ scl, const int* __restrict__ off) {
+  const int rr = blockIdx.y;
+  if (off[rr]) return;
+  a += rr * n; b += rr * n;
+  const double sc = scl[rr];
+  VLOOP(n) b[i] = mk<float>((float)(a[i].x * sc), (float)(a[i].y * sc));
+}
+// x64[r] += scl[r] * d32[r]
+__global__ void k_axpy64_b(c128* __restrict__ x, const c64* __restrict__ d, long long n,
+                           const double* __restrict__ scl, const int* __restrict__ off) {
+  const int rr = blockIdx.y;
+  if (off[rr]) return;
+  x += rr * n; d += rr * n;
+  const double sc = scl[rr];
+  VLOOP(n) x[i] = mk<double>(x[i].x + sc * (double)d[i].x, x[i].y + sc * (double)d[i].y);
+}
+// r = b - w with |r|^2 partials (slot 2) per right-hand side
+__global__ void __launch_bounds__(kVT) k_resid_b(const c128* __restrict__ b, const c128* __restrict__ w,
+                                                 c128* __restrict__ r, long long n, double* part,
+                                                 const int* __restrict__ off) {
+  const int rr = blockIdx.y;
+  if (off && off[rr]) return;
+  b += rr * n; w += rr * n; r += rr * n; part += rr * kPS;
+  double acc[3] = {0.0, 0.0, 0.0};
+  VLOOP(n) {
+    const c128 t = b[i] - w[i];
+    r[i] = t;
+    acc[2] += t.x * t.x + t.y * t.y;
+  }
+  block_store<3>(acc, part, 0);
+}
+__global__ void k_take_norms_b(Scal* s, const double* part, int nb, const int* off) {
+  const int rr = blockIdx.x;
+  if (off && off[rr]) return;
+  const double v = fin(part + rr * kPS, 2, nb);
+  if (threadIdx.x == 0) s[rr].sres = sqrt(v);
+}
+
+// Device and pinned memory of one batched solve, grown on demand.
+struct BatchMem {
+  int cap = 0;
+  Scal* ds = nullptr;        // [cap] scalars
+  Scal* hs = nullptr;        // pinned mirror
+  double* part = nullptr;    // [cap][kPS] partials
+  double* mvpart = nullptr;  // [cap][2 * xinv blocks] product partials
+  int* mask = nullptr;       // [cap] done flags (skip in the product)
+  int* off = nullptr;        // [cap] right-hand sides left out of an inner solve
+  double* dvals = nullptr;   // [2 cap]: tolerances, scales
+  int* h_off = nullptr;      // pinned [cap]
+  double* h_vals = nullptr;  // pinned [2 cap]
+  void* sv = nullptr;        // solver vectors
+  size_t sv_bytes = 0;
+};
+
+void bm_release(BatchMem* m) {
+  cudaFree(m->ds); cudaFreeHost(m->hs); cudaFree(m->part); cudaFree(m->mvpart); cudaFree(m->mask);
+  cudaFree(m->off); cudaFree(m->dvals); cudaFreeHost(m->h_off); cudaFreeHost(m->h_vals);
+  cudaFree(m->sv);
+  *m = BatchMem();
+}
+
+int bm_ensure(dda_t h, int nrhs, size_t sv_bytes) {
+  BatchMem* m = (BatchMem*)h->bm;
+  if (!m) {
+    m = new (std::nothrow) BatchMem();
+    if (!m) return dda_fail(h, DDA_ERR_OOM, "batch state");
+    h->bm = m;
+  }
+  if (m->cap < nrhs) {
+    BatchMem fresh;
+    fresh.sv = m->sv; fresh.sv_bytes = m->sv_bytes;
+    m->sv = nullptr; m->sv_bytes = 0;
+    bm_release(m);
+    *m = fresh;
+    const size_t mvp = 2 * (size_t)fast_xinv_blocks(h->g.nrows, false) * nrhs;
+    if (cudaMalloc(&m->ds, nrhs * sizeof(Scal)) != cudaSuccess ||
+        cudaMallocHost(&m->hs, nrhs * sizeof(Scal)) != cudaSuccess ||
+        cudaMalloc(&m->part, (size_t)nrhs * kPS * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&m->mvpart, mvp * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&m->mask, nrhs * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&m->off, nrhs * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&m->dvals, 2 * nrhs * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&m->h_off, nrhs * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&m->h_vals, 2 * nrhs * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      bm_release(m);
+      return dda_fail(h, DDA_ERR_OOM, "batched solver state");
+    }
+    m->cap = nrhs;
+  }
+  if (m->sv_bytes < sv_bytes) {
+    cudaFree(m->sv);
+    m->sv = nullptr; m->sv_bytes = 0;
+    if (cudaMalloc(&m->sv, sv_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "batched solver vectors");
+    }
+    m->sv_bytes = sv_bytes;
+  }
+  return DDA_OK;
+}
+
+struct BRun {
+  dda_t h;
+  cudaStream_t st;
+  long long n;
+  int nb, nrhs;
+  BatchMem* m;
+  // inner-solve stagnation stop (complex64 only): per right-hand side best
+  // residual and the step it was reached at
+  bool stall = false;
+  std::vector<double> best;
+  std::vector<int> best_k;
+};
+
+int bsync(BRun& b) {
+  DDA_CK(b.h, cudaMemcpyAsync(b.m->hs, b.m->ds, b.nrhs * sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
+  DDA_CK(b.h, cudaStreamSynchronize(b.st));
+  return DDA_OK;
+}
+
+// Batched QMR-CS (same kernels and arithmetic as the single right-hand-side
+// path) on b[nrhs][n] -> x; tol per right-hand side from m->dvals (or tol);
+// right-hand sides with off[r] (device) start done.  Returns after every
+// right-hand side is done or maxiter steps.
+template <typename R>
+int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double tol,
+                    const double* tols_dev, const int* off_dev, int maxiter, int* steps_out) {
+  dda_t h = b.h;
+  cudaStream_t st = b.st;
+  const long long n = b.n;
+  const int nb = b.nb, nr = b.nrhs;
+  BatchMem* m = b.m;
+  Scal* s = m->ds;
+  double* part = m->part;
+  cpx<R>*v = vec[0], *p = vec[1], *pt = vec[2], *d = vec[3], *sv = vec[4], *r = vec[5];
+  const dim3 vg(nb, nr);
+  k_norms<R><<<vg, kVT, 0, st>>>(rhs, n, part, nullptr); count_launch();
+  k_qmr_init<<<nr, kVT, 0, st>>>(s, part, nb, tol, tols_dev, off_dev, m->mask); count_launch();
+  k_qmr_start<R><<<vg, kVT, 0, st>>>(rhs, v, p, r, x, d, sv, n, s); count_launch();
+  LK(h);
+  RK(bsync(b));
+  if (b.stall) {
+    b.best.assign(nr, 1e300);
+    b.best_k.assign(nr, 0);
+  }
+  Work<R>& w = work<R>(h);
+  const cpx<R>* beta = w.beta;
+  int k = 0;
+  bool active = false;
+  for (int i = 0; i < nr; ++i) active = active || !m->hs[i].done;
+  while (active && k < maxiter) {
+    for (int j = 0; j < kSyncEvery && k < maxiter; ++j, ++k) {
+      int dnb = 0;
+      cudaError_t e = launch_matvec<R>(h->g, h->lat(), w, beta, h->n_mat, p, pt, nr, false, st,
+                                       m->mvpart, &dnb, m->mask);
+      if (e != cudaSuccess) return dda_cuda_fail(h, e, "batched product");
+      if (dnb > 0) {
+        k_qmr_a<<<nr, kVT, 0, st>>>(s, m->mvpart, 1, 2, 2LL * dnb, dnb); count_launch();
+      } else {
+        k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
+        k_qmr_a<<<nr, kVT, 0, st>>>(s, part, kNB, 1, kPS, nb); count_launch();
+      }
+      k_qmr_k1<R><<<vg, kVT, 0, st>>>(pt, v, n, s, part); count_launch();
+      k_qmr_b<<<nr, kVT, 0, st>>>(s, part, nb); count_launch();
+      k_qmr_k2<R><<<vg, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part); count_launch();
+      k_qmr_c<<<nr, kVT, 0, st>>>(s, part, nb, m->mask); count_launch();
+      LK(h);
+    }
+    RK(bsync(b));
+    active = false;
+    for (int i = 0; i < nr; ++i) {
+      Scal& q = m->hs[i];
+      if (q.done) continue;
+      if (b.stall) {
+        if (q.res < 0.99 * b.best[i]) {
+          b.best[i] = q.res;
+          b.best_k[i] = q.iters;
+        } else if (q.res < 1e-4 && q.iters - b.best_k[i] >= 10) {
+          // stagnated at the complex64 floor: end this inner solve
+          const int one = 1;
+          DDA_CK(h, cudaMemcpyAsync(&s[i].done, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+          DDA_CK(h, cudaMemcpyAsync(&m->mask[i], &one, sizeof(int), cudaMemcpyHostToDevice, st));
+          DDA_CK(h, cudaStreamSynchronize(st));
+          q.done = 1;
+          continue;
+        }
+      }
+      active = true;
+    }
+  }
+  *steps_out = k;
+  return DDA_OK;
+}
+
+}  // namespace
+}  // namespace dda
+
+void batch_free(dda_t h) {
+  if (h && h->bm) {
+    BatchMem* m = (BatchMem*)h->bm;
+    bm_release(m);
+    delete m;
+    h->bm = nullptr;
+  }
+}
+
+int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
+                             const double* pol, void* P_dev, dda_solve_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = dda_beta_internal(h, o->pol, nrhs, prop, pol);
+  if (rc != DDA_OK) return rc;
+  const long long n = 3 * h->g.n_occ;
+  const bool refined = o->prec == DDA_FP32_REFINED;
+  const int nvec = 6;
+  // complex64: the 6 QMR vectors, x32 and the inner right-hand side, then
+  // b64, x64, r64, w64; FP64: the 6 QMR vectors, b64, x64
+  const size_t bytes = refined ? (size_t)nrhs * n * ((nvec + 2) * sizeof(c64) + 4 * sizeof(c128))
+                               : (size_t)nrhs * n * (nvec + 2) * sizeof(c128);
+  rc = bm_ensure(h, nrhs, bytes);
+  if (rc != DDA_OK) return rc;
+  rc = ensure_work_cap<double>(h, h->w64, nrhs);
+  if (rc != DDA_OK) return rc;
+  if (refined) {
+    rc = ensure_work_cap<float>(h, h->w32, nrhs);
+    if (rc != DDA_OK) return rc;
+  }
+  BatchMem* m = (BatchMem*)h->bm;
+  BRun b;
+  b.h = h; b.st = h->stream; b.n = n; b.nrhs = nrhs; b.m = m;
+  long long nbl = (n + 4LL * kVT - 1) / (4LL * kVT);
+  b.nb = (int)(nbl < 1 ? 1 : (nbl > kNB ? kNB : nbl));
+  const int rows_grid = (int)std::min<long long>((h->g.nrows + 7) / 8, 152LL * 32);
+  cudaStream_t st = b.st;
+  std::vector<int> status(nrhs, DDA_NOT_CONVERGED), iters(nrhs, 0), outer(nrhs, 0);
+  std::vector<int> mv64(nrhs, 0);
+  std::vector<double> res_true(nrhs, NAN), res_recur(nrhs, NAN);
+  // b64 per right-hand side (FP64, Eq. (3))
+  c128* b64;
+  c128* x64;
+  c128* r64 = nullptr;
+  c128* w64;
+  if (!refined) {
+    c128* base = (c128*)m->sv;
+    b64 = base + (size_t)nvec * nrhs * n;
+    x64 = b64 + (size_t)nrhs * n;
+    w64 = base;                                    // reused after the solve
+  } else {
+    c64* base = (c64*)m->sv;
+    b64 = (c128*)(base + (size_t)(nvec + 2) * nrhs * n);
+    x64 = b64 + (size_t)nrhs * n;
+    r64 = x64 + (size_t)nrhs * n;
+    w64 = r64 + (size_t)nrhs * n;
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    Wave wv;
+    for (int q = 0; q < 3; ++q) wv.a[q] = prop[3 * r + q];
+    for (int q = 0; q < 6; ++q) wv.e[q] = pol[6 * r + q];
+    k_rhs<double><<<rows_grid, 256, 0, st>>>(b64 + (size_t)r * n, h->lat(),
+                                             h->w64.beta + (long long)r * h->n_mat * 3,
+                                             h->g.n_occ, h->g.nx, h->g.ny, h->g.nz, h->g.nrows,
+                                             h->kd, wv); count_launch();
+  }
+  LK(h);
+  const dim3 vg(b.nb, nrhs);
+  std::vector<double> bn(nrhs, 0.0);
+  if (!refined) {
+    c128* base = (c128*)m->sv;
+    c128* vec[nvec];
+    for (int i = 0; i < nvec; ++i) vec[i] = base + (size_t)i * nrhs * n;
+    int steps = 0;
+    RK(run_qmr_batched<double>(b, b64, x64, vec, o->tol, nullptr, nullptr, o->maxiter, &steps));
+    for (int r = 0; r < nrhs; ++r) {
+      status[r] = m->hs[r].status;
+      iters[r] = m->hs[r].iters;
+      res_recur[r] = m->hs[r].res;
+      bn[r] = m->hs[r].bnorm;
+    }
+    // true residuals in FP64, one batched product
+    cudaError_t e = launch_matvec<double>(h->g, h->lat(), h->w64, h->w64.beta, h->n_mat, x64, w64,
+                                          nrhs, false, st);
+    if (e != cudaSuccess) return dda_cuda_fail(h, e, "batched product");
+    k_resid_b<<<vg, kVT, 0, st>>>(b64, w64, base + (size_t)nrhs * n, n, m->part, nullptr); count_launch();
+    k_take_norms_b<<<nrhs, kVT, 0, st>>>(m->ds, m->part, b.nb, nullptr); count_launch();
+    LK(h);
+    RK(bsync(b));
+    for (int r = 0; r < nrhs; ++r) {
+      res_true[r] = bn[r] > 0 ? m->hs[r].sres / bn[r] : 0.0;
+      if (status[r] == DDA_OK && !(res_true[r] < o->tol)) status[r] = DDA_NOT_CONVERGED;
+      mv64[r] = iters[r] + 1;
+    }
+  } else {
+    c64* base = (c64*)m->sv;
+    c64* vec[nvec];
+    for (int i = 0; i < nvec; ++i) vec[i] = base + (size_t)i * nrhs * n;
+    c64* x32 = base + (size_t)nvec * nrhs * n;
+    c64* rhs32 = x32 + (size_t)nrhs * n;
+    k_norms<double><<<vg, kVT, 0, st>>>(b64, n, m->part, nullptr); count_launch();
+    k_take_norms_b<<<nrhs, kVT, 0, st>>>(m->ds, m->part, b.nb, nullptr); count_launch();
+    k_copy<double><<<b.nb, kVT, 0, st>>>(b64, r64, (long long)nrhs * n); count_launch();
+    k_zero<double><<<b.nb, kVT, 0, st>>>(x64, (long long)nrhs * n); count_launch();
+    LK(h);
+    RK(bsync(b));
+    std::vector<double> rn(nrhs);
+    std::vector<char> fin_(nrhs, 0);
+    for (int r = 0; r < nrhs; ++r) {
+      bn[r] = m->hs[r].sres;
+      rn[r] = bn[r];
+      if (!(bn[r] > 0)) { fin_[r] = 1; status[r] = DDA_OK; res_true[r] = 0.0; }
+      else res_true[r] = 1.0;
+    }
+    int left = o->maxiter;
+    b.stall = true;
+    for (int it_out = 0; it_out < 64 && left > 0; ++it_out) {
+      bool any = false;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!fin_[r] && rn[r] / bn[r] < o->tol) { fin_[r] = 1; status[r] = DDA_OK; }
+        m->h_off[r] = fin_[r];
+        m->h_vals[r] = std::max(o->inner_tol, 0.5 * o->tol * bn[r] / rn[r]);   // inner targets
+        m->h_vals[nrhs + r] = fin_[r] ? 0.0 : 1.0 / rn[r];                     // scales
+        any = any || !fin_[r];
+      }
+      if (!any) break;
+      DDA_CK(h, cudaMemcpyAsync(m->off, m->h_off, nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+      DDA_CK(h, cudaMemcpyAsync(m->dvals, m->h_vals, 2 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+      k_to32s_b<<<vg, kVT, 0, st>>>(r64, rhs32, n, m->dvals + nrhs, m->off); count_launch();
+      LK(h);
+      int steps = 0;
+      RK(run_qmr_batched<float>(b, rhs32, x32, vec, 0.0, m->dvals, m->off, left, &steps));
+      left -= steps;
+      for (int r = 0; r < nrhs; ++r) {
+        if (fin_[r]) continue;
+        iters[r] += m->hs[r].iters;
+        outer[r] += 1;
+        m->h_vals[nrhs + r] = rn[r];
+      }
+      DDA_CK(h, cudaMemcpyAsync(m->dvals + nrhs, m->h_vals + nrhs, nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+      std::vector<int> inner_status(nrhs);
+      for (int r = 0; r < nrhs; ++r) inner_status[r] = m->hs[r].status;
+      k_axpy64_b<<<vg, kVT, 0, st>>>(x64, x32, n, m->dvals + nrhs, m->off); count_launch();
+      cudaError_t e = launch_matvec<double>(h->g, h->lat(), h->w64, h->w64.beta, h->n_mat, x64, w64,
+                                            nrhs, false, st, nullptr, nullptr, m->off);
+      if (e != cudaSuccess) return dda_cuda_fail(h, e, "batched product");
+      k_resid_b<<<vg, kVT, 0, st>>>(b64, w64, r64, n, m->part, m->off); count_launch();
+      k_take_norms_b<<<nrhs, kVT, 0, st>>>(m->ds, m->part, b.nb, m->off); count_launch();
+      LK(h);
+      RK(bsync(b));
+      for (int r = 0; r < nrhs; ++r) {
+        if (fin_[r]) continue;
+        mv64[r] += 1;
+        const double rn_new = m->hs[r].sres;
+        res_true[r] = rn_new / bn[r];
+        if (!std::isfinite(rn_new)) { fin_[r] = 1; status[r] = DDA_ERR_NONFINITE; continue; }
+        if (res_true[r] < o->tol) { fin_[r] = 1; status[r] = DDA_OK; continue; }
+        if (inner_status[r] == DDA_BREAKDOWN || inner_status[r] == DDA_ERR_NONFINITE) {
+          fin_[r] = 1; status[r] = inner_status[r]; continue;
+        }
+        if (!(rn_new < 0.999 * rn[r])) { fin_[r] = 1; status[r] = DDA_NOT_CONVERGED; continue; }
+        rn[r] = rn_new;
+      }
+    }
+    for (int r = 0; r < nrhs; ++r) res_recur[r] = res_true[r];
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    k_pfinal<double><<<b.nb, kVT, 0, st>>>(x64 + (size_t)r * n, (c128*)P_dev + (size_t)r * n,
+                                           h->d_mat, h->w64.beta + (long long)r * h->n_mat * 3,
+                                           h->g.n_occ); count_launch();
+  }
+  LK(h);
+  DDA_CK(h, cudaStreamSynchronize(st));
+  tr_flush(&h->tracer);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int worst = DDA_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    dda_solve_info& inf = info[r];
+    inf = dda_solve_info{};
+    inf.status = status[r];
+    inf.iters = iters[r];
+    inf.matvecs = iters[r] + mv64[r];
+    inf.matvecs_fp64 = refined ? mv64[r] : iters[r] + 1;
+    if (!refined) inf.matvecs = iters[r] + 1;
+    inf.outer = outer[r];
+    inf.rel_res_true = res_true[r];
+    inf.rel_res_recur = res_recur[r];
+    inf.seconds = secs;
+    if (status_rank(status[r]) > status_rank(worst)) worst = status[r];
   }
   return worst;
 }

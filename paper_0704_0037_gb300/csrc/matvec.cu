@@ -32,7 +32,8 @@ template <typename R, bool CONJ>
 __global__ void __launch_bounds__(256) k_p1(const cpx<R>* __restrict__ x, cpx<R>* __restrict__ B1,
                                             LatticeDev lat, const cpx<R>* __restrict__ beta,
                                             long long n_occ, int nrows, FftPlan p,
-                                            const cpx<R>* __restrict__ tw, int logT) {
+                                            const cpx<R>* __restrict__ tw, int logT, int bstride,
+                                            const int* __restrict__ skip) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = p.M;
   const int T = 1 << logT;
@@ -40,12 +41,14 @@ __global__ void __launch_bounds__(256) k_p1(const cpx<R>* __restrict__ x, cpx<R>
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* b0 = s_tw + M;
   cpx<R>* b1 = b0 + (size_t)M * ldm;
-  const int c = blockIdx.y;
+  const int cc = blockIdx.y, c = cc % 3;     // 3 * (right-hand side) + component
+  if (skip && skip[cc / 3]) return;
+  beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
   load_tw(s_tw, tw, M);
   for (int i = threadIdx.x; i < M * ldm; i += blockDim.x) b0[i] = mk<R>(0, 0);
   __syncthreads();
-  const cpx<R>* xc = x + (long long)c * n_occ;
+  const cpx<R>* xc = x + (long long)cc * n_occ;
   for (int t = 0; t < T; ++t) {
     const int row = r0 + t;
     if (row >= nrows) break;
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(256) k_p1(const cpx<R>* __restrict__ x, cpx<R>
   }
   __syncthreads();
   cpx<R>* res = stockham<R, false>(b0, b1, ldm, logT, p, s_tw);
-  cpx<R>* out = B1 + (long long)c * nrows * M;
+  cpx<R>* out = B1 + (long long)cc * nrows * M;
   for (int it = threadIdx.x; it < M * T; it += blockDim.x) {
     const int t = it / M, m = it - t * M;
     const int row = r0 + t;
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(256) k_p5(const cpx<R>* __restrict__ B1, const
                                             cpx<R>* __restrict__ y, LatticeDev lat,
                                             const cpx<R>* __restrict__ beta, long long n_occ,
                                             int nrows, FftPlan p, const cpx<R>* __restrict__ tw,
-                                            int logT) {
+                                            int logT, int bstride, const int* __restrict__ skip) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int M = p.M;
   const int T = 1 << logT;
@@ -80,10 +83,12 @@ __global__ void __launch_bounds__(256) k_p5(const cpx<R>* __restrict__ B1, const
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* b0 = s_tw + M;
   cpx<R>* b1 = b0 + (size_t)M * ldm;
-  const int c = blockIdx.y;
+  const int cc = blockIdx.y, c = cc % 3;
+  if (skip && skip[cc / 3]) return;
+  beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
   load_tw(s_tw, tw, M);
-  const cpx<R>* in = B1 + (long long)c * nrows * M;
+  const cpx<R>* in = B1 + (long long)cc * nrows * M;
   for (int it = threadIdx.x; it < M * T; it += blockDim.x) {
     const int t = it / M, m = it - t * M;
     const int row = r0 + t;
@@ -91,8 +96,8 @@ __global__ void __launch_bounds__(256) k_p5(const cpx<R>* __restrict__ B1, const
   }
   __syncthreads();
   cpx<R>* res = stockham<R, true>(b0, b1, ldm, logT, p, s_tw);
-  const cpx<R>* xc = x + (long long)c * n_occ;
-  cpx<R>* yc = y + (long long)c * n_occ;
+  const cpx<R>* xc = x + (long long)cc * n_occ;
+  cpx<R>* yc = y + (long long)cc * n_occ;
   for (int t = 0; t < T; ++t) {
     const int row = r0 + t;
     if (row >= nrows) break;
@@ -113,6 +118,8 @@ struct LineGeom {
   int contig;
   long long in_sm, in_st, in_so, in_sb;
   long long out_sm, out_st, out_so, out_sb;
+  const int* skip;     // batch b is skipped when skip[b / per] != 0 (null: none)
+  int per;
 };
 
 // in may equal out (in-place passes of the D-matrix build): every block reads
@@ -129,6 +136,7 @@ __global__ void __launch_bounds__(256) k_lines(const cpx<R>* in, cpx<R>* out,
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* b0 = s_tw + M;
   cpx<R>* b1 = b0 + (size_t)M * ldm;
+  if (lg.skip && lg.skip[blockIdx.z / lg.per]) return;
   const int t0 = blockIdx.x * T;
   const long long ib = blockIdx.z * lg.in_sb + blockIdx.y * lg.in_so;
   const long long ob = blockIdx.z * lg.out_sb + blockIdx.y * lg.out_so;
@@ -169,9 +177,12 @@ static __device__ __forceinline__ int fold(int k, int M, int& neg) {
 template <typename R>
 __global__ void __launch_bounds__(256) k_p3(cpx<R>* __restrict__ B2, const cpx<R>* __restrict__ D,
                                             int nz, int Mx, int My, FftPlan p,
-                                            const cpx<R>* __restrict__ tw, int logT) {
+                                            const cpx<R>* __restrict__ tw, int logT,
+                                            const int* __restrict__ skip) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Mz = p.M;
+  if (skip && skip[blockIdx.z]) return;
+  B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
   const int T = 1 << logT;
   const int Tm = T - 1;
   const int ldm = T;
@@ -267,13 +278,13 @@ cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const Fft
                          const cpx<R>* tw, bool inverse, int n_in, int n_out, int nt, int n_outer,
                          int n_batch, bool contig, long long in_sm, long long in_st,
                          long long in_so, long long in_sb, long long out_sm, long long out_st,
-                         long long out_so, long long out_sb, cudaStream_t st) {
+                         long long out_so, long long out_sb, cudaStream_t st, const int* skip) {
   (void)g;
   const int logTmax = sizeof(R) == 4 ? 4 : 3;
   const int lt = pick_logT(p.M, sizeof(cpx<R>), 2, contig ? 1 : 0, logTmax);
   const size_t sm = smem_bytes(p.M, sizeof(cpx<R>), 2, lt, contig ? 1 : 0);
   LineGeom lg{n_in, n_out, nt, contig ? 1 : 0, in_sm, in_st, in_so, in_sb,
-              out_sm, out_st, out_so, out_sb};
+              out_sm, out_st, out_so, out_sb, skip, 3};
   dim3 grid((nt + (1 << lt) - 1) >> lt, n_outer, n_batch);
   cudaError_t e;
   if (inverse) {
@@ -291,7 +302,7 @@ cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const Fft
 template <typename R>
 cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, const cpx<R>* beta,
                           int n_mat, const cpx<R>* x, cpx<R>* y, int nrhs, bool adjoint,
-                          cudaStream_t st, double* dotp, int* dot_nb) {
+                          cudaStream_t st, double* dotp, int* dot_nb, const int* skip) {
   if (dot_nb) *dot_nb = 0;
   const int logTmax = sizeof(R) == 4 ? 4 : 3;
   const size_t el = sizeof(cpx<R>);
@@ -309,51 +320,62 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
   if ((e = allow_smem(k_p5<R, true>, sm1)) != cudaSuccess) return e;
   if ((e = allow_smem(k_p3<R>, sm3)) != cudaSuccess) return e;
   const long long nv = 3LL * g.n_occ;
+  const int bstride = n_mat * 3;
   // per axis: the register-resident passes when the padded length has a
   // compile-time split, the shared-memory Stockham passes otherwise
   const bool fx = g.engine == 0 && fast_supported(g.Mx);
   const bool fy = g.engine == 0 && fast_supported(g.My);
   const bool fz = g.engine == 0 && fast_supported(g.Mz);
-  for (int r = 0; r < nrhs; ++r) {
-    const cpx<R>* xr = x + r * nv;
-    cpx<R>* yr = y + r * nv;
-    const cpx<R>* br = beta + (long long)r * n_mat * 3;
+  const int dnb = fast_xinv_blocks(g.nrows, sizeof(R) == 4);
+  if (dotp && dot_nb && fx) *dot_nb = dnb;
+  // right-hand sides in chunks of the work buffers' capacity, each chunk in
+  // one launch per pass
+  const int cap = w.cap > 0 ? w.cap : 1;
+  for (int r0 = 0; r0 < nrhs; r0 += cap) {
+    const int cnt = nrhs - r0 < cap ? nrhs - r0 : cap;
+    const cpx<R>* xr = x + r0 * nv;
+    cpx<R>* yr = y + r0 * nv;
+    const cpx<R>* br = beta + (long long)r0 * bstride;
+    const int* sk = skip ? skip + r0 : nullptr;
     FastArgs fa{};
     fa.lat = lat; fa.beta = br; fa.D = w.D; fa.n_occ = g.n_occ; fa.nrows = g.nrows;
     fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = adjoint; fa.st = st;
-    dim3 g1((g.nrows + (1 << lt1) - 1) >> lt1, 3);
+    fa.nrhs = cnt; fa.bstride = bstride; fa.skip = sk;
+    dim3 g1((g.nrows + (1 << lt1) - 1) >> lt1, 3 * cnt);
     const int tb = sizeof(R) == 4 ? TR_P1_C64 : TR_P1_C128;
-    // P1: x lines of the occupied rows, gather and beta -> B1 [3][nz][ny][Mx]
+    // P1: x lines of the occupied rows, gather and beta -> B1 [rhs][3][nz][ny][Mx]
     tr_begin(g.tr, st);
     if (fx) {
       fa.in = xr; fa.out = w.B1; fa.tw = twx;
       if ((e = fast_pass<R>(g.Mx, FP_XFWD, fa)) != cudaSuccess) return e;
     } else if (adjoint) {
-      k_p1<R, true><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+      k_p1<R, true><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1,
+                                          bstride, sk); count_launch();
     } else {
-      k_p1<R, false><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+      k_p1<R, false><<<g1, 256, sm1, st>>>(xr, w.B1, lat, br, g.n_occ, g.nrows, g.px, twx, lt1,
+                                           bstride, sk); count_launch();
     }
     tr_end(g.tr, st, tb);
     tr_begin(g.tr, st);
-    // P2: y lines of B1 [3][nz][ny][Mx] -> B2 [3][nz][My][Mx]
+    // P2: y lines of B1 [rhs][3][nz][ny][Mx] -> B2 [rhs][3][nz][My][Mx]
     if (fy) {
       fa.in = w.B1; fa.out = w.B2; fa.tw = twy;
       e = fast_pass<R>(g.My, FP_YFWD, fa);
     } else {
-      e = launch_lines<R>(g, w.B1, w.B2, g.py, twy, false, g.ny, g.My, g.Mx, g.nz, 3, false,
+      e = launch_lines<R>(g, w.B1, w.B2, g.py, twy, false, g.ny, g.My, g.Mx, g.nz, 3 * cnt, false,
                           g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx,
-                          g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx, st);
+                          g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx, st, sk);
     }
     if (e != cudaSuccess) return e;
     tr_end(g.tr, st, tb + 1);
-    dim3 g3((g.Mx + (1 << lt3) - 1) >> lt3, g.My);
+    dim3 g3((g.Mx + (1 << lt3) - 1) >> lt3, g.My, cnt);
     tr_begin(g.tr, st);
     // P3: z lines, product with the octant of FFT(G), inverse z lines (in place)
     if (fz) {
       fa.out = w.B2; fa.tw = twz;
       if ((e = fast_pass<R>(g.Mz, FP_ZCONV, fa)) != cudaSuccess) return e;
     } else {
-      k_p3<R><<<g3, 256, sm3, st>>>(w.B2, w.D, g.nz, g.Mx, g.My, g.pz, twz, lt3); count_launch();
+      k_p3<R><<<g3, 256, sm3, st>>>(w.B2, w.D, g.nz, g.Mx, g.My, g.pz, twz, lt3, sk); count_launch();
     }
     tr_end(g.tr, st, tb + 2);
     tr_begin(g.tr, st);
@@ -362,25 +384,24 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
       fa.in = w.B2; fa.out = w.B1; fa.tw = twy;
       e = fast_pass<R>(g.My, FP_YINV, fa);
     } else {
-      e = launch_lines<R>(g, w.B2, w.B1, g.py, twy, true, g.My, g.ny, g.Mx, g.nz, 3, false,
+      e = launch_lines<R>(g, w.B2, w.B1, g.py, twy, true, g.My, g.ny, g.Mx, g.nz, 3 * cnt, false,
                           g.Mx, 1, (long long)g.My * g.Mx, (long long)g.nz * g.My * g.Mx,
-                          g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx, st);
+                          g.Mx, 1, (long long)g.ny * g.Mx, (long long)g.nz * g.ny * g.Mx, st, sk);
     }
     if (e != cudaSuccess) return e;
     tr_end(g.tr, st, tb + 3);
     tr_begin(g.tr, st);
-    // P5: inverse x, keep the occupied x, y = x - beta u
+    // P5: inverse x, keep the occupied x, y = x - beta u (+ partials of x^T y)
     if (fx) {
       fa.in = w.B1; fa.x = xr; fa.out = yr; fa.tw = twx;
-      if (dotp && nrhs == 1 && dot_nb) {
-        fa.dotp = dotp;
-        *dot_nb = fast_xinv_blocks(g.nrows, sizeof(R) == 4);
-      }
+      if (dotp && dot_nb) fa.dotp = dotp + (size_t)r0 * 2 * dnb;
       if ((e = fast_pass<R>(g.Mx, FP_XINV, fa)) != cudaSuccess) return e;
     } else if (adjoint) {
-      k_p5<R, true><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+      k_p5<R, true><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1,
+                                          bstride, sk); count_launch();
     } else {
-      k_p5<R, false><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1); count_launch();
+      k_p5<R, false><<<g1, 256, sm1, st>>>(w.B1, xr, yr, lat, br, g.n_occ, g.nrows, g.px, twx, lt1,
+                                           bstride, sk); count_launch();
     }
     tr_end(g.tr, st, tb + 4);
   }
@@ -389,18 +410,20 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
 
 template cudaError_t launch_matvec<float>(const Geom&, const LatticeDev&, Work<float>&,
                                           const c64*, int, const c64*, c64*, int, bool,
-                                          cudaStream_t, double*, int*);
+                                          cudaStream_t, double*, int*, const int*);
 template cudaError_t launch_matvec<double>(const Geom&, const LatticeDev&, Work<double>&,
                                            const c128*, int, const c128*, c128*, int, bool,
-                                           cudaStream_t, double*, int*);
+                                           cudaStream_t, double*, int*, const int*);
 template cudaError_t launch_lines<double>(const Geom&, const c128*, c128*, const FftPlan&,
                                           const c128*, bool, int, int, int, int, int, bool,
                                           long long, long long, long long, long long, long long,
-                                          long long, long long, long long, cudaStream_t);
+                                          long long, long long, long long, cudaStream_t,
+                                          const int*);
 template cudaError_t launch_lines<float>(const Geom&, const c64*, c64*, const FftPlan&,
                                          const c64*, bool, int, int, int, int, int, bool,
                                          long long, long long, long long, long long, long long,
-                                         long long, long long, long long, cudaStream_t);
+                                         long long, long long, long long, cudaStream_t,
+                                         const int*);
 
 // Factor M into radices 8, 4, 2, 3, 5, 7 (in that order of preference).
 FftPlan make_plan(int M) {

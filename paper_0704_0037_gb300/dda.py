@@ -33,7 +33,7 @@ PREC = {"fp64": DDA_FP64, "fp32_refined": DDA_FP32_REFINED}
 
 # every entry point declared in include/dda.h
 EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec",
-           "dda_matvec_adjoint", "dda_solve", "dda_scatter", "dda_mueller_plane",
+           "dda_matvec_adjoint", "dda_solve", "dda_solve_batch", "dda_scatter", "dda_mueller_plane",
            "dda_mueller_plane_full", "dda_asymmetry", "dda_symmetry", "dda_mueller_plane_sym",
            "dda_orientation_average",
            "dda_farfield_noalloc", "dda_trace",
@@ -89,6 +89,8 @@ def lib():
         "dda_matvec_adjoint": ([_vp, _ip, _vp, _vp, _ip], _ip),
         "dda_solve": ([_vp, ctypes.POINTER(SolveOpts), _ip, _dp, _dp, _vp, _dp, _ip,
                        ctypes.POINTER(SolveInfo)], _ip),
+        "dda_solve_batch": ([_vp, ctypes.POINTER(SolveOpts), _ip, _dp, _dp, _vp,
+                             ctypes.POINTER(SolveInfo)], _ip),
         "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane_full": ([_ip, _dp, _dp, _dp, _dp], _ip),
@@ -213,6 +215,19 @@ def dda_solve(h, opts, prop, pol, P, hist_len=0):
                          _dev_ptr(P, torch.complex128), _dptr(hist), int(hist_len), info)
     _check(h, rc)
     return rc, [i.as_dict() for i in info], hist
+
+
+def dda_solve_batch(h, opts, prop, pol, P):
+    """All right-hand sides at once (QMR-CS).  Returns (status, [info dicts])."""
+    import torch
+    o = _opts(opts)
+    nrhs = int(np.asarray(prop).size // 3)
+    a, e = _vecs(prop, pol, nrhs)
+    info = (SolveInfo * nrhs)()
+    rc = lib().dda_solve_batch(h, ctypes.byref(o), nrhs, _dptr(a), _dptr(e),
+                               _dev_ptr(P, torch.complex128), info)
+    _check(h, rc)
+    return rc, [i.as_dict() for i in info]
 
 
 def dda_scatter(h, pol_prescription, P, prop, pol, dirs=None, weights=None):
