@@ -200,6 +200,25 @@ int dda_solve_batch(dda_t h, const dda_solve_opts* opts, int nrhs, const double*
                     const double* pol_host, void* P_dev, dda_solve_info* info);
 
 /*
+ * dda_solve_many -- many particles at once (no counterpart in the paper): a
+ * pool of n_threads host threads takes the particles in order; each builds
+ * the particle's D-matrix for opts->prec if it is missing and runs
+ * dda_solve_batch on it, so the kernels of different particles overlap on
+ * the device.  Each handle must be distinct (a handle is not thread-safe)
+ * and should own a distinct non-default stream (dda_init_lattice) for the
+ * particles to overlap.
+ *   hs[i], nrhs[i], prop[i], pol[i], P[i], info[i] : as dda_solve_batch for
+ *   particle i (arrays of n_part pointers).
+ *   status_out : n_part ints, the status of each particle.
+ * Returns the worst status (errors before NOT_CONVERGED before OK), or
+ * DDA_ERR_ARG for null or repeated arguments (nothing runs then).
+ */
+int dda_solve_many(int n_part, dda_t const* hs, const dda_solve_opts* opts, const int* nrhs,
+                   const double* const* prop_host, const double* const* pol_host,
+                   void* const* P_dev, dda_solve_info* const* info, int n_threads,
+                   int* status_out);
+
+/*
  * dda_scatter -- scattering quantities of Sec. 3.1 from P (FP64 sums).
  *   pol_prescription : the prescription P was computed with (Q_abs needs alpha).
  *   P_dev     : device [nrhs][3][N_occ] complex128.

@@ -80,7 +80,7 @@ def build(force=False, verbose=False, extra_flags=()):
         msg = "\n".join(f"{os.path.basename(s)}:\n{out}" for s, out in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -236,6 +236,7 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   }
   dda_ctx* h = new (std::nothrow) dda_ctx();
   if (!h) return DDA_ERR_OOM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); h->device = 0; }
   Geom& g = h->g;
   g.nx = nx; g.ny = ny; g.nz = nz;
   g.nrows = ny * nz;

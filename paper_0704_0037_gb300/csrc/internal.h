@@ -104,6 +104,7 @@ int smooth_size(int lo);
 // The handle.
 struct dda_ctx {
   int sym_flags = 0;        // DDA_SYM_* found at init
+  int device = 0;           // CUDA device current at dda_init_lattice
   dda::Geom g{};
   int n_mat = 0;
   std::vector<double> m;          // 2*n_mat

@@ -33,7 +33,7 @@ PREC = {"fp64": DDA_FP64, "fp32_refined": DDA_FP32_REFINED}
 
 # every entry point declared in include/dda.h
 EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec",
-           "dda_matvec_adjoint", "dda_solve", "dda_solve_batch", "dda_scatter", "dda_mueller_plane",
+           "dda_matvec_adjoint", "dda_solve", "dda_solve_batch", "dda_solve_many", "dda_scatter", "dda_mueller_plane",
            "dda_mueller_plane_full", "dda_asymmetry", "dda_symmetry", "dda_mueller_plane_sym",
            "dda_orientation_average",
            "dda_farfield_noalloc", "dda_trace",
@@ -91,6 +91,9 @@ def lib():
                        ctypes.POINTER(SolveInfo)], _ip),
         "dda_solve_batch": ([_vp, ctypes.POINTER(SolveOpts), _ip, _dp, _dp, _vp,
                              ctypes.POINTER(SolveInfo)], _ip),
+        "dda_solve_many": ([_ip, ctypes.POINTER(_vp), ctypes.POINTER(SolveOpts), ctypes.POINTER(_ip),
+                            ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_vp),
+                            ctypes.POINTER(ctypes.POINTER(SolveInfo)), _ip, ctypes.POINTER(_ip)], _ip),
         "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane_full": ([_ip, _dp, _dp, _dp, _dp], _ip),
@@ -130,9 +133,12 @@ def _check(h, rc):
 
 
 def _stream_ptr(stream):
+    """cudaStream_t of a torch stream (or of torch's current one), or a raw handle."""
     if stream is None:
         import torch
         return _vp(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return _vp(stream.cuda_stream)
     return _vp(int(stream))
 
 
@@ -228,6 +234,38 @@ def dda_solve_batch(h, opts, prop, pol, P):
                                _dev_ptr(P, torch.complex128), info)
     _check(h, rc)
     return rc, [i.as_dict() for i in info]
+
+
+def dda_solve_many(handles, opts, props, pols, Ps, n_threads=8):
+    """Particles in parallel host threads (each handle on its own stream).
+    Returns (worst status, [status per particle], [[info dicts] per particle])."""
+    import torch
+    o = _opts(opts)
+    n = len(handles)
+    hs = (_vp * n)(*handles)
+    nr = (_ip * n)()
+    keep = []
+    pa = (_dp * n)()
+    pe = (_dp * n)()
+    pp = (_vp * n)()
+    infos = []
+    ip = (ctypes.POINTER(SolveInfo) * n)()
+    for i in range(n):
+        k = int(np.asarray(props[i]).size // 3)
+        a, e = _vecs(props[i], pols[i], k)
+        keep += [a, e]
+        nr[i] = k
+        pa[i] = _dptr(a)
+        pe[i] = _dptr(e)
+        pp[i] = _dev_ptr(Ps[i], torch.complex128)
+        inf = (SolveInfo * k)()
+        infos.append(inf)
+        ip[i] = ctypes.cast(inf, ctypes.POINTER(SolveInfo))
+    st = (_ip * n)()
+    rc = lib().dda_solve_many(n, hs, ctypes.byref(o), nr, pa, pe, pp, ip, int(n_threads), st)
+    if rc < 0 and all(s == 0 for s in st):
+        raise DDAError(rc, "dda_solve_many arguments")
+    return rc, list(st), [[x.as_dict() for x in inf] for inf in infos]
 
 
 def dda_scatter(h, pol_prescription, P, prop, pol, dirs=None, weights=None):

@@ -93,6 +93,43 @@ WORKLOADS = {
 }
 
 
+def batch_instances(count=128, seed=704037):
+    """Seeded batch of particles (numpy PCG64), drawn per particle in this
+    order: shape uniform over (sphere, ellipsoid, cube); size parameter
+    x ~ U[2, 15] (volume-equivalent); refractive index m ~ U[1.05, 2.0] (real);
+    for ellipsoids two axis ratios ~ U[1, 3]; then 8 incidence directions
+    uniform on the sphere.  The lattice has n = clamp(ceil(10 x m / pi), 16, 64)
+    dipoles along the major axis (about 10 per wavelength in the medium,
+    Sec. 3.1's rule) and n / ratio along the minor axes.  Each direction gets
+    two perpendicular polarisations: 16 right-hand sides per particle.
+    Returns a list of dicts (shape, x, m, occ, prop (16, 3), pol (16, 3))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        shape = ("sphere", "ellipsoid", "cube")[int(rng.integers(0, 3))]
+        x = float(rng.uniform(2.0, 15.0))
+        m = float(rng.uniform(1.05, 2.0))
+        ratios = rng.uniform(1.0, 3.0, size=2) if shape == "ellipsoid" else np.ones(2)
+        a = rng.standard_normal((8, 3))
+        a /= np.linalg.norm(a, axis=1, keepdims=True)
+        n = int(min(64, max(16, math.ceil(10.0 * x * m / math.pi))))
+        if shape == "sphere":
+            occ = sphere(n)
+        elif shape == "cube":
+            occ = cube(n, n, n)
+        else:
+            ny = max(2, int(round(n / ratios[0])))
+            nz = max(2, int(round(n / ratios[1])))
+            occ = ellipsoid(n, ny, nz)
+        prop, pol = [], []
+        for ai in a:
+            for e in perpendicular_pols(ai):
+                prop.append(ai)
+                pol.append(e)
+        out.append(dict(shape=shape, x=x, m=m, occ=occ, prop=np.array(prop), pol=np.array(pol)))
+    return out
+
+
 def angles_deg(count=181):
     """Scattering angles 0..180 degrees in equal steps (181 -> 1 degree)."""
     return np.linspace(0.0, 180.0, count)

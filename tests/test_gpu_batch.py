@@ -96,3 +96,36 @@ def test_solve_batch_refined(sphere16_cldr):
     with pytest.raises(dda.DDAError) as ei:
         dda.dda_solve_batch(p.h, dict(opts, solver=dda.DDA_BICGSTAB), prop, pol, P)
     assert ei.value.status == dda.DDA_ERR_ARG
+
+
+def test_solve_many_equals_one_by_one():
+    """Particles in parallel host threads on their own streams give the same
+    results as one dda_solve_batch call per particle."""
+    torch, dda = need_gpu()
+    parts = [(inputs.sphere(10), 1.3 + 0.01j), (inputs.ellipsoid(12, 8, 6), 1.5),
+             (inputs.cube(6, 6, 6), 1.2 + 0.1j)]
+    opts = dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_CLDR, prec=dda.DDA_FP32_REFINED, tol=1e-6,
+                maxiter=2000, inner_tol=1e-4)
+    hs, props, pols, Ps, streams = [], [], [], [], []
+    for k, (occ, m) in enumerate(parts):
+        s = torch.cuda.Stream()
+        p = dda.Particle(occ, [m], 0.45, stream=s)
+        prop, pol = _orientations(2, 20 + k)
+        hs.append(p); props.append(prop); pols.append(pol); streams.append(s)
+        Ps.append(torch.zeros((len(prop), 3, p.n_occ), dtype=torch.complex128, device="cuda"))
+    torch.cuda.synchronize()
+    st, sts, infos = dda.dda_solve_many([p.h for p in hs], opts, props, pols, Ps, n_threads=2)
+    assert st == 0 and sts == [0, 0, 0]
+    for k, p in enumerate(hs):
+        Q = torch.zeros_like(Ps[k])
+        st1, info1 = dda.dda_solve_batch(p.h, opts, props[k], pols[k], Q)
+        assert torch.equal(Q, Ps[k])
+        assert [i["iters"] for i in info1] == [i["iters"] for i in infos[k]]
+        assert all(i["rel_res_true"] < 1e-6 for i in infos[k])
+        p.close()
+    with pytest.raises(dda.DDAError):       # the same handle twice is refused
+        q = dda.Particle(inputs.cube(4, 4, 4), [1.2], 0.4)
+        with q:
+            P = torch.zeros((2, 3, q.n_occ), dtype=torch.complex128, device="cuda")
+            dda.dda_solve_many([q.h, q.h], opts, [props[0], props[0]], [pols[0], pols[0]], [P, P])
+
