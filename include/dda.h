@@ -66,9 +66,15 @@ enum dda_solver { DDA_QMR_CS = 0, DDA_BICG_CS = 1, DDA_BICGSTAB = 2, DDA_CGNR = 
 
 /* Arithmetic of the product / solve.  DDA_FP64: complex128 everywhere (the
  * paper's choice, Sec. 2).  DDA_FP32_REFINED: complex64 vectors and FFTs with
- * FP64 D-matrix build, Krylov scalars, inner products and an FP64 outer
- * iterative refinement on the true residual. */
-enum dda_prec { DDA_FP64 = 0, DDA_FP32_REFINED = 1 };
+ * an FP64-class D-matrix build, FP64 Krylov scalars and inner products, and
+ * an outer iterative refinement on the true residual computed from complex128
+ * vectors.  On grids whose three padded lengths have register-resident passes
+ * (32, 64, 128, 256, 270) the FP32_REFINED D-matrix build and its residual
+ * products run in double-float arithmetic (pairs of floats, about 48
+ * significant bits, on the FP32 pipe); elsewhere in FP64.
+ * DDA_FP64_PAIR (dda_matvec only): that double-float product on complex128
+ * vectors; needs a DDA_FP32_REFINED build on such a grid, no adjoint. */
+enum dda_prec { DDA_FP64 = 0, DDA_FP32_REFINED = 1, DDA_FP64_PAIR = 2 };
 
 /*
  * dda_init_lattice -- create a handle for one particle (Sec. 2 Eq. (1); the

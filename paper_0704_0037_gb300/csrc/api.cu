@@ -176,6 +176,7 @@ int ensure_work_cap(dda_t h, Work<R>& w, int want) {
 }
 template int ensure_work_cap<float>(dda_t, Work<float>&, int);
 template int ensure_work_cap<double>(dda_t, Work<double>&, int);
+template int ensure_work_cap<df>(dda_t, Work<df>&, int);
 
 }  // namespace dda
 
@@ -307,6 +308,12 @@ extern "C" int dda_build_Dmatrix(dda_t h, int prec) {
   if (prec == DDA_FP32_REFINED) {
     rc = ensure_work<float>(h, h->w32);
     if (rc != DDA_OK) return rc;
+    // double-float tables when every axis has register-resident passes
+    const Geom& g = h->g;
+    if (g.engine == 0 && fast_supported(g.Mx) && fast_supported(g.My) && fast_supported(g.Mz)) {
+      rc = ensure_work<df>(h, h->wdf);
+      if (rc != DDA_OK) return rc;
+    }
   }
   return dda_build_D_internal(h, prec == DDA_FP32_REFINED);
 }
@@ -335,6 +342,15 @@ static int matvec_common(dda_t h, int prec, const void* x, void* y, int nrhs, bo
     if (rc != DDA_OK) return rc;
     e = launch_matvec<float>(h->g, h->lat(), h->w32, h->w32.beta, h->n_mat, (const c64*)x,
                              (c64*)y, nrhs, adjoint, h->stream);
+  } else if (prec == DDA_FP64_PAIR) {
+    if (adjoint) return dda_fail(h, DDA_ERR_ARG, "no adjoint in double-float");
+    if (!h->wdf.have_D)
+      return dda_fail(h, DDA_ERR_STATE, "double-float D-matrix not built (FP32_REFINED build "
+                                        "on a grid with register-resident passes)");
+    const int rc = ensure_work_cap<df>(h, h->wdf, nrhs);
+    if (rc != DDA_OK) return rc;
+    e = launch_matvec_df(h->g, h->lat(), h->wdf, h->w64.beta, h->n_mat, (const c128*)x, (c128*)y,
+                         nrhs, h->stream);
   } else {
     return dda_fail(h, DDA_ERR_ARG, "unknown precision");
   }
@@ -562,6 +578,7 @@ extern "C" int dda_free(dda_t h) {
   tr_destroy(&h->tracer);
   free_work(h->w64);
   free_work(h->w32);
+  free_work(h->wdf);
   cudaFree(h->d_row_off); cudaFree(h->d_xi); cudaFree(h->d_mat);
   cudaFree(h->sv); cudaFree(h->d_part); cudaFree(h->d_mvpart); cudaFree(h->d_scal); cudaFreeHost(h->h_scal);
   batch_free(h);

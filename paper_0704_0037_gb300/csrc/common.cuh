@@ -101,6 +101,66 @@ template <> __host__ __device__ __forceinline__ c64 fmas<float>(c64 a, float s, 
 #endif
 }
 
+// ---------------------------------------------------------------- double-float
+// A real number carried as an unevaluated sum hi + lo of two floats
+// (|lo| <= ulp(hi)/2), about 48 significant bits; the FP32 pipe runs the
+// arithmetic.  The algorithms are the classical error-free transformations:
+// Knuth's two-sum for the rounding error of a sum, Dekker's fast two-sum to
+// renormalise, and the exact product error a*b - fl(a*b) from one fused
+// multiply-add.  Sum and product use the cheap ("sloppy") double-word forms:
+// their error is a small multiple of 2^-46 relative to the operands' magnitude,
+// which is the error an FFT's rounding analysis needs.  Used for the FP64-class
+// products (the refinement residual, the D-matrix build) on parts whose FP64
+// pipe is a small fraction of the FP32 one.
+struct __align__(8) df {
+  float hi, lo;
+  __host__ __device__ constexpr df() : hi(0.0f), lo(0.0f) {}
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  // split of a double (compile-time constants, table entries)
+  __host__ __device__ constexpr explicit df(double v)
+      : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+
+#if defined(__CUDA_ARCH__)
+#define DDA_FADD(a, b) __fadd_rn((a), (b))
+#define DDA_FSUB(a, b) __fsub_rn((a), (b))
+#define DDA_FMUL(a, b) __fmul_rn((a), (b))
+#define DDA_FFMA(a, b, c) __fmaf_rn((a), (b), (c))
+#else
+#define DDA_FADD(a, b) ((a) + (b))
+#define DDA_FSUB(a, b) ((a) - (b))
+#define DDA_FMUL(a, b) ((a) * (b))
+#define DDA_FFMA(a, b, c) fmaf((a), (b), (c))
+#endif
+
+__host__ __device__ __forceinline__ df operator+(df a, df b) {
+  const float s = DDA_FADD(a.hi, b.hi);
+  const float bb = DDA_FSUB(s, a.hi);
+  float e = DDA_FADD(DDA_FSUB(a.hi, DDA_FSUB(s, bb)), DDA_FSUB(b.hi, bb));   // two-sum error
+  e = DDA_FADD(e, DDA_FADD(a.lo, b.lo));
+  const float h = DDA_FADD(s, e);
+  return df(h, DDA_FSUB(e, DDA_FSUB(h, s)));                                 // fast two-sum
+}
+__host__ __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__host__ __device__ __forceinline__ df operator*(df a, df b) {
+  const float p = DDA_FMUL(a.hi, b.hi);
+  float e = DDA_FFMA(a.hi, b.hi, -p);                                        // exact product error
+  e = DDA_FFMA(a.hi, b.lo, e);
+  e = DDA_FFMA(a.lo, b.hi, e);
+  const float h = DDA_FADD(p, e);
+  return df(h, DDA_FSUB(e, DDA_FSUB(h, p)));
+}
+
+template <> struct __align__(16) cpx<df> { df x, y; };
+using cdf = cpx<df>;
+
+__host__ __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+__host__ __device__ __forceinline__ c128 to128(cdf a) {
+  return mk<double>(df_to_double(a.x), df_to_double(a.y));
+}
+__host__ __device__ __forceinline__ cdf to_cdf(c128 a) { return mk<df>(df(a.x), df(a.y)); }
+
 template <typename R> __host__ __device__ __forceinline__ cpx<R> cvt(c128 a) {
   return mk<R>((R)a.x, (R)a.y);
 }

@@ -13,10 +13,14 @@
 // keeps that parity, which is how Sec. 2's "symmetry of the interaction
 // matrix" reduces the memory of its Fourier transform.  1/(Mx My Mz) is folded in.
 #include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 
 namespace dda {
+
+__device__ __forceinline__ c128 store_as(c128 v, c128*) { return v; }
+__device__ __forceinline__ cdf store_as(c128 v, cdf*) { return to_cdf(v); }
 
 // G for every non-negative offset (dx, dy, dz) < (nx, ny, nz), all six
 // components from one evaluation of exp(i kappa rho): table[6][nz][ny][nx].
@@ -57,7 +61,8 @@ __global__ void k_green_table(c128* __restrict__ table, double kd, int nx, int n
 // stands for offset j (j < n) or j - M (j > M - n), zero otherwise; a
 // negative offset along an axis flips the sign iff exactly one of mu, nu is
 // that axis (G_mu,nu is odd along it).
-__global__ void k_green_fill(c128* __restrict__ grid, const c128* __restrict__ table, int mu,
+template <typename T>
+__global__ void k_green_fill(T* __restrict__ grid, const c128* __restrict__ table, int mu,
                              int nu, int nx, int ny, int nz, int Mx, int My, int Mz) {
   const long long total = (long long)Mx * My * Mz;
   const long long tsz = (long long)nx * ny * nz;
@@ -83,12 +88,14 @@ __global__ void k_green_fill(c128* __restrict__ grid, const c128* __restrict__ t
       out = table[comp * tsz + ((long long)az * ny + ay) * nx + ax];
       if (flip) out = mk<double>(-out.x, -out.y);
     }
-    grid[i] = out;
+    grid[i] = store_as(out, (T*)nullptr);
   }
 }
 
-__global__ void k_octant(const c128* __restrict__ grid, c128* __restrict__ D, int Mx, int My,
-                         int Mz, double inv) {
+// octant of the transformed grid, scaled by inv; also as double-float when Ddf
+template <typename T>
+__global__ void k_octant(const T* __restrict__ grid, c128* __restrict__ D, cdf* __restrict__ Ddf,
+                         int Mx, int My, int Mz, double inv) {
   const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = Mz / 2 + 1;
   const long long total = (long long)hx * hy * hz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -97,8 +104,10 @@ __global__ void k_octant(const c128* __restrict__ grid, c128* __restrict__ D, in
     const long long q = i / hx;
     const int fy = (int)(q % hy);
     const int fz = (int)(q / hy);
-    const c128 v = grid[((long long)fz * My + fy) * Mx + fx];
-    D[i] = mk<double>(v.x * inv, v.y * inv);
+    const c128 v = to128(grid[((long long)fz * My + fy) * Mx + fx]);
+    const c128 sv = mk<double>(v.x * inv, v.y * inv);
+    D[i] = sv;
+    if (Ddf) Ddf[i] = to_cdf(sv);
   }
 }
 
@@ -113,6 +122,95 @@ static int grid_for(long long n) {
   if (b > 152LL * 16) b = 152LL * 16;
   if (b < 1) b = 1;
   return (int)b;
+}
+
+template <typename R> Work<R>& dwork(dda_t h);
+template <> Work<double>& dwork<double>(dda_t h) { return h->w64; }
+template <> Work<df>& dwork<df>(dda_t h) { return h->wdf; }
+
+// One component (mu, nu) with the register-resident passes in arithmetic R
+// (double or double-float): fill, x pass grid -> grid2, y pass grid2 -> grid,
+// z pass grid -> grid2, octant.  Component (mu, nu) is even or odd along y and
+// z, and transforms along the other axes keep that: line y > My/2 is sy times
+// line My - y.  So the x pass runs only on rows y <= My/2, z <= Mz/2, the y
+// pass only on planes z <= Mz/2 and reads rows y <= My/2 (mirroring the rest),
+// and the z pass reads planes z <= Mz/2.
+template <typename R>
+cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const c128* table,
+                                 const int comp[2], int c, double inv) {
+  const Geom& g = h->g;
+  cudaStream_t st = h->stream;
+  const long long full = (long long)g.Mx * g.My * g.Mz;
+  const long long oct = g.oct();
+  const cpx<R>* twx = dwork<R>(h).tw;
+  const cpx<R>* twy = twx + g.Mx;
+  const cpx<R>* twz = twy + g.My;
+  tr_begin(g.tr, st);
+  k_green_fill<cpx<R>><<<grid_for(full), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
+                                                       g.nz, g.Mx, g.My, g.Mz); count_launch();
+  tr_end(g.tr, st, TR_DB_GREEN);
+  tr_begin(g.tr, st);
+  const int hx = g.Mx / 2 + 1, hy = g.My / 2 + 1, hz = g.Mz / 2 + 1;
+  const int mu = comp[0], nu = comp[1];
+  const int sy = ((mu == 1) != (nu == 1)) ? -1 : 1;
+  const int sz = ((mu == 2) != (nu == 2)) ? -1 : 1;
+  FastArgs fa{};
+  fa.st = st;
+  fa.in = grid; fa.out = grid2; fa.tw = twx;
+  fa.nrows = hy * hz; fa.ny = hy; fa.My = g.My;
+  cudaError_t e;
+  if ((e = fast_pass<R>(g.Mx, FP_XFULL, fa)) != cudaSuccess) return e;
+  fa.in = grid2; fa.out = grid; fa.tw = twy; fa.nrows = hx; fa.nz = hz; fa.Mx = g.Mx;
+  fa.msign = sy;
+  if ((e = fast_pass<R>(g.My, FP_SFULL, fa)) != cudaSuccess) return e;
+  fa.in = grid; fa.out = grid2; fa.tw = twz; fa.nrows = hy * g.Mx; fa.nz = 1;
+  fa.Mx = g.My * g.Mx; fa.msign = sz;
+  if ((e = fast_pass<R>(g.Mz, FP_SFULL, fa)) != cudaSuccess) return e;
+  tr_end(g.tr, st, TR_DB_LINES);
+  tr_begin(g.tr, st);
+  cdf* ddf = std::is_same<R, df>::value ? h->wdf.D + c * oct : nullptr;
+  k_octant<cpx<R>><<<grid_for(oct), 256, 0, st>>>(grid2, h->w64.D + c * oct, ddf, g.Mx, g.My, g.Mz,
+                                                  inv); count_launch();
+  tr_end(g.tr, st, TR_DB_OCTANT);
+  return cudaGetLastError();
+}
+
+// One component with the shared-memory Stockham passes (FP64, in place).
+cudaError_t build_component_generic(dda_t h, c128* grid, const c128* table, const int comp[2],
+                                    int c, double inv) {
+  const Geom& g = h->g;
+  cudaStream_t st = h->stream;
+  const long long full = (long long)g.Mx * g.My * g.Mz;
+  const long long oct = g.oct();
+  const c128* twx = h->w64.tw;
+  const c128* twy = twx + g.Mx;
+  const c128* twz = twy + g.My;
+  tr_begin(g.tr, st);
+  k_green_fill<c128><<<grid_for(full), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
+                                                     g.nz, g.Mx, g.My, g.Mz); count_launch();
+  tr_end(g.tr, st, TR_DB_GREEN);
+  tr_begin(g.tr, st);
+  // x lines (contiguous) over the whole grid; then only the octant is
+  // needed, so y lines run for kx <= Mx/2 and z lines for kx <= Mx/2,
+  // ky <= My/2 (the other entries are left untransformed).
+  const int hx = g.Mx / 2 + 1, hy = g.My / 2 + 1;
+  cudaError_t e = launch_lines<double>(g, grid, grid, g.px, twx, false, g.Mx, g.Mx,
+                                       g.My * g.Mz, 1, 1, true, 1, g.Mx, 0, 0, 1, g.Mx, 0, 0, st);
+  if (e != cudaSuccess) return e;
+  e = launch_lines<double>(g, grid, grid, g.py, twy, false, g.My, g.My, hx, g.Mz, 1, false,
+                           g.Mx, 1, (long long)g.My * g.Mx, 0, g.Mx, 1,
+                           (long long)g.My * g.Mx, 0, st);
+  if (e != cudaSuccess) return e;
+  e = launch_lines<double>(g, grid, grid, g.pz, twz, false, g.Mz, g.Mz, hx, hy, 1, false,
+                           (long long)g.My * g.Mx, 1, g.Mx, 0, (long long)g.My * g.Mx, 1,
+                           g.Mx, 0, st);
+  if (e != cudaSuccess) return e;
+  tr_end(g.tr, st, TR_DB_LINES);
+  tr_begin(g.tr, st);
+  k_octant<c128><<<grid_for(oct), 256, 0, st>>>(grid, h->w64.D + c * oct, nullptr, g.Mx, g.My,
+                                                g.Mz, inv); count_launch();
+  tr_end(g.tr, st, TR_DB_OCTANT);
+  return cudaGetLastError();
 }
 
 }  // namespace dda
@@ -131,12 +229,24 @@ int dda_build_D_internal(dda_t h, bool want32) {
       return dda_fail(h, DDA_ERR_OOM, "cannot allocate the FP64 D-matrix octant");
     }
   }
-  c128* grid = nullptr;
-  c128* grid2 = nullptr;
-  c128* table = nullptr;
   const long long tsz = (long long)g.nx * g.ny * g.nz;
   const bool fast = g.engine == 0 && fast_supported(g.Mx) && fast_supported(g.My) &&
                     fast_supported(g.Mz);
+  // FP32_REFINED builds in double-float when every axis has register-resident
+  // passes: the FP64-class D-matrix then costs FP32-pipe arithmetic (the FP64
+  // pipe is ~1/58 of it on this part), and the double-float octant also
+  // serves the refinement's residual products
+  const bool use_df = want32 && fast && h->wdf.tw != nullptr;
+  if (use_df && !h->wdf.D) {
+    if (cudaMalloc(&h->wdf.D, 6 * oct * sizeof(cdf)) != cudaSuccess) {
+      h->wdf.D = nullptr;
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "cannot allocate the double-float D-matrix octant");
+    }
+  }
+  void* grid = nullptr;
+  void* grid2 = nullptr;
+  c128* table = nullptr;
   if (cudaMalloc(&grid, full * sizeof(c128)) != cudaSuccess ||
       cudaMalloc(&table, 6 * tsz * sizeof(c128)) != cudaSuccess ||
       (fast && cudaMalloc(&grid2, full * sizeof(c128)) != cudaSuccess)) {
@@ -150,61 +260,11 @@ int dda_build_D_internal(dda_t h, bool want32) {
   tr_end(g.tr, st, TR_DB_GREEN);
   const int comps[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
   const double inv = 1.0 / (double)full;
-  const c128* twx = h->w64.tw;
-  const c128* twy = twx + g.Mx;
-  const c128* twz = twy + g.My;
   cudaError_t e = cudaSuccess;
   for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
-    tr_begin(g.tr, st);
-    k_green_fill<<<grid_for(full), 256, 0, st>>>(grid, table, comps[c][0], comps[c][1], g.nx, g.ny,
-                                                 g.nz, g.Mx, g.My, g.Mz); count_launch();
-    tr_end(g.tr, st, TR_DB_GREEN);
-    tr_begin(g.tr, st);
-    // x lines (contiguous) over the whole grid; then only the octant is
-    // needed, so y lines run for kx <= Mx/2 and z lines for kx <= Mx/2,
-    // ky <= My/2 (the other entries are left untransformed).
-    const int hx = g.Mx / 2 + 1, hy = g.My / 2 + 1;
-    const c128* spec = grid;
-    if (grid2) {   // register-resident passes, grid -> grid2 -> grid -> grid2
-      // Component (mu, nu) is even or odd along y and z, and transforms along
-      // the other axes keep that: line y > My/2 is sy times line My - y.  So
-      // the x pass runs only on rows y <= My/2, z <= Mz/2, the y pass only on
-      // planes z <= Mz/2 and reads rows y <= My/2 (mirroring the rest), and
-      // the z pass reads planes z <= Mz/2.
-      const int mu = comps[c][0], nu = comps[c][1];
-      const int sy = ((mu == 1) != (nu == 1)) ? -1 : 1;
-      const int sz = ((mu == 2) != (nu == 2)) ? -1 : 1;
-      const int hz = g.Mz / 2 + 1;
-      FastArgs fa{};
-      fa.st = st;
-      fa.in = grid; fa.out = grid2; fa.tw = twx;
-      fa.nrows = hy * hz; fa.ny = hy; fa.My = g.My;
-      if ((e = fast_pass<double>(g.Mx, FP_XFULL, fa)) != cudaSuccess) break;
-      fa.in = grid2; fa.out = grid; fa.tw = twy; fa.nrows = hx; fa.nz = hz; fa.Mx = g.Mx;
-      fa.msign = sy;
-      if ((e = fast_pass<double>(g.My, FP_SFULL, fa)) != cudaSuccess) break;
-      fa.in = grid; fa.out = grid2; fa.tw = twz; fa.nrows = hy * g.Mx; fa.nz = 1;
-      fa.Mx = g.My * g.Mx; fa.msign = sz;
-      if ((e = fast_pass<double>(g.Mz, FP_SFULL, fa)) != cudaSuccess) break;
-      spec = grid2;
-    } else {       // shared-memory Stockham passes, in place
-      e = launch_lines<double>(g, grid, grid, g.px, twx, false, g.Mx, g.Mx,
-                               g.My * g.Mz, 1, 1, true, 1, g.Mx, 0, 0, 1, g.Mx, 0, 0, st);
-      if (e != cudaSuccess) break;
-      e = launch_lines<double>(g, grid, grid, g.py, twy, false, g.My, g.My, hx, g.Mz, 1, false,
-                               g.Mx, 1, (long long)g.My * g.Mx, 0, g.Mx, 1,
-                               (long long)g.My * g.Mx, 0, st);
-      if (e != cudaSuccess) break;
-      e = launch_lines<double>(g, grid, grid, g.pz, twz, false, g.Mz, g.Mz, hx, hy, 1, false,
-                               (long long)g.My * g.Mx, 1, g.Mx, 0, (long long)g.My * g.Mx, 1,
-                               g.Mx, 0, st);
-      if (e != cudaSuccess) break;
-    }
-    tr_end(g.tr, st, TR_DB_LINES);
-    tr_begin(g.tr, st);
-    k_octant<<<grid_for(oct), 256, 0, st>>>(spec, h->w64.D + c * oct, g.Mx, g.My, g.Mz, inv); count_launch();
-    tr_end(g.tr, st, TR_DB_OCTANT);
-    e = cudaGetLastError();
+    if (use_df) e = build_component_fast<df>(h, (cdf*)grid, (cdf*)grid2, table, comps[c], c, inv);
+    else if (fast) e = build_component_fast<double>(h, (c128*)grid, (c128*)grid2, table, comps[c], c, inv);
+    else e = build_component_generic(h, (c128*)grid, table, comps[c], c, inv);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   tr_flush(g.tr);
@@ -213,6 +273,7 @@ int dda_build_D_internal(dda_t h, bool want32) {
   cudaFree(table);
   if (e != cudaSuccess) return dda_cuda_fail(h, e, "D-matrix build");
   h->w64.have_D = true;
+  h->wdf.have_D = use_df;
   if (want32) {
     if (!h->w32.D) {
       if (cudaMalloc(&h->w32.D, 6 * oct * sizeof(c64)) != cudaSuccess) {

@@ -12,7 +12,7 @@ cudaError_t run_pass(int pass, const FastArgs& a) {
   const cpx<R>* tw = (const cpx<R>*)a.tw;
   switch (pass) {
     case FP_XFWD:
-      return P::xfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.lat, (const cpx<R>*)a.beta, a.n_occ,
+      return P::xfwd((const typename P::V*)a.in, (cpx<R>*)a.out, a.lat, (const cpx<R>*)a.beta, a.n_occ,
                      a.nrows, tw, a.adj, a.nrhs, a.bstride, a.skip, a.st);
     case FP_YFWD:
       return P::yfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.nrhs, a.skip, a.st);
@@ -22,7 +22,7 @@ cudaError_t run_pass(int pass, const FastArgs& a) {
     case FP_YINV:
       return P::yinv((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.nrhs, a.skip, a.st);
     case FP_XINV:
-      return P::xinv((const cpx<R>*)a.in, (const cpx<R>*)a.x, (cpx<R>*)a.out, a.lat,
+      return P::xinv((const cpx<R>*)a.in, (const typename P::V*)a.x, (typename P::V*)a.out, a.lat,
                      (const cpx<R>*)a.beta, a.n_occ, a.nrows, tw, a.adj, a.dotp, a.nrhs, a.bstride,
                      a.skip, a.st);
     case FP_XFULL:

@@ -24,5 +24,10 @@ template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a) 
 }
 template cudaError_t fast_pass<float>(int, int, const FastArgs&);
 template cudaError_t fast_pass<double>(int, int, const FastArgs&);
+template <> cudaError_t fast_pass<df>(int M, int pass, const FastArgs& a) {
+  if (M == 270) return fast_pass_270_df(pass, a);
+  if (M == 256) return fast_pass_256_df(pass, a);
+  return fast_pass_small_df(M, pass, a);
+}
 
 }  // namespace dda

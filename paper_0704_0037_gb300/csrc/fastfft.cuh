@@ -30,6 +30,25 @@ template <int M1, int M2> constexpr int kQ = M1 > M2 ? M1 : M2;
 template <typename R>
 __device__ __forceinline__ cpx<R> zero() { return mk<R>((R)0, (R)0); }
 
+// Element type of the product's input and output vectors: the arithmetic
+// type for complex64 and complex128, complex128 for the double-float passes
+// (their vectors are the FP64 refinement's).
+template <typename R> struct VecOf { using type = cpx<R>; };
+template <> struct VecOf<df> { using type = c128; };
+
+__device__ __forceinline__ c64 vload(const c64& v, c64*) { return v; }
+__device__ __forceinline__ c128 vload(const c128& v, c128*) { return v; }
+__device__ __forceinline__ cdf vload(const c128& v, cdf*) { return to_cdf(v); }
+__device__ __forceinline__ c64 vstore(const c64& v) { return v; }
+__device__ __forceinline__ c128 vstore(const c128& v) { return v; }
+__device__ __forceinline__ c128 vstore(const cdf& v) { return to128(v); }
+template <typename R> __device__ __forceinline__ cpx<R> vin(const typename VecOf<R>::type& v) {
+  return vload(v, (cpx<R>*)nullptr);
+}
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(df v) { return df_to_double(v); }
+
 template <typename R>
 __device__ __forceinline__ void load_tw(cpx<R>* s_tw, const cpx<R>* __restrict__ tw, int M, int nt) {
   for (int i = threadIdx.x; i < M; i += nt) s_tw[i] = tw[i];
@@ -280,7 +299,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict
 template <int M> constexpr int kLD = (M % 2 == 1) ? M : M + 1;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const cpx<R>* __restrict__ x,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const typename VecOf<R>::type* __restrict__ x,
                                                           cpx<R>* __restrict__ B1, LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
@@ -298,7 +317,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const cpx<R>* __res
   load_tw(s_tw, tw, M, NT);
   for (int i = threadIdx.x; i < T * LD; i += NT) a[i] = zero<R>();
   __syncthreads();
-  const cpx<R>* xc = x + (long long)cc * n_occ;
+  const typename VecOf<R>::type* xc = x + (long long)cc * n_occ;
   {
     // one warp per row: the dipoles of a row are contiguous in x
     constexpr int NW = NT / 32;
@@ -308,7 +327,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const cpx<R>* __res
       if (row >= nrows) break;
       const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
       for (long long i = s0 + lane; i < s1; i += 32) {
-        cpx<R> v = xc[i];
+        cpx<R> v = vin<R>(xc[i]);
         if (CONJ) v = conjg(v);
         a[t * LD + lat.xi[i]] = beta[lat.mat[i] * 3 + c] * v;
       }
@@ -356,8 +375,9 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const cpx<R>* __res
 // occupied x; grid (ceil(nrows/T), 3)
 template <typename R, int M1, int M2, int T, bool CONJ>
 __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __restrict__ B1,
-                                                          const cpx<R>* __restrict__ x,
-                                                          cpx<R>* __restrict__ y, LatticeDev lat,
+                                                          const typename VecOf<R>::type* __restrict__ x,
+                                                          typename VecOf<R>::type* __restrict__ y,
+                                                          LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
                                                           const cpx<R>* __restrict__ tw,
@@ -407,8 +427,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
     for (int i = 0; i < M1; ++i) at[j + M2 * i] = v[i];
   }
   __syncthreads();
-  const cpx<R>* xc = x + (long long)cc * n_occ;
-  cpx<R>* yc = y + (long long)cc * n_occ;
+  const typename VecOf<R>::type* xc = x + (long long)cc * n_occ;
+  typename VecOf<R>::type* yc = y + (long long)cc * n_occ;
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double dre = 0.0, dim = 0.0;       // partial x^T y (bilinear) when dotp is set
@@ -416,19 +436,21 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
     const int row = r0 + tt;
     if (row >= nrows) break;
     const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
-    R fr = 0, fi = 0;
+    R fr = (R)0, fi = (R)0;
     for (long long i = s0 + lane; i < s1; i += 32) {
-      cpx<R> v = xc[i];
+      const cpx<R> xv = vin<R>(xc[i]);
+      cpx<R> v = xv;
       if (CONJ) v = conjg(v);
       cpx<R> o = v - beta[lat.mat[i] * 3 + c] * a[tt * LD + lat.xi[i]];
       if (CONJ) o = conjg(o);
-      yc[i] = o;
-      const cpx<R> xv = xc[i];
-      fr += xv.x * o.x - xv.y * o.y;
-      fi += xv.x * o.y + xv.y * o.x;
+      yc[i] = vstore(o);
+      if (dotp) {
+        fr = fr + (xv.x * o.x - xv.y * o.y);
+        fi = fi + (xv.x * o.y + xv.y * o.x);
+      }
     }
-    dre += (double)fr;
-    dim += (double)fi;
+    dre += to_d(fr);
+    dim += to_d(fi);
   }
   if (dotp) {
     // block partial of the product's input times its output, for the solver
@@ -558,7 +580,8 @@ struct Passes {
     count_launch();
     return cudaGetLastError();
   }
-  static cudaError_t xfwd(const cpx<R>* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,
+  using V = typename VecOf<R>::type;
+  static cudaError_t xfwd(const V* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,
                           long long n_occ, int nrows, const cpx<R>* tw, bool adj, int nrhs,
                           int bstride, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
@@ -602,7 +625,7 @@ struct Passes {
     count_launch();
     return cudaGetLastError();
   }
-  static cudaError_t xinv(const cpx<R>* B1, const cpx<R>* x, cpx<R>* y, const LatticeDev& lat,
+  static cudaError_t xinv(const cpx<R>* B1, const V* x, V* y, const LatticeDev& lat,
                           const cpx<R>* beta, long long n_occ, int nrows, const cpx<R>* tw, bool adj,
                           double* dotp, int nrhs, int bstride, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);

@@ -18,7 +18,7 @@ namespace dda {
 enum TraceId {
   TR_P1_C64, TR_P2_C64, TR_P3_C64, TR_P4_C64, TR_P5_C64,
   TR_P1_C128, TR_P2_C128, TR_P3_C128, TR_P4_C128, TR_P5_C128,
-  TR_DB_GREEN, TR_DB_LINES, TR_DB_OCTANT, TR_FARFIELD, TR_QSUMS, TR_COUNT
+  TR_DB_GREEN, TR_DB_LINES, TR_DB_OCTANT, TR_FARFIELD, TR_QSUMS, TR_PRODUCT_DF, TR_COUNT
 };
 struct Tracer {
   bool on = false;
@@ -69,6 +69,7 @@ struct Work {
   cpx<R>* beta = nullptr;   // [nrhs][n_mat][3]
   bool have_D = false;
   int cap = 0;              // right-hand sides B1 and B2 hold
+  int cap_beta = 0;         // entries of beta (double-float tables only)
 };
 
 // Grow the product buffers of w to hold min(want, what fits) right-hand
@@ -96,6 +97,14 @@ cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const Fft
                          long long out_so, long long out_sb, cudaStream_t st,
                          const int* skip = nullptr);
 
+// y = A x in double-float arithmetic for complex128 vectors x, y
+// ([nrhs][3][n_occ]); register-resident passes only (cudaErrorNotSupported
+// when an axis has no split).  beta: complex128 [nrhs][n_mat][3], converted
+// into w.beta; skip as launch_matvec.
+cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, const c128* beta,
+                             int n_mat, const c128* x, c128* y, int nrhs, cudaStream_t st,
+                             const int* skip = nullptr);
+
 FftPlan make_plan(int M);
 int smooth_size(int lo);
 
@@ -117,6 +126,7 @@ struct dda_ctx {
   uint8_t* d_mat = nullptr;
   dda::Work<double> w64;
   dda::Work<float> w32;
+  dda::Work<dda::df> wdf;         // double-float D-matrix and buffers (FP32_REFINED residuals)
   dda::Tracer tracer;
   int beta_nrhs = 0;              // RHS count of the current beta tables
   int beta_cap = 0;               // RHS capacity of the beta allocations
@@ -224,6 +234,11 @@ template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_270(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_256(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_small(int M, int pass, const FastArgs& a);
+// double-float passes (fast_df_*.cu); fast_pass<df> dispatches to them
+cudaError_t fast_pass_270_df(int pass, const FastArgs& a);
+cudaError_t fast_pass_256_df(int pass, const FastArgs& a);
+cudaError_t fast_pass_small_df(int M, int pass, const FastArgs& a);
+template <> cudaError_t fast_pass<df>(int M, int pass, const FastArgs& a);
 }  // namespace dda
 
 namespace dda {

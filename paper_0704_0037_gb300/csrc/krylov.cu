@@ -1030,7 +1030,16 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
         left -= ru.iters - it0;
         outer++;
         k_axpy64<<<ru.nb, kVT, 0, ru.st>>>(x64, x32, n, rn); count_launch();
-        RK(matvec<double>(ru, x64, w64, false));
+        if (h->wdf.have_D) {       // residual product in double-float
+          cudaError_t e = launch_matvec_df(h->g, h->lat(), h->wdf,
+                                           h->w64.beta + (long long)r * h->n_mat * 3, h->n_mat,
+                                           x64, w64, 1, ru.st);
+          if (e != cudaSuccess) return dda_cuda_fail(h, e, "double-float residual product");
+          ru.matvecs++;
+          ru.matvecs64++;
+        } else {
+          RK(matvec<double>(ru, x64, w64, false));
+        }
         k_resid<<<ru.nb, kVT, 0, ru.st>>>(b64, w64, r64, n, ru.part); count_launch();
         k_take_norm<<<1, kVT, 0, ru.st>>>(ru.ds, ru.part, ru.nb); count_launch();
         LK(h);
@@ -1306,6 +1315,10 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
   if (refined) {
     rc = ensure_work_cap<float>(h, h->w32, nrhs);
     if (rc != DDA_OK) return rc;
+    if (h->wdf.have_D) {
+      rc = ensure_work_cap<df>(h, h->wdf, nrhs);
+      if (rc != DDA_OK) return rc;
+    }
   }
   BatchMem* m = (BatchMem*)h->bm;
   BRun b;
@@ -1420,8 +1433,11 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
       std::vector<int> inner_status(nrhs);
       for (int r = 0; r < nrhs; ++r) inner_status[r] = m->hs[r].status;
       k_axpy64_b<<<vg, kVT, 0, st>>>(x64, x32, n, m->dvals + nrhs, m->off); count_launch();
-      cudaError_t e = launch_matvec<double>(h->g, h->lat(), h->w64, h->w64.beta, h->n_mat, x64, w64,
-                                            nrhs, false, st, nullptr, nullptr, m->off);
+      cudaError_t e = h->wdf.have_D
+          ? launch_matvec_df(h->g, h->lat(), h->wdf, h->w64.beta, h->n_mat, x64, w64, nrhs, st,
+                             m->off)
+          : launch_matvec<double>(h->g, h->lat(), h->w64, h->w64.beta, h->n_mat, x64, w64, nrhs,
+                                  false, st, nullptr, nullptr, m->off);
       if (e != cudaSuccess) return dda_cuda_fail(h, e, "batched product");
       k_resid_b<<<vg, kVT, 0, st>>>(b64, w64, r64, n, m->part, m->off); count_launch();
       k_take_norms_b<<<nrhs, kVT, 0, st>>>(m->ds, m->part, b.nb, m->off); count_launch();

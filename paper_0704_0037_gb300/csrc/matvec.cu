@@ -408,6 +408,56 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
   return cudaGetLastError();
 }
 
+__global__ void k_beta_df(const c128* __restrict__ b, cdf* __restrict__ o, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = to_cdf(b[i]);
+}
+
+cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, const c128* beta,
+                             int n_mat, const c128* x, c128* y, int nrhs, cudaStream_t st,
+                             const int* skip) {
+  if (!(fast_supported(g.Mx) && fast_supported(g.My) && fast_supported(g.Mz)) || g.engine != 0)
+    return cudaErrorNotSupported;
+  const int bstride = n_mat * 3;
+  // beta as double-float, grown with the number of right-hand sides
+  if (w.cap_beta < nrhs * bstride) {
+    cudaFree(w.beta);
+    w.beta = nullptr;
+    w.cap_beta = 0;
+    cudaError_t e = cudaMalloc(&w.beta, (size_t)nrhs * bstride * sizeof(cdf));
+    if (e != cudaSuccess) return e;
+    w.cap_beta = nrhs * bstride;
+  }
+  const int nb = nrhs * bstride;
+  k_beta_df<<<(nb + 127) / 128, 128, 0, st>>>(beta, w.beta, nb); count_launch();
+  const long long nv = 3LL * g.n_occ;
+  const cdf* twx = w.tw;
+  const cdf* twy = w.tw + g.Mx;
+  const cdf* twz = w.tw + g.Mx + g.My;
+  const int cap = w.cap > 0 ? w.cap : 1;
+  cudaError_t e = cudaSuccess;
+  for (int r0 = 0; r0 < nrhs; r0 += cap) {
+    const int cnt = nrhs - r0 < cap ? nrhs - r0 : cap;
+    FastArgs fa{};
+    fa.lat = lat; fa.beta = w.beta + (long long)r0 * bstride; fa.D = w.D; fa.n_occ = g.n_occ;
+    fa.nrows = g.nrows; fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = false;
+    fa.st = st; fa.nrhs = cnt; fa.bstride = bstride; fa.skip = skip ? skip + r0 : nullptr;
+    tr_begin(g.tr, st);
+    fa.in = x + r0 * nv; fa.out = w.B1; fa.tw = twx;
+    if ((e = fast_pass<df>(g.Mx, FP_XFWD, fa)) != cudaSuccess) return e;
+    fa.in = w.B1; fa.out = w.B2; fa.tw = twy;
+    if ((e = fast_pass<df>(g.My, FP_YFWD, fa)) != cudaSuccess) return e;
+    fa.out = w.B2; fa.tw = twz;
+    if ((e = fast_pass<df>(g.Mz, FP_ZCONV, fa)) != cudaSuccess) return e;
+    fa.in = w.B2; fa.out = w.B1; fa.tw = twy;
+    if ((e = fast_pass<df>(g.My, FP_YINV, fa)) != cudaSuccess) return e;
+    fa.in = w.B1; fa.x = x + r0 * nv; fa.out = y + r0 * nv; fa.tw = twx;
+    if ((e = fast_pass<df>(g.Mx, FP_XINV, fa)) != cudaSuccess) return e;
+    tr_end(g.tr, st, TR_PRODUCT_DF);
+  }
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_matvec<float>(const Geom&, const LatticeDev&, Work<float>&,
                                           const c64*, int, const c64*, c64*, int, bool,
                                           cudaStream_t, double*, int*, const int*);

@@ -23,7 +23,7 @@ DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM, DDA_ERR_STATE, DDA_ERR_NONFINITE, DDA_ER
     -1, -2, -3, -4, -5, -6
 DDA_CM, DDA_RR, DDA_LDR, DDA_CLDR = 0, 1, 2, 3
 DDA_QMR_CS, DDA_BICG_CS, DDA_BICGSTAB, DDA_CGNR = 0, 1, 2, 3
-DDA_FP64, DDA_FP32_REFINED = 0, 1
+DDA_FP64, DDA_FP32_REFINED, DDA_FP64_PAIR = 0, 1, 2
 
 STATUS_NAMES = {0: "ok", 1: "not_converged", 2: "breakdown", -1: "err_arg", -2: "err_cuda",
                 -3: "err_oom", -4: "err_state", -5: "err_nonfinite", -6: "err_timeout"}
@@ -189,7 +189,7 @@ def dda_set_beta(h, pol_prescription, prop, pol):
 
 def dda_matvec(h, prec, x, y, nrhs=1):
     import torch
-    dt = torch.complex128 if prec == DDA_FP64 else torch.complex64
+    dt = torch.complex64 if prec == DDA_FP32_REFINED else torch.complex128
     return _check(h, lib().dda_matvec(h, int(prec), _dev_ptr(x, dt), _dev_ptr(y, dt), int(nrhs)))
 
 

@@ -32,7 +32,7 @@ CASES = [
 def _run(p, prob, prec, presc, props, pols, x, adjoint=False):
     torch, dda = need_gpu()
     dda.dda_set_beta(p.h, dda.POL[presc], props, pols)
-    dt = torch.complex128 if prec == dda.DDA_FP64 else torch.complex64
+    dt = torch.complex64 if prec == dda.DDA_FP32_REFINED else torch.complex128
     xd = torch.from_numpy(x).to(device="cuda", dtype=dt)
     yd = torch.empty_like(xd)
     f = dda.dda_matvec_adjoint if adjoint else dda.dda_matvec
@@ -67,6 +67,45 @@ def test_matvec_fp32(name, occ, m):
         x = inputs.random_vectors(8, 1, p.n_occ)
         y, ref = _run(p, prob, dda.DDA_FP32_REFINED, "ldr", [(0, 0, 1)], [(1, 0, 0)], x)
         assert rel_l2(y, ref) <= 1e-5
+
+
+DF_CASES = [
+    ("sphere16", inputs.sphere(16), [1.5]),                                      # 32^3
+    ("random16x64x16", inputs.random_occupancy(16, 64, 16, 0.5, seed=4, n_mat=2),
+     [1.5 + 0.1j, 2.0]),                                                        # 32 x 128 x 32
+    ("ellipsoid64x16x16", inputs.ellipsoid(64, 16, 16), [1.33]),                 # 128 x 32 x 32
+]
+
+
+@pytest.mark.parametrize("name,occ,m", DF_CASES, ids=[c[0] for c in DF_CASES])
+def test_matvec_double_float(name, occ, m):
+    """The double-float product (FP32_REFINED build on a grid with
+    register-resident passes; used for the refinement residuals) is within
+    FP64 tolerance of the oracle, for several right-hand sides at once."""
+    torch, dda = need_gpu()
+    p, prob = twin(occ, m, 0.55)
+    with p:
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+        x = inputs.random_vectors(9, 2, p.n_occ)
+        props = [(0.6, 0.0, 0.8), (0.0, 0.0, 1.0)]
+        pols = [(0.8, 0.0, -0.6), (0.0, 1.0, 0.0)]
+        y, ref = _run(p, prob, dda.DDA_FP64_PAIR, "cldr", props, pols, x)
+        assert rel_l2(y, ref) <= 1e-12
+        # the FP64 octant derived from the double-float build serves FP64 products
+        y64, _ = _run(p, prob, dda.DDA_FP64, "cldr", props, pols, x)
+        assert rel_l2(y64, ref) <= 1e-12
+
+
+def test_double_float_needs_its_build():
+    torch, dda = need_gpu()
+    p, prob = twin(inputs.sphere(16), [1.5], 0.5)
+    with p:
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP64)
+        dda.dda_set_beta(p.h, dda.DDA_LDR, [(0, 0, 1)], [(1, 0, 0)])
+        x = torch.zeros((1, 3, p.n_occ), dtype=torch.complex128, device="cuda")
+        with pytest.raises(dda.DDAError) as ei:
+            dda.dda_matvec(p.h, dda.DDA_FP64_PAIR, x, torch.empty_like(x))
+        assert ei.value.status == dda.DDA_ERR_STATE
 
 
 def test_matvec_multi_rhs_and_adjoint():
@@ -160,7 +199,7 @@ def _sampled_reference(pos, beta, kd, x, idx):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined", "fp64_pair"])
 def test_matvec_full_size_sampled(prec_name):
     """Sphere x = 40, m = 1.05 at 134^3 (1,260,552 dipoles), padded 270^3:
     sampled outputs against the direct sum."""
@@ -169,11 +208,11 @@ def test_matvec_full_size_sampled(prec_name):
     p = dda.Particle(occ, [1.05], 40.0, volume_corrected=True)
     with p:
         assert p.n_occ == 1260552 and p.grid == (270, 270, 270)
-        prec = dda.PREC[prec_name]
-        dda.dda_build_Dmatrix(p.h, prec)
+        prec = dda.PREC[prec_name] if prec_name != "fp64_pair" else dda.DDA_FP64_PAIR
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP64 if prec == dda.DDA_FP64 else dda.DDA_FP32_REFINED)
         dda.dda_set_beta(p.h, dda.DDA_LDR, [(0, 0, 1)], [(1, 0, 0)])
         x = inputs.random_vectors(21, 1, p.n_occ)
-        dt = torch.complex128 if prec == dda.DDA_FP64 else torch.complex64
+        dt = torch.complex64 if prec == dda.DDA_FP32_REFINED else torch.complex128
         xd = torch.from_numpy(x).to("cuda", dt)
         yd = torch.empty_like(xd)
         dda.dda_matvec(p.h, prec, xd, yd)
@@ -186,4 +225,4 @@ def test_matvec_full_size_sampled(prec_name):
         ref = _sampled_reference(prob.pos, beta, prob.kd, x[0], idx)
         scale = np.sqrt(np.mean(np.abs(ref) ** 2))
         err = np.abs(y[:, idx] - ref).max() / scale
-        assert err <= (1e-12 if prec == dda.DDA_FP64 else 1e-5), err
+        assert err <= (1e-5 if prec == dda.DDA_FP32_REFINED else 1e-12), err
