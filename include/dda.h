@@ -178,7 +178,10 @@ typedef struct {
  *   info      : host array of nrhs dda_solve_info.
  * Also leaves beta set for these RHS (as dda_set_beta).  Requires
  * dda_build_Dmatrix for DDA_FP64, and with DDA_FP32_REFINED for that mode.
- * Returns the worst per-RHS status (errors first, then BREAKDOWN,
+ * With DDA_QMR_CS and no res_hist the right-hand sides are solved together as
+ * dda_solve_batch does (same iterates; info[r].seconds is then the whole
+ * call's time); otherwise one after the other, with the scalars read every
+ * step.  Returns the worst per-RHS status (errors first, then BREAKDOWN,
  * NOT_CONVERGED).  Synchronises the stream.
  */
 int dda_solve(dda_t h, const dda_solve_opts* opts, int nrhs, const double* prop_host,

@@ -332,7 +332,9 @@ static int matvec_common(dda_t h, int prec, const void* x, void* y, int nrhs, bo
   cudaError_t e;
   if (prec == DDA_FP64) {
     if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "FP64 D-matrix not built");
-    const int rc = ensure_work_cap<double>(h, h->w64, nrhs);
+    int rc = ensure_d64(h);
+    if (rc != DDA_OK) return rc;
+    rc = ensure_work_cap<double>(h, h->w64, nrhs);
     if (rc != DDA_OK) return rc;
     e = launch_matvec<double>(h->g, h->lat(), h->w64, h->w64.beta, h->n_mat, (const c128*)x,
                               (c128*)y, nrhs, adjoint, h->stream);
@@ -380,6 +382,11 @@ extern "C" int dda_solve(dda_t h, const dda_solve_opts* o, int nrhs, const doubl
   if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "FP64 D-matrix not built");
   if (o->prec == DDA_FP32_REFINED && !h->w32.have_D)
     return dda_fail(h, DDA_ERR_STATE, "FP32 D-matrix not built");
+  // QMR-CS without a residual history runs on the batched driver (same
+  // arithmetic; the host reads the scalars every 8 steps instead of every
+  // step, and converged right-hand sides skip their products)
+  if (o->solver == DDA_QMR_CS && !hist)
+    return dda_solve_batch_internal(h, o, nrhs, prop, pol, P_dev, info);
   return dda_solve_internal(h, o, nrhs, prop, pol, P_dev, hist, hist_len, info);
 }
 

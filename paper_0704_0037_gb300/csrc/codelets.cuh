@@ -78,7 +78,7 @@ __host__ __device__ __forceinline__ cpx<R> tw_mul(cpx<R> z) {
   } else {
     constexpr R c = (R)kCos<m, N>;
     constexpr R s = INV ? (R)kSin<m, N> : (R)(-kSin<m, N>);
-    return mk<R>(z.x * c - z.y * s, z.x * s + z.y * c);
+    return z * mk<R>(c, s);
   }
 }
 

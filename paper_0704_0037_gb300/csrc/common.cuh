@@ -35,8 +35,7 @@ template <typename R, bool INV> __host__ __device__ __forceinline__ cpx<R> mul_m
 }
 // a * conj(w) when INV else a * w  (twiddles are stored for the forward sign)
 template <typename R, bool INV> __host__ __device__ __forceinline__ cpx<R> twiddle(cpx<R> a, cpx<R> w) {
-  return INV ? mk<R>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y)
-             : mk<R>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+  return INV ? a * conjg(w) : a * w;
 }
 
 // a * s + c for complex a, c and real s
@@ -154,6 +153,120 @@ __host__ __device__ __forceinline__ df operator*(df a, df b) {
 
 template <> struct __align__(16) cpx<df> { df x, y; };
 using cdf = cpx<df>;
+
+// Complex double-float on sm_100-class devices: the two real parts' high
+// words form one f32x2 register pair and the low words another, so each step
+// of the double-float algorithms above runs once for both parts (the same
+// roundings per part as the scalar form).
+#ifdef DDA_F32X2
+struct df2 { unsigned long long h, l; };   // (re.hi, im.hi), (re.lo, im.lo)
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ df2 dpack(const cpx<df>& a) {
+  return df2{pk2(a.x.hi, a.y.hi), pk2(a.x.lo, a.y.lo)};
+}
+__device__ __forceinline__ cpx<df> dunpack(df2 p) {
+  const c64 h = upk2(p.h), l = upk2(p.l);
+  cpx<df> r;
+  r.x = df(h.x, l.x);
+  r.y = df(h.y, l.y);
+  return r;
+}
+// componentwise double-float sum and product of the two parts
+__device__ __forceinline__ df2 dadd2(df2 a, df2 b) {
+  const unsigned long long s = f2add(a.h, b.h);
+  const unsigned long long bb = f2sub(s, a.h);
+  unsigned long long e = f2add(f2sub(a.h, f2sub(s, bb)), f2sub(b.h, bb));
+  e = f2add(e, f2add(a.l, b.l));
+  const unsigned long long h = f2add(s, e);
+  return df2{h, f2sub(e, f2sub(h, s))};
+}
+__device__ __forceinline__ df2 dmul2(df2 a, df2 b) {
+  // The rounded product comes from an fma with a zero addend the compiler
+  // cannot see through (a - a): a paired multiply followed by the paired add
+  // below may otherwise be contracted into one fused operation, which adds
+  // the product's rounding error a second time.
+  const unsigned long long z = f2sub(a.h, a.h);
+  const unsigned long long p = f2fma(a.h, b.h, z);
+  unsigned long long e = f2fma(a.h, b.h, f2sub(0ull, p));
+  e = f2fma(a.h, b.l, e);
+  e = f2fma(a.l, b.h, e);
+  const unsigned long long h = f2add(p, e);
+  return df2{h, f2sub(e, f2sub(h, p))};
+}
+// the pair (v, v) of a double-float scalar
+__device__ __forceinline__ df2 dsplat(df v) { return df2{pk2(v.hi, v.hi), pk2(v.lo, v.lo)}; }
+// multiply the first part by -1 (exact)
+__device__ __forceinline__ df2 dneg_re(df2 a) {
+  const unsigned long long m = pk2(-1.0f, 1.0f);
+  return df2{f2mul(a.h, m), f2mul(a.l, m)};
+}
+// (a + ib)(c + id) = (ac - bd) + i(ad + bc): (ac, ad) + (-bd, bc)
+__device__ __forceinline__ cpx<df> dcmul(const cpx<df>& z, const cpx<df>& w) {
+  const df2 wp = dpack(w);
+  const df2 ws{pk2(w.y.hi, w.x.hi), pk2(w.y.lo, w.x.lo)};
+  const df2 p1 = dmul2(dsplat(z.x), wp);
+  const df2 p2 = dmul2(dsplat(z.y), ws);
+  return dunpack(dadd2(p1, dneg_re(p2)));
+}
+#endif
+
+template <> __host__ __device__ __forceinline__ cpx<df> operator+<df>(cpx<df> a, cpx<df> b) {
+#ifdef DDA_F32X2
+  return dunpack(dadd2(dpack(a), dpack(b)));
+#else
+  return mk<df>(a.x + b.x, a.y + b.y);
+#endif
+}
+template <> __host__ __device__ __forceinline__ cpx<df> operator-<df>(cpx<df> a, cpx<df> b) {
+#ifdef DDA_F32X2
+  const df2 bp = dpack(b);
+  const unsigned long long z = 0ull;
+  return dunpack(dadd2(dpack(a), df2{f2sub(z, bp.h), f2sub(z, bp.l)}));
+#else
+  return mk<df>(a.x - b.x, a.y - b.y);
+#endif
+}
+template <> __host__ __device__ __forceinline__ cpx<df> operator*<df>(cpx<df> a, cpx<df> b) {
+#ifdef DDA_F32X2
+  return dcmul(a, b);
+#else
+  return mk<df>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+#endif
+}
+template <> __host__ __device__ __forceinline__ cpx<df> scale<df>(cpx<df> a, df s) {
+#ifdef DDA_F32X2
+  return dunpack(dmul2(dpack(a), dsplat(s)));
+#else
+  return mk<df>(a.x * s, a.y * s);
+#endif
+}
+template <> __host__ __device__ __forceinline__ cpx<df> fmas<df>(cpx<df> a, df s, cpx<df> c) {
+#ifdef DDA_F32X2
+  return dunpack(dadd2(dmul2(dpack(a), dsplat(s)), dpack(c)));
+#else
+  return mk<df>(a.x * s + c.x, a.y * s + c.y);
+#endif
+}
 
 __host__ __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 __host__ __device__ __forceinline__ c128 to128(cdf a) {

@@ -21,94 +21,118 @@ namespace dda {
 
 __device__ __forceinline__ c128 store_as(c128 v, c128*) { return v; }
 __device__ __forceinline__ cdf store_as(c128 v, cdf*) { return to_cdf(v); }
+__device__ __forceinline__ c128 neg_of(c128 v) { return mk<double>(-v.x, -v.y); }
+__device__ __forceinline__ cdf neg_of(cdf v) { return mk<df>(-v.x, -v.y); }
 
 // G for every non-negative offset (dx, dy, dz) < (nx, ny, nz), all six
 // components from one evaluation of exp(i kappa rho): table[6][nz][ny][nx].
-__global__ void k_green_table(c128* __restrict__ table, double kd, int nx, int ny, int nz) {
+template <typename T>
+__global__ void k_green_table(T* __restrict__ table, double kd, int nx, int ny, int nz) {
   const long long total = (long long)nx * ny * nz;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % nx);
-    const long long q = i / nx;
-    const int iy = (int)(q % ny);
-    const int iz = (int)(q / ny);
-    const double d[3] = {(double)ix, (double)iy, (double)iz};
-    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    c128 g[6];
-    for (int c = 0; c < 6; ++c) g[c] = mk<double>(0.0, 0.0);
-    if (r2 > 0.0) {
-      const double rho = sqrt(r2);
-      const double kr = kd * rho;
-      double s, c;
-      sincos(kr, &s, &c);
-      const double inv3 = 1.0 / (r2 * rho);
-      const c128 pref = mk<double>(c * inv3, s * inv3);
-      const c128 a = mk<double>(kr * kr - 1.0, kr);
-      const c128 b = mk<double>((kr * kr - 3.0) / r2, 3.0 * kr / r2);
-      const int mu_of[6] = {0, 0, 0, 1, 1, 2}, nu_of[6] = {0, 1, 2, 1, 2, 2};
-      for (int k = 0; k < 6; ++k) {
-        const double dd = d[mu_of[k]] * d[nu_of[k]];
-        c128 t = mk<double>(-b.x * dd, -b.y * dd);
-        if (mu_of[k] == nu_of[k]) t = t + a;
-        g[k] = pref * t;
+  const int rows = ny * nz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {     // a block per (y, z) row
+    const int iy = row % ny, iz = row / ny;
+    for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+      const long long i = (long long)row * nx + ix;
+      const double d[3] = {(double)ix, (double)iy, (double)iz};
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      c128 g[6];
+      for (int c = 0; c < 6; ++c) g[c] = mk<double>(0.0, 0.0);
+      if (r2 > 0.0) {
+        const double rho = sqrt(r2);
+        const double kr = kd * rho;
+        double sn, cn;
+        sincos(kr, &sn, &cn);
+        const double inv3 = 1.0 / (r2 * rho);
+        const c128 pref = mk<double>(cn * inv3, sn * inv3);
+        const c128 a = mk<double>(kr * kr - 1.0, kr);
+        const c128 b = mk<double>((kr * kr - 3.0) / r2, 3.0 * kr / r2);
+        const int mu_of[6] = {0, 0, 0, 1, 1, 2}, nu_of[6] = {0, 1, 2, 1, 2, 2};
+        for (int k = 0; k < 6; ++k) {
+          const double dd = d[mu_of[k]] * d[nu_of[k]];
+          c128 t = mk<double>(-b.x * dd, -b.y * dd);
+          if (mu_of[k] == nu_of[k]) t = t + a;
+          g[k] = pref * t;
+        }
       }
+      for (int k = 0; k < 6; ++k) table[(long long)k * total + i] = store_as(g[k], (T*)nullptr);
     }
-    for (int k = 0; k < 6; ++k) table[(long long)k * total + i] = g[k];
   }
 }
 
 // Component (mu, nu) of G on the padded grid from the table: grid index j
 // stands for offset j (j < n) or j - M (j > M - n), zero otherwise; a
 // negative offset along an axis flips the sign iff exactly one of mu, nu is
-// that axis (G_mu,nu is odd along it).
+// that axis (G_mu,nu is odd along it).  A block per (y, z) row of the grid.
 template <typename T>
-__global__ void k_green_fill(T* __restrict__ grid, const c128* __restrict__ table, int mu,
+__global__ void k_green_fill(T* __restrict__ grid, const T* __restrict__ table, int mu,
                              int nu, int nx, int ny, int nz, int Mx, int My, int Mz) {
-  const long long total = (long long)Mx * My * Mz;
   const long long tsz = (long long)nx * ny * nz;
   const int comp = mu == 0 ? nu : (mu == 1 ? 2 + nu : 5);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % Mx);
-    const long long q = i / Mx;
-    const int iy = (int)(q % My);
-    const int iz = (int)(q / My);
-    c128 out = mk<double>(0.0, 0.0);
-    const bool ux = ix < nx || ix > Mx - nx;
-    const bool uy = iy < ny || iy > My - ny;
-    const bool uz = iz < nz || iz > Mz - nz;
-    if (ux && uy && uz) {
-      const int ax = ix < nx ? ix : Mx - ix;
-      const int ay = iy < ny ? iy : My - iy;
-      const int az = iz < nz ? iz : Mz - iz;
-      const bool neg[3] = {ix >= nx, iy >= ny, iz >= nz};
-      bool flip = false;
-      for (int a = 0; a < 3; ++a)
-        if (neg[a] && ((mu == a) != (nu == a))) flip = !flip;
-      out = table[comp * tsz + ((long long)az * ny + ay) * nx + ax];
-      if (flip) out = mk<double>(-out.x, -out.y);
+  const bool oddx = (mu == 0) != (nu == 0), oddy = (mu == 1) != (nu == 1),
+             oddz = (mu == 2) != (nu == 2);
+  const int rows = My * Mz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int iy = row % My, iz = row / My;
+    const bool uyz = (iy < ny || iy > My - ny) && (iz < nz || iz > Mz - nz);
+    const int ay = iy < ny ? iy : My - iy;
+    const int az = iz < nz ? iz : Mz - iz;
+    const bool flip_yz = ((iy >= ny) && oddy) != ((iz >= nz) && oddz);
+    const T* trow = table + comp * tsz + ((long long)az * ny + ay) * nx;
+    T* out = grid + (long long)row * Mx;
+    T zero;
+    zero.x = decltype(zero.x)(0.0);
+    zero.y = decltype(zero.y)(0.0);
+    for (int ix = threadIdx.x; ix < Mx; ix += blockDim.x) {
+      T v = zero;
+      if (uyz && (ix < nx || ix > Mx - nx)) {
+        v = trow[ix < nx ? ix : Mx - ix];
+        if (flip_yz != ((ix >= nx) && oddx)) v = neg_of(v);
+      }
+      out[ix] = v;
     }
-    grid[i] = store_as(out, (T*)nullptr);
   }
 }
 
-// octant of the transformed grid, scaled by inv; also as double-float when Ddf
-template <typename T>
-__global__ void k_octant(const T* __restrict__ grid, c128* __restrict__ D, cdf* __restrict__ Ddf,
-                         int Mx, int My, int Mz, double inv) {
+// octant of the transformed FP64 grid, scaled by inv
+__global__ void k_octant(const c128* __restrict__ grid, c128* __restrict__ D, int Mx, int My, int Mz,
+                         double inv) {
   const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = Mz / 2 + 1;
-  const long long total = (long long)hx * hy * hz;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int fx = (int)(i % hx);
-    const long long q = i / hx;
-    const int fy = (int)(q % hy);
-    const int fz = (int)(q / hy);
-    const c128 v = to128(grid[((long long)fz * My + fy) * Mx + fx]);
-    const c128 sv = mk<double>(v.x * inv, v.y * inv);
-    D[i] = sv;
-    if (Ddf) Ddf[i] = to_cdf(sv);
+  const int rows = hy * hz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int fy = row % hy, fz = row / hy;
+    const c128* src = grid + ((long long)fz * My + fy) * Mx;
+    for (int fx = threadIdx.x; fx < hx; fx += blockDim.x) {
+      const c128 v = src[fx];
+      D[(long long)row * hx + fx] = mk<double>(v.x * inv, v.y * inv);
+    }
   }
+}
+
+// octant of the transformed double-float grid, scaled by inv (double-float
+// arithmetic), and its complex64 rounding (the high words)
+__global__ void k_octant_df(const cdf* __restrict__ grid, cdf* __restrict__ Ddf,
+                            c64* __restrict__ D32, int Mx, int My, int Mz, df inv) {
+  const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = Mz / 2 + 1;
+  const int rows = hy * hz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int fy = row % hy, fz = row / hy;
+    const cdf* src = grid + ((long long)fz * My + fy) * Mx;
+    for (int fx = threadIdx.x; fx < hx; fx += blockDim.x) {
+      const cdf v = src[fx];
+      const cdf sv = mk<df>(v.x * inv, v.y * inv);
+      const long long i = (long long)row * hx + fx;
+      Ddf[i] = sv;
+      D32[i] = mk<float>(sv.x.hi, sv.y.hi);
+    }
+  }
+}
+
+// complex128 from double-float (the FP64 octant derived on demand)
+__global__ void k_df_to128(const cdf* __restrict__ a, c128* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = to128(a[i]);
 }
 
 __global__ void k_to32(const c128* __restrict__ a, c64* __restrict__ b, long long n) {
@@ -116,6 +140,8 @@ __global__ void k_to32(const c128* __restrict__ a, c64* __restrict__ b, long lon
        i += (long long)gridDim.x * blockDim.x)
     b[i] = mk<float>((float)a[i].x, (float)a[i].y);
 }
+
+static int rows_grid(int rows) { return rows < 152 * 64 ? rows : 152 * 64; }
 
 static int grid_for(long long n) {
   long long b = (n + 255) / 256;
@@ -136,7 +162,7 @@ template <> Work<df>& dwork<df>(dda_t h) { return h->wdf; }
 // pass only on planes z <= Mz/2 and reads rows y <= My/2 (mirroring the rest),
 // and the z pass reads planes z <= Mz/2.
 template <typename R>
-cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const c128* table,
+cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const cpx<R>* table,
                                  const int comp[2], int c, double inv) {
   const Geom& g = h->g;
   cudaStream_t st = h->stream;
@@ -146,7 +172,7 @@ cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const c12
   const cpx<R>* twy = twx + g.Mx;
   const cpx<R>* twz = twy + g.My;
   tr_begin(g.tr, st);
-  k_green_fill<cpx<R>><<<grid_for(full), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
+  k_green_fill<cpx<R>><<<rows_grid(g.My * g.Mz), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
                                                        g.nz, g.Mx, g.My, g.Mz); count_launch();
   tr_end(g.tr, st, TR_DB_GREEN);
   tr_begin(g.tr, st);
@@ -168,9 +194,13 @@ cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const c12
   if ((e = fast_pass<R>(g.Mz, FP_SFULL, fa)) != cudaSuccess) return e;
   tr_end(g.tr, st, TR_DB_LINES);
   tr_begin(g.tr, st);
-  cdf* ddf = std::is_same<R, df>::value ? h->wdf.D + c * oct : nullptr;
-  k_octant<cpx<R>><<<grid_for(oct), 256, 0, st>>>(grid2, h->w64.D + c * oct, ddf, g.Mx, g.My, g.Mz,
-                                                  inv); count_launch();
+  const int orows = rows_grid((g.My / 2 + 1) * (g.Mz / 2 + 1));
+  if constexpr (std::is_same<R, df>::value) {
+    k_octant_df<<<orows, 256, 0, st>>>(grid2, h->wdf.D + c * oct, h->w32.D + c * oct, g.Mx, g.My,
+                                       g.Mz, df(inv)); count_launch();
+  } else {
+    k_octant<<<orows, 256, 0, st>>>(grid2, h->w64.D + c * oct, g.Mx, g.My, g.Mz, inv); count_launch();
+  }
   tr_end(g.tr, st, TR_DB_OCTANT);
   return cudaGetLastError();
 }
@@ -186,7 +216,7 @@ cudaError_t build_component_generic(dda_t h, c128* grid, const c128* table, cons
   const c128* twy = twx + g.Mx;
   const c128* twz = twy + g.My;
   tr_begin(g.tr, st);
-  k_green_fill<c128><<<grid_for(full), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
+  k_green_fill<c128><<<rows_grid(g.My * g.Mz), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
                                                      g.nz, g.Mx, g.My, g.Mz); count_launch();
   tr_end(g.tr, st, TR_DB_GREEN);
   tr_begin(g.tr, st);
@@ -207,8 +237,8 @@ cudaError_t build_component_generic(dda_t h, c128* grid, const c128* table, cons
   if (e != cudaSuccess) return e;
   tr_end(g.tr, st, TR_DB_LINES);
   tr_begin(g.tr, st);
-  k_octant<c128><<<grid_for(oct), 256, 0, st>>>(grid, h->w64.D + c * oct, nullptr, g.Mx, g.My,
-                                                g.Mz, inv); count_launch();
+  k_octant<<<rows_grid((g.My / 2 + 1) * (g.Mz / 2 + 1)), 256, 0, st>>>(grid, h->w64.D + c * oct,
+                                                                        g.Mx, g.My, g.Mz, inv); count_launch();
   tr_end(g.tr, st, TR_DB_OCTANT);
   return cudaGetLastError();
 }
@@ -222,31 +252,35 @@ int dda_build_D_internal(dda_t h, bool want32) {
   cudaStream_t st = h->stream;
   const long long full = (long long)g.Mx * g.My * g.Mz;
   const long long oct = g.oct();
-  if (!h->w64.D) {
-    if (cudaMalloc(&h->w64.D, 6 * oct * sizeof(c128)) != cudaSuccess) {
-      h->w64.D = nullptr;
-      cudaGetLastError();
-      return dda_fail(h, DDA_ERR_OOM, "cannot allocate the FP64 D-matrix octant");
-    }
-  }
   const long long tsz = (long long)g.nx * g.ny * g.nz;
   const bool fast = g.engine == 0 && fast_supported(g.Mx) && fast_supported(g.My) &&
                     fast_supported(g.Mz);
   // FP32_REFINED builds in double-float when every axis has register-resident
   // passes: the FP64-class D-matrix then costs FP32-pipe arithmetic (the FP64
-  // pipe is ~1/58 of it on this part), and the double-float octant also
-  // serves the refinement's residual products
+  // pipe is ~1/58 of it on this part); the double-float octant serves the
+  // refinement's residual products, its high words are the complex64 octant,
+  // and the complex128 octant is derived only if an FP64 product asks for it
   const bool use_df = want32 && fast && h->wdf.tw != nullptr;
-  if (use_df && !h->wdf.D) {
-    if (cudaMalloc(&h->wdf.D, 6 * oct * sizeof(cdf)) != cudaSuccess) {
-      h->wdf.D = nullptr;
+  auto alloc = [&](void** p, size_t bytes, const char* what) -> int {
+    if (*p) return DDA_OK;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      *p = nullptr;
       cudaGetLastError();
-      return dda_fail(h, DDA_ERR_OOM, "cannot allocate the double-float D-matrix octant");
+      return dda_fail(h, DDA_ERR_OOM, what);
     }
+    return DDA_OK;
+  };
+  int rc = DDA_OK;
+  if (use_df) {
+    rc = alloc((void**)&h->wdf.D, 6 * oct * sizeof(cdf), "cannot allocate the double-float D-matrix octant");
+    if (rc == DDA_OK) rc = alloc((void**)&h->w32.D, 6 * oct * sizeof(c64), "cannot allocate the FP32 D-matrix octant");
+  } else {
+    rc = alloc((void**)&h->w64.D, 6 * oct * sizeof(c128), "cannot allocate the FP64 D-matrix octant");
   }
+  if (rc != DDA_OK) return rc;
   void* grid = nullptr;
   void* grid2 = nullptr;
-  c128* table = nullptr;
+  void* table = nullptr;
   if (cudaMalloc(&grid, full * sizeof(c128)) != cudaSuccess ||
       cudaMalloc(&table, 6 * tsz * sizeof(c128)) != cudaSuccess ||
       (fast && cudaMalloc(&grid2, full * sizeof(c128)) != cudaSuccess)) {
@@ -256,15 +290,19 @@ int dda_build_D_internal(dda_t h, bool want32) {
     return dda_fail(h, DDA_ERR_OOM, "cannot allocate the Green's tensor grid");
   }
   tr_begin(g.tr, st);
-  k_green_table<<<grid_for(tsz), 256, 0, st>>>(table, h->kd, g.nx, g.ny, g.nz); count_launch();
+  if (use_df) {
+    k_green_table<cdf><<<rows_grid(g.ny * g.nz), 128, 0, st>>>((cdf*)table, h->kd, g.nx, g.ny, g.nz); count_launch();
+  } else {
+    k_green_table<c128><<<rows_grid(g.ny * g.nz), 128, 0, st>>>((c128*)table, h->kd, g.nx, g.ny, g.nz); count_launch();
+  }
   tr_end(g.tr, st, TR_DB_GREEN);
   const int comps[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
   const double inv = 1.0 / (double)full;
   cudaError_t e = cudaSuccess;
   for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
-    if (use_df) e = build_component_fast<df>(h, (cdf*)grid, (cdf*)grid2, table, comps[c], c, inv);
-    else if (fast) e = build_component_fast<double>(h, (c128*)grid, (c128*)grid2, table, comps[c], c, inv);
-    else e = build_component_generic(h, (c128*)grid, table, comps[c], c, inv);
+    if (use_df) e = build_component_fast<df>(h, (cdf*)grid, (cdf*)grid2, (const cdf*)table, comps[c], c, inv);
+    else if (fast) e = build_component_fast<double>(h, (c128*)grid, (c128*)grid2, (const c128*)table, comps[c], c, inv);
+    else e = build_component_generic(h, (c128*)grid, (const c128*)table, comps[c], c, inv);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   tr_flush(g.tr);
@@ -273,19 +311,33 @@ int dda_build_D_internal(dda_t h, bool want32) {
   cudaFree(table);
   if (e != cudaSuccess) return dda_cuda_fail(h, e, "D-matrix build");
   h->w64.have_D = true;
+  h->d64_from_df = use_df;
   h->wdf.have_D = use_df;
   if (want32) {
-    if (!h->w32.D) {
-      if (cudaMalloc(&h->w32.D, 6 * oct * sizeof(c64)) != cudaSuccess) {
-        h->w32.D = nullptr;
-        cudaGetLastError();
-        return dda_fail(h, DDA_ERR_OOM, "cannot allocate the FP32 D-matrix octant");
-      }
+    if (!use_df) {
+      rc = alloc((void**)&h->w32.D, 6 * oct * sizeof(c64), "cannot allocate the FP32 D-matrix octant");
+      if (rc != DDA_OK) return rc;
+      k_to32<<<grid_for(6 * oct), 256, 0, st>>>(h->w64.D, h->w32.D, 6 * oct); count_launch();
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return dda_cuda_fail(h, e, "D-matrix FP32 copy");
     }
-    k_to32<<<grid_for(6 * oct), 256, 0, st>>>(h->w64.D, h->w32.D, 6 * oct); count_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return dda_cuda_fail(h, e, "D-matrix FP32 copy");
     h->w32.have_D = true;
   }
+  return DDA_OK;
+}
+
+// The complex128 octant of a double-float build, made when first needed.
+int ensure_d64(dda_t h) {
+  if (!h->d64_from_df) return DDA_OK;
+  const long long n = 6 * h->g.oct();
+  if (!h->w64.D && cudaMalloc(&h->w64.D, n * sizeof(c128)) != cudaSuccess) {
+    h->w64.D = nullptr;
+    cudaGetLastError();
+    return dda_fail(h, DDA_ERR_OOM, "cannot allocate the FP64 D-matrix octant");
+  }
+  k_df_to128<<<grid_for(n), 256, 0, h->stream>>>(h->wdf.D, h->w64.D, n); count_launch();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return dda_cuda_fail(h, e, "FP64 D-matrix from double-float");
+  h->d64_from_df = false;
   return DDA_OK;
 }

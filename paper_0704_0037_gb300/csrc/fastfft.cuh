@@ -19,6 +19,8 @@
 // stored row by row.
 #pragma once
 
+#include <type_traits>
+
 #include "codelets.cuh"
 #include "internal.h"
 
@@ -157,6 +159,22 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yinv(const cpx<R>* __restri
   }
 }
 
+// ---------------------------------------------------------------- async copies
+// 16-byte global -> shared copies that complete in the background (the
+// pre-TMA asynchronous copy of sm_80 and later); a zero source size fills the
+// destination with zeros without reading.  Waits are on commit groups, with
+// no spin loop of ours.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // ---------------------------------------------------------------- P3: z fused
 // In place on B2 [3][nz][My][Mx]: per (kx, ky) line, forward z transform of the
 // nz nonzero inputs, 3x3 product with the octant of FFT(G) (parity signs),
@@ -185,22 +203,51 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict
   const long long plane = (long long)My * Mx;
   const long long comp = (long long)nz * plane;
   const long long col = (long long)ky * Mx + kx;
-  load_tw(s_tw, tw, M, NT);
-  __syncthreads();
-  if (q < M2) {
-    const int j = q;
-#pragma unroll 1
+  {
+    // Stage the nz x T input tile of every component in the first nz rows of
+    // that component's own region of s: asynchronous 16-byte copies, all
+    // three components in flight at once (the region is free until the
+    // component's phase 1 overwrites it).  Chunks past the last column are
+    // zero-filled without reading (padded lengths with register-resident
+    // passes are even, so a chunk never straddles the end of a row).
+    constexpr int E = 16 / (int)sizeof(cpx<R>);   // elements per chunk
+    constexpr int CPR = T / E;                     // chunks per tile row
+    const int kx0 = blockIdx.x * T;
     for (int c = 0; c < 3; ++c) {
-      cpx<R> v[M1];
+      cpx<R>* tile = s + c * M * T;
+      const cpx<R>* src = B2 + c * comp + (long long)ky * Mx + kx0;
+      for (int k = threadIdx.x; k < nz * CPR; k += NT) {
+        const int z = k / CPR, u = k - z * CPR;
+        const bool ok = kx0 + u * E < Mx;
+        cp_async16(tile + z * T + u * E, ok ? (const void*)(src + z * plane + u * E) : (const void*)B2,
+                   ok);
+      }
+      cp_async_commit();
+    }
+  }
+  (void)col;
+  load_tw(s_tw, tw, M, NT);
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    if (c == 0) cp_async_wait<2>();
+    else if (c == 1) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();           // this component's tile (and the twiddles) complete
+    cpx<R>* sc = s + c * M * T;
+    const int j = q;
+    cpx<R> v[M1];
+    if (q < M2) {
 #pragma unroll
       for (int i = 0; i < M1; ++i) {
         const int z = j + M2 * i;
-        v[i] = (z < nz && kx < Mx) ? B2[c * comp + z * plane + col] : zero<R>();
+        v[i] = z < nz ? sc[z * T + t] : zero<R>();
       }
+    }
+    __syncthreads();           // every read of the tile before the region is rewritten
+    if (q < M2) {
       cl::Dft<R, false, M1>::run(v);
 #pragma unroll
       for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
-      cpx<R>* sc = s + c * M * T;
 #pragma unroll
       for (int k1 = 0; k1 < M1; ++k1) sc[(k1 * M2 + j) * T + t] = v[k1];
     }
@@ -431,12 +478,14 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
   typename VecOf<R>::type* yc = y + (long long)cc * n_occ;
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double dre = 0.0, dim = 0.0;       // partial x^T y (bilinear) when dotp is set
+  // partial x^T y (bilinear) when dotp is set: per thread and per warp in
+  // the arithmetic's precision (FP32 for complex64: no FP64 work per
+  // element), across warps in FP64
+  R tr = (R)0, ti = (R)0;
   for (int tt = wid; tt < T && wid < NW; tt += NW) {   // one warp per row; a partial warp idles
     const int row = r0 + tt;
     if (row >= nrows) break;
     const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
-    R fr = (R)0, fi = (R)0;
     for (long long i = s0 + lane; i < s1; i += 32) {
       const cpx<R> xv = vin<R>(xc[i]);
       cpx<R> v = xv;
@@ -445,22 +494,34 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
       if (CONJ) o = conjg(o);
       yc[i] = vstore(o);
       if (dotp) {
-        fr = fr + (xv.x * o.x - xv.y * o.y);
-        fi = fi + (xv.x * o.y + xv.y * o.x);
+        tr = tr + (xv.x * o.x - xv.y * o.y);
+        ti = ti + (xv.x * o.y + xv.y * o.x);
       }
     }
-    dre += to_d(fr);
-    dim += to_d(fi);
   }
   if (dotp) {
     // block partial of the product's input times its output, for the solver
     // (only full warps did work; a trailing partial warp holds zeros and skips)
     __shared__ double sd[2][NT / 32 + 1];
     if (wid < NW) {
+      double dre, dim;
+      if constexpr (std::is_same<R, float>::value) {
+        float fr = tr, fi = ti;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dre += __shfl_down_sync(0xffffffffu, dre, o);
-        dim += __shfl_down_sync(0xffffffffu, dim, o);
+        for (int o = 16; o > 0; o >>= 1) {
+          fr += __shfl_down_sync(0xffffffffu, fr, o);
+          fi += __shfl_down_sync(0xffffffffu, fi, o);
+        }
+        dre = fr;
+        dim = fi;
+      } else {
+        dre = to_d(tr);
+        dim = to_d(ti);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dre += __shfl_down_sync(0xffffffffu, dre, o);
+          dim += __shfl_down_sync(0xffffffffu, dim, o);
+        }
       }
       if (lane == 0) { sd[0][wid] = dre; sd[1][wid] = dim; }
     }

@@ -97,15 +97,15 @@ __host__ __device__ __forceinline__ void bfly7(cpx<R>* v) {
 }
 
 // z * w8^k, w8 = exp(-i pi/4) (forward) or its conjugate (inverse)
+// (w8^1 = (1 -+ i)/sqrt2, w8^3 = (-1 -+ i)/sqrt2: z w8^1 = (z + mul_mi(z))/sqrt2,
+// z w8^3 = (mul_mi(z) - z)/sqrt2)
 template <typename R, bool INV, int K>
 __host__ __device__ __forceinline__ cpx<R> rot8(cpx<R> z) {
   const R r2 = (R)DDA_R2;
-  if (K == 1) return INV ? mk<R>((z.x - z.y) * r2, (z.x + z.y) * r2)
-                         : mk<R>((z.x + z.y) * r2, (z.y - z.x) * r2);
+  if (K == 1) return scale<R>(z + mul_mi<R, INV>(z), r2);
   if (K == 2) return mul_mi<R, INV>(z);
   // K == 3
-  return INV ? mk<R>((-z.x - z.y) * r2, (z.x - z.y) * r2)
-             : mk<R>((z.y - z.x) * r2, (-z.x - z.y) * r2);
+  return scale<R>(mul_mi<R, INV>(z) - z, r2);
 }
 
 template <typename R, bool INV>

@@ -18,7 +18,8 @@ namespace dda {
 enum TraceId {
   TR_P1_C64, TR_P2_C64, TR_P3_C64, TR_P4_C64, TR_P5_C64,
   TR_P1_C128, TR_P2_C128, TR_P3_C128, TR_P4_C128, TR_P5_C128,
-  TR_DB_GREEN, TR_DB_LINES, TR_DB_OCTANT, TR_FARFIELD, TR_QSUMS, TR_PRODUCT_DF, TR_COUNT
+  TR_DB_GREEN, TR_DB_LINES, TR_DB_OCTANT, TR_FARFIELD, TR_QSUMS, TR_P1_DF, TR_P2_DF,
+  TR_P3_DF, TR_P4_DF, TR_P5_DF, TR_QMR_K1, TR_QMR_K2, TR_QMR_SCALARS, TR_COUNT
 };
 struct Tracer {
   bool on = false;
@@ -114,6 +115,7 @@ int smooth_size(int lo);
 struct dda_ctx {
   int sym_flags = 0;        // DDA_SYM_* found at init
   int device = 0;           // CUDA device current at dda_init_lattice
+  bool d64_from_df = false; // w64.D not yet derived from the double-float octant
   dda::Geom g{};
   int n_mat = 0;
   std::vector<double> m;          // 2*n_mat
@@ -164,6 +166,8 @@ int dda_beta_internal(dda_t h, int presc, int nrhs, const double* prop, const do
 // D-matrix (dmatrix.cu)
 int dda_build_D_internal(dda_t h, bool want32);
 // solvers (krylov.cu)
+// the FP64 octant of a double-float build, derived on first use (dmatrix.cu)
+int ensure_d64(dda_t h);
 // all right-hand sides at once (QMR-CS only); frees with batch_free (krylov.cu)
 int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                              const double* pol, void* P_dev, dda_solve_info* info);

@@ -54,16 +54,23 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // Reduce K per-thread values over the block and store them as this block's
-// partials part[k * kNB + blockIdx.x] (k = slot0 .. slot0+K-1).
-template <int K>
+// partials part[k * kNB + blockIdx.x] (k = slot0 .. slot0+K-1).  A = float
+// (partials of complex64 vectors, FP32-accurate already) sums within each
+// warp in FP32 and across warps in FP64; A = double sums in FP64 throughout.
+template <int K, typename A = double>
 __device__ void block_store(double (&v)[K], double* part, int slot0) {
   __shared__ double sh[K][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double s = warp_sum(v[k]);
+    const double s = (double)warp_sum((A)v[k]);
     if (lane == 0) sh[k][wid] = s;
   }
   __syncthreads();
@@ -128,23 +135,26 @@ __device__ void fin_k(const double* p, long long ks, long long is, int nb, doubl
   __syncthreads();
 }
 
-// Running sum of FP64 products for complex128 vectors; for complex64 vectors
-// runs of 16 terms are summed in FP32 and each run is added in FP64 (the FP64
-// pipe is ~1/60 of the FP32 rate on this part).
+// Running sum of the products for complex128 vectors in FP64; for complex64
+// vectors a compensated (Kahan) sum in FP32, whose error is a few units of
+// 2^-24 of the sum of magnitudes whatever the number of terms, with no FP64
+// work per term (the FP64 pipe is ~1/58 of the FP32 rate on this part, and a
+// conditional FP64 flush every few terms gets if-converted into an FP64 add
+// per term).
 template <typename R> struct Acc {
   double d = 0.0;
   __device__ __forceinline__ void add(R v) { d += v; }
   __device__ __forceinline__ double get() const { return d; }
 };
 template <> struct Acc<float> {
-  double d = 0.0;
-  float f = 0.0f;
-  int k = 0;
+  float s = 0.0f, c = 0.0f;
   __device__ __forceinline__ void add(float v) {
-    f += v;
-    if (++k == 16) { d += (double)f; f = 0.0f; k = 0; }
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
   }
-  __device__ __forceinline__ double get() const { return d + (double)f; }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
 __device__ __forceinline__ c128 csqrt_p(c128 z) {
@@ -184,7 +194,7 @@ __global__ void __launch_bounds__(kVT) k_dot(const cpx<R>* __restrict__ a, const
     a1.add(ax * by + ay * bx);
   }
   double v[2] = {a0.get(), a1.get()};
-  block_store<2>(v, part, slot);
+  block_store<2, R>(v, part, slot);
 }
 
 // |a|^2 and, optionally, a^T a (bilinear)
@@ -341,7 +351,25 @@ __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, c
   if (s->done) return;
   const cpx<R> be = cs<R>(s->q.beta);
   Acc<R> q0, q1, q2;
-  VLOOP(n) {
+  // four elements per step with their loads issued together (two short
+  // streams: without that the sweep is latency-bound)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    cpx<R> a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { a[u] = pt[i + u * stride]; b[u] = v[i + u * stride]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const cpx<R> t = a[u] - be * b[u];
+      v[i + u * stride] = t;
+      const R x = t.x, y = t.y;
+      q0.add(x * x - y * y);
+      q1.add((R)2 * x * y);
+      q2.add(x * x + y * y);
+    }
+  }
+  for (; i < n; i += stride) {
     const cpx<R> t = pt[i] - be * v[i];
     v[i] = t;
     const R x = t.x, y = t.y;
@@ -350,7 +378,7 @@ __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, c
     q2.add(x * x + y * y);
   }
   double acc[3] = {q0.get(), q1.get(), q2.get()};
-  block_store<3>(acc, part, 0);
+  block_store<3, R>(acc, part, 0);
 }
 
 // rho_{i+1}, delta_{i+1}, the quasi-minimisation scalars of step i and the
@@ -421,7 +449,7 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* 
     p[i] = vn - cp * pi;
   }
   double a[1] = {acc.get()};
-  block_store<1>(a, part, 0);
+  block_store<1, R>(a, part, 0);
 }
 
 __global__ void k_qmr_c(Scal* s, const double* part, int nb, int* mask) {
@@ -936,6 +964,10 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
                        dda_solve_info* info) {
   int rc = dda_beta_internal(h, o->pol, nrhs, prop, pol);
   if (rc != DDA_OK) return rc;
+  if (o->prec == DDA_FP64 || !h->wdf.have_D) {
+    rc = ensure_d64(h);
+    if (rc != DDA_OK) return rc;
+  }
   const long long n = 3 * h->g.n_occ;
   const bool refined = o->prec == DDA_FP32_REFINED;
   const int nvec = 10;
@@ -1246,16 +1278,27 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
       cudaError_t e = launch_matvec<R>(h->g, h->lat(), w, beta, h->n_mat, p, pt, nr, false, st,
                                        m->mvpart, &dnb, m->mask);
       if (e != cudaSuccess) return dda_cuda_fail(h, e, "batched product");
+      Tracer* tr = h->g.tr;
+      tr_begin(tr, st);
       if (dnb > 0) {
         k_qmr_a<<<nr, kVT, 0, st>>>(s, m->mvpart, 1, 2, 2LL * dnb, dnb); count_launch();
       } else {
         k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
         k_qmr_a<<<nr, kVT, 0, st>>>(s, part, kNB, 1, kPS, nb); count_launch();
       }
+      tr_end(tr, st, TR_QMR_SCALARS);
+      tr_begin(tr, st);
       k_qmr_k1<R><<<vg, kVT, 0, st>>>(pt, v, n, s, part); count_launch();
+      tr_end(tr, st, TR_QMR_K1);
+      tr_begin(tr, st);
       k_qmr_b<<<nr, kVT, 0, st>>>(s, part, nb); count_launch();
+      tr_end(tr, st, TR_QMR_SCALARS);
+      tr_begin(tr, st);
       k_qmr_k2<R><<<vg, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part); count_launch();
+      tr_end(tr, st, TR_QMR_K2);
+      tr_begin(tr, st);
       k_qmr_c<<<nr, kVT, 0, st>>>(s, part, nb, m->mask); count_launch();
+      tr_end(tr, st, TR_QMR_SCALARS);
       LK(h);
     }
     RK(bsync(b));
@@ -1301,6 +1344,10 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
   auto t0 = std::chrono::steady_clock::now();
   int rc = dda_beta_internal(h, o->pol, nrhs, prop, pol);
   if (rc != DDA_OK) return rc;
+  if (o->prec == DDA_FP64 || !h->wdf.have_D) {
+    rc = ensure_d64(h);
+    if (rc != DDA_OK) return rc;
+  }
   const long long n = 3 * h->g.n_occ;
   const bool refined = o->prec == DDA_FP32_REFINED;
   const int nvec = 6;

@@ -445,15 +445,23 @@ cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, 
     tr_begin(g.tr, st);
     fa.in = x + r0 * nv; fa.out = w.B1; fa.tw = twx;
     if ((e = fast_pass<df>(g.Mx, FP_XFWD, fa)) != cudaSuccess) return e;
+    tr_end(g.tr, st, TR_P1_DF);
+    tr_begin(g.tr, st);
     fa.in = w.B1; fa.out = w.B2; fa.tw = twy;
     if ((e = fast_pass<df>(g.My, FP_YFWD, fa)) != cudaSuccess) return e;
+    tr_end(g.tr, st, TR_P2_DF);
+    tr_begin(g.tr, st);
     fa.out = w.B2; fa.tw = twz;
     if ((e = fast_pass<df>(g.Mz, FP_ZCONV, fa)) != cudaSuccess) return e;
+    tr_end(g.tr, st, TR_P3_DF);
+    tr_begin(g.tr, st);
     fa.in = w.B2; fa.out = w.B1; fa.tw = twy;
     if ((e = fast_pass<df>(g.My, FP_YINV, fa)) != cudaSuccess) return e;
+    tr_end(g.tr, st, TR_P4_DF);
+    tr_begin(g.tr, st);
     fa.in = w.B1; fa.x = x + r0 * nv; fa.out = y + r0 * nv; fa.tw = twx;
     if ((e = fast_pass<df>(g.Mx, FP_XINV, fa)) != cudaSuccess) return e;
-    tr_end(g.tr, st, TR_PRODUCT_DF);
+    tr_end(g.tr, st, TR_P5_DF);
   }
   return cudaGetLastError();
 }

@@ -11,7 +11,9 @@ namespace dda {
 static const char* kNames[TR_COUNT] = {
     "p1_xfft_c64", "p2_yfft_c64", "p3_zconv_c64", "p4_yifft_c64", "p5_xifft_c64",
     "p1_xfft_c128", "p2_yfft_c128", "p3_zconv_c128", "p4_yifft_c128", "p5_xifft_c128",
-    "dbuild_green", "dbuild_lines", "dbuild_octant", "farfield", "qsums", "product_df"};
+    "dbuild_green", "dbuild_lines", "dbuild_octant", "farfield", "qsums", "p1_xfft_df", "p2_yfft_df", "p3_zconv_df", "p4_yifft_df",
+    "p5_xifft_df",
+    "qmr_k1", "qmr_k2", "qmr_scalars"};
 
 const char* trace_name(int id) { return (id >= 0 && id < TR_COUNT) ? kNames[id] : "?"; }
 

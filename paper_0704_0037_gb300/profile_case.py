@@ -17,7 +17,9 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=134)
     ap.add_argument("--x", type=float, default=40.0)
     ap.add_argument("--m", type=float, default=1.05)
-    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--prec", choices=["fp32", "fp64", "df"], default="fp32",
+                    help="fp32: complex64 product; fp64: complex128; df: the double-float "
+                         "product of the FP32-refined form (complex128 vectors)")
     ap.add_argument("--products", type=int, default=3)
     a = ap.parse_args(argv)
     import torch
@@ -27,9 +29,9 @@ def main(argv=None):
     torch.cuda.set_device(0)
     occ = inputs.sphere(a.n)
     with dda.Particle(occ, [a.m], a.x, volume_corrected=True) as p:
-        prec = dda.DDA_FP32_REFINED if a.prec == "fp32" else dda.DDA_FP64
+        prec = {"fp32": dda.DDA_FP32_REFINED, "fp64": dda.DDA_FP64, "df": dda.DDA_FP64_PAIR}[a.prec]
         dt = torch.complex64 if a.prec == "fp32" else torch.complex128
-        dda.dda_build_Dmatrix(p.h, prec)
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP64 if a.prec == "fp64" else dda.DDA_FP32_REFINED)
         dda.dda_set_beta(p.h, dda.DDA_LDR, [(0, 0, 1)], [(1, 0, 0)])
         x = torch.from_numpy(inputs.random_vectors(1, 1, p.n_occ)).to("cuda", dt)
         y = torch.empty_like(x)
