@@ -171,6 +171,12 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, or
+# dram__bytes.sum.per_second x duration) from one ncu capture of the kernel
+# as it is now; profiles/fk_zconv_c64_sphere134.md gives the command.  Only
+# valid for the 134^3 sphere on the 270^3 grid; None elsewhere.
+NCU_TRAFFIC_134 = {"p3_zconv_c64": 647.8e6}
+
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe's nominal 1.25 TFLOP/s)
 
 
@@ -302,9 +308,10 @@ def run_ours(args, rank, world, local_rank):
         md = models.get(dom)
         if md and md.get("bound") == "hbm":
             achieved = md["bytes"] / avg_s / 1e9
+            tr = NCU_TRAFFIC_134.get(dom) if n == N_SPHERE else None
             roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "peak_note": f"hbm_gbs {peak_note}"}
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
+                    "algorithmic_bytes": md["bytes"], "peak_note": f"hbm_gbs {peak_note}"}
         else:
             achieved = md["flops"] / avg_s / 1e12 if md else None
             roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
