@@ -56,9 +56,15 @@ def parse():
                     help="run only the warm-up and timed steps (for profilers)")
     ap.add_argument("--inner-tol", type=float, default=INNER_TOL)
     ap.add_argument("--n", type=int, default=N_SPHERE, help=argparse.SUPPRESS)
-    ap.add_argument("--workload", default="sphere134", choices=["sphere134", "batch128"],
+    ap.add_argument("--workload", default="sphere134", choices=["sphere134", "batch128", "sphere"],
                     help="sphere134: the headline line; batch128: the seeded 128-particle "
-                         "batch (16 right-hand sides each), all right-hand sides to 1e-5")
+                         "batch (16 right-hand sides each), all right-hand sides to 1e-5; "
+                         "sphere: one sphere (--n, --x, --m) solved once in each form")
+    ap.add_argument("--x", type=float, default=X_SIZE, help="sphere workload: size parameter")
+    ap.add_argument("--m", type=float, default=M_INDEX, help="sphere workload: refractive index")
+    ap.add_argument("--maxiter", type=int, default=100000, help="sphere workload: iteration cap")
+    ap.add_argument("--forms", default="fp32_refined,fp64",
+                    help="sphere workload: the forms to run (comma separated)")
     ap.add_argument("--batch-count", type=int, default=128, help=argparse.SUPPRESS)
     ap.add_argument("--batch-threads", type=int, default=16,
                     help="host threads (particles in flight) of the batch workload")
@@ -537,6 +543,52 @@ def run_batch(args, rank, world, local_rank):
             "worst_rel_res_true": worst_res, "matvecs_fp64": mv64}
 
 
+def run_sphere(args):
+    """One sphere (n^3 box, size parameter x, real index m, LDR, x-polarised
+    incidence along z) solved once with QMR-CS to a true residual of 1e-5 in the
+    FP32-refined form and in the plain FP64 form, each timed with CUDA events
+    around the solve (D-matrix built before).  For the long solves of the
+    high-index spheres (Table 1: tens of thousands of iterations)."""
+    import torch
+    from paper_0704_0037_gb300 import build, dda, inputs
+    build.build()
+    occ = inputs.sphere(args.n)
+    prop = np.array([[0.0, 0.0, 1.0]])
+    pol = np.array([[1.0, 0.0, 0.0]])
+    p = dda.Particle(occ, [args.m], args.x, volume_corrected=True)
+    dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+    P = torch.zeros((1, 3, p.n_occ), dtype=torch.complex128, device="cuda")
+    out = {}
+    forms = [f for f in (("fp32_refined", dda.DDA_FP32_REFINED), ("fp64", dda.DDA_FP64))
+             if f[0] in args.forms.split(",")]
+    for name, prec in forms:
+        opts = dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_LDR, prec=prec, tol=TOL,
+                    maxiter=args.maxiter, inner_tol=INNER_TOL)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        st, info, _ = dda.dda_solve(p.h, opts, prop, pol, P)
+        e1.record()
+        e1.synchronize()
+        F, q = dda.dda_scatter(p.h, dda.DDA_LDR, P, prop, pol, np.array([[0.0, 0.0, 1.0]]))
+        i = info[0]
+        out[name] = {"time_to_residual_s": e0.elapsed_time(e1) / 1e3, "status": i["status_name"],
+                     "iters": i["iters"], "matvecs": i["matvecs"], "matvecs_fp64": i["matvecs_fp64"],
+                     "outer": i["outer"], "rel_res_true": i["rel_res_true"], "qext": float(q[0, 0])}
+    p.close()
+    r = (out["fp64"]["time_to_residual_s"] / out["fp32_refined"]["time_to_residual_s"]
+         if "fp64" in out and "fp32_refined" in out else None)
+    return {"metric": "time to true residual 1e-5, FP32-refined form vs plain FP64 form",
+            "value": out[forms[0][0]]["time_to_residual_s"], "unit": "s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+df", "data": "synthetic (sphere occupancy)",
+            "config": {"workload": f"sphere x={args.x:g} m={args.m:g} LDR, {args.n}^3 box, "
+                                   "QMR-CS to 1e-5", "n_box": args.n, "x": args.x, "m": args.m,
+                       "n_occ": int(p.n_occ), "grid": list(p.grid), "maxiter": args.maxiter},
+            "forms": out, "speedup_vs_fp64_form": r}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -551,6 +603,10 @@ def main():
     if world > 1:
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group(backend="nccl")
+    if args.workload == "sphere":
+        if rank == 0:
+            print(json.dumps(run_sphere(args)))
+        return
     if args.workload == "batch128":
         res = run_batch(args, rank, world, local_rank)
         if rank == 0 and res is not None:

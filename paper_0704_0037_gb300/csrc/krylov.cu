@@ -19,6 +19,8 @@
 #include <chrono>
 #include <cmath>
 
+#include <cstdlib>
+
 #include "internal.h"
 
 namespace dda {
@@ -1118,6 +1120,27 @@ namespace dda {
 namespace {
 
 constexpr int kSyncEvery = 8;
+// An inner solve with complex64 Krylov vectors gets at most this many steps
+// per refinement step.  If it needs more (hard problems: thousands of
+// iterations, where the complex64 Lanczos process loses its biorthogonality
+// and convergence slows far below the FP64 rate), the following inner solves
+// keep the Krylov vectors and scalars in complex128 with the double-float
+// products (FP64-class accuracy at the FP32 pipe's cost; FP64 products where
+// the grid has no double-float D-matrix): measured on the
+// 128^3 sphere with m = 2, complex128 vectors with complex64 products still
+// stall (1.5e-3 after 100,000 steps; the FP64 form needs 50,872), so the
+// product's accuracy, not only the vectors', sets the rate.
+constexpr int kC64InnerCap = 1000;
+// the cap, or DDA_C64_INNER_CAP from the environment (a tuning knob; tests use
+// a small value to exercise the switch on small problems)
+int c64_inner_cap() {
+  const char* v = std::getenv("DDA_C64_INNER_CAP");
+  if (v) {
+    const int c = std::atoi(v);
+    if (c > 0) return c;
+  }
+  return kC64InnerCap;
+}
 
 // b32[r] = (complex64)(a64[r] * scl[r]) for right-hand sides with off[r] == 0
 __global__ void k_to32s_b(const c128* __restrict__ a, c64* __restrict__ b, long long n,
@@ -1159,6 +1182,25 @@ __global__ void k_take_norms_b(Scal* s, const double* part, int nb, const int* o
   if (threadIdx.x == 0) s[rr].sres = sqrt(v);
 }
 
+// b[r] = a[r] * scl[r] (complex128)
+__global__ void k_scale_b(const c128* __restrict__ a, c128* __restrict__ b, long long n,
+                          const double* __restrict__ scl, const int* __restrict__ off) {
+  const int rr = blockIdx.y;
+  if (off[rr]) return;
+  a += rr * n; b += rr * n;
+  const double sc = scl[rr];
+  VLOOP(n) b[i] = mk<double>(a[i].x * sc, a[i].y * sc);
+}
+// x64[r] += scl[r] * d64[r]
+__global__ void k_axpy_b(c128* __restrict__ x, const c128* __restrict__ d, long long n,
+                         const double* __restrict__ scl, const int* __restrict__ off) {
+  const int rr = blockIdx.y;
+  if (off[rr]) return;
+  x += rr * n; d += rr * n;
+  const double sc = scl[rr];
+  VLOOP(n) x[i] = mk<double>(x[i].x + sc * d[i].x, x[i].y + sc * d[i].y);
+}
+
 // Device and pinned memory of one batched solve, grown on demand.
 struct BatchMem {
   int cap = 0;
@@ -1173,12 +1215,15 @@ struct BatchMem {
   double* h_vals = nullptr;  // pinned [2 cap]
   void* sv = nullptr;        // solver vectors
   size_t sv_bytes = 0;
+  void* sv2 = nullptr;       // vectors of the mixed inner solves (allocated on first use)
+  size_t sv2_bytes = 0;
 };
 
 void bm_release(BatchMem* m) {
   cudaFree(m->ds); cudaFreeHost(m->hs); cudaFree(m->part); cudaFree(m->mvpart); cudaFree(m->mask);
   cudaFree(m->off); cudaFree(m->dvals); cudaFreeHost(m->h_off); cudaFreeHost(m->h_vals);
   cudaFree(m->sv);
+  cudaFree(m->sv2);
   *m = BatchMem();
 }
 
@@ -1192,7 +1237,9 @@ int bm_ensure(dda_t h, int nrhs, size_t sv_bytes) {
   if (m->cap < nrhs) {
     BatchMem fresh;
     fresh.sv = m->sv; fresh.sv_bytes = m->sv_bytes;
+    fresh.sv2 = m->sv2; fresh.sv2_bytes = m->sv2_bytes;
     m->sv = nullptr; m->sv_bytes = 0;
+    m->sv2 = nullptr; m->sv2_bytes = 0;
     bm_release(m);
     *m = fresh;
     const size_t mvp = 2 * (size_t)fast_xinv_blocks(h->g.nrows, false) * nrhs;
@@ -1248,7 +1295,11 @@ int bsync(BRun& b) {
 // right-hand side is done or maxiter steps.
 template <typename R>
 int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double tol,
-                    const double* tols_dev, const int* off_dev, int maxiter, int* steps_out) {
+                    const double* tols_dev, const int* off_dev, int maxiter, int* steps_out,
+                    bool df_products = false) {
+  // df_products (R = double): the products in double-float from the
+  // double-float D-matrix (FP64-class accuracy), Krylov vectors and scalars in
+  // complex128
   dda_t h = b.h;
   cudaStream_t st = b.st;
   const long long n = b.n;
@@ -1275,8 +1326,14 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
   while (active && k < maxiter) {
     for (int j = 0; j < kSyncEvery && k < maxiter; ++j, ++k) {
       int dnb = 0;
-      cudaError_t e = launch_matvec<R>(h->g, h->lat(), w, beta, h->n_mat, p, pt, nr, false, st,
-                                       m->mvpart, &dnb, m->mask);
+      cudaError_t e;
+      if (df_products) {
+        e = launch_matvec_df(h->g, h->lat(), h->wdf, h->w64.beta, h->n_mat, (const c128*)p,
+                             (c128*)pt, nr, st, m->mask);
+      } else {
+        e = launch_matvec<R>(h->g, h->lat(), w, beta, h->n_mat, p, pt, nr, false, st, m->mvpart,
+                             &dnb, m->mask);
+      }
       if (e != cudaSuccess) return dda_cuda_fail(h, e, "batched product");
       Tracer* tr = h->g.tr;
       tr_begin(tr, st);
@@ -1453,6 +1510,9 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
     }
     int left = o->maxiter;
     b.stall = true;
+    bool mixed = false;
+    c128* mvec[nvec] = {};
+    c128 *xm = nullptr, *rhsm = nullptr;
     for (int it_out = 0; it_out < 64 && left > 0; ++it_out) {
       bool any = false;
       for (int r = 0; r < nrhs; ++r) {
@@ -1465,10 +1525,21 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
       if (!any) break;
       DDA_CK(h, cudaMemcpyAsync(m->off, m->h_off, nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
       DDA_CK(h, cudaMemcpyAsync(m->dvals, m->h_vals, 2 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-      k_to32s_b<<<vg, kVT, 0, st>>>(r64, rhs32, n, m->dvals + nrhs, m->off); count_launch();
-      LK(h);
       int steps = 0;
-      RK(run_qmr_batched<float>(b, rhs32, x32, vec, 0.0, m->dvals, m->off, left, &steps));
+      bool capped = false;
+      b.stall = !mixed;          // the stagnation stop is for the complex64 rounding floor
+      if (!mixed) {
+        k_to32s_b<<<vg, kVT, 0, st>>>(r64, rhs32, n, m->dvals + nrhs, m->off); count_launch();
+        LK(h);
+        const int cap = std::min(left, c64_inner_cap());
+        RK(run_qmr_batched<float>(b, rhs32, x32, vec, 0.0, m->dvals, m->off, cap, &steps));
+        capped = steps >= cap && cap < left;
+      } else {
+        k_scale_b<<<vg, kVT, 0, st>>>(r64, rhsm, n, m->dvals + nrhs, m->off); count_launch();
+        LK(h);
+        RK(run_qmr_batched<double>(b, rhsm, xm, mvec, 0.0, m->dvals, m->off, left, &steps,
+                                   h->wdf.have_D));
+      }
       left -= steps;
       for (int r = 0; r < nrhs; ++r) {
         if (fin_[r]) continue;
@@ -1478,8 +1549,16 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
       }
       DDA_CK(h, cudaMemcpyAsync(m->dvals + nrhs, m->h_vals + nrhs, nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
       std::vector<int> inner_status(nrhs);
-      for (int r = 0; r < nrhs; ++r) inner_status[r] = m->hs[r].status;
-      k_axpy64_b<<<vg, kVT, 0, st>>>(x64, x32, n, m->dvals + nrhs, m->off); count_launch();
+      bool unfinished = false;
+      for (int r = 0; r < nrhs; ++r) {
+        inner_status[r] = m->hs[r].status;
+        if (!fin_[r] && !m->hs[r].done) unfinished = true;
+      }
+      if (!mixed) {
+        k_axpy64_b<<<vg, kVT, 0, st>>>(x64, x32, n, m->dvals + nrhs, m->off); count_launch();
+      } else {
+        k_axpy_b<<<vg, kVT, 0, st>>>(x64, xm, n, m->dvals + nrhs, m->off); count_launch();
+      }
       cudaError_t e = h->wdf.have_D
           ? launch_matvec_df(h->g, h->lat(), h->wdf, h->w64.beta, h->n_mat, x64, w64, nrhs, st,
                              m->off)
@@ -1502,6 +1581,25 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
         }
         if (!(rn_new < 0.999 * rn[r])) { fin_[r] = 1; status[r] = DDA_NOT_CONVERGED; continue; }
         rn[r] = rn_new;
+      }
+      if (!mixed && capped && unfinished) {
+        // switch the remaining inner solves to complex128 Krylov vectors and
+        // FP64-class products
+        const size_t need = (size_t)nrhs * n * (nvec + 2) * sizeof(c128);
+        if (m->sv2_bytes < need) {
+          cudaFree(m->sv2);
+          m->sv2 = nullptr; m->sv2_bytes = 0;
+          if (cudaMalloc(&m->sv2, need) != cudaSuccess) {
+            cudaGetLastError();
+            return dda_fail(h, DDA_ERR_OOM, "mixed inner-solve vectors");
+          }
+          m->sv2_bytes = need;
+        }
+        c128* b2 = (c128*)m->sv2;
+        for (int i = 0; i < nvec; ++i) mvec[i] = b2 + (size_t)i * nrhs * n;
+        xm = b2 + (size_t)nvec * nrhs * n;
+        rhsm = xm + (size_t)nrhs * n;
+        mixed = true;
       }
     }
     for (int r = 0; r < nrhs; ++r) res_recur[r] = res_true[r];

@@ -244,3 +244,19 @@ def test_solve_is_deterministic(sphere16):
     _, i2, P2, h2 = _solve(p, "qmr_cs", "fp32_refined", 1e-6, hist_len=200)
     assert np.array_equal(h1, h2)
     assert bool((P1 == P2).all())
+
+
+def test_fp32_refined_switches_to_mixed_inner_solves(sphere16, monkeypatch):
+    """Inner solves with complex64 Krylov vectors are capped per refinement
+    step; past the cap the next inner solves keep complex128 vectors with
+    double-float products.  A cap of 5 steps forces the switch here; the
+    solve still reaches the FP64 tolerance and the exact solution."""
+    torch, dda = need_gpu()
+    p, prob, exact = sphere16
+    monkeypatch.setenv("DDA_C64_INNER_CAP", "5")
+    st, info, P, _ = _solve(p, "qmr_cs", "fp32_refined", 1e-9, maxiter=3000, inner_tol=1e-10)
+    assert st == 0, info
+    for r in range(2):
+        assert info[r]["rel_res_true"] < 1e-9
+        assert info[r]["outer"] >= 2
+    assert rel_l2(P.cpu().numpy(), exact) < 1e-7
