@@ -345,6 +345,23 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict
 // B1 [3][nrows][M]; grid (ceil(nrows/T), 3)
 template <int M> constexpr int kLD = (M % 2 == 1) ? M : M + 1;
 
+// Row t (0 <= t < T) of the block holding dipole i: the last t with
+// off[t] <= i, for the non-decreasing offsets off[0..T] of the block's rows
+// (off[0] <= i < off[T]; empty rows are skipped over).
+template <int T>
+__device__ __forceinline__ int row_of(const long long* off, long long i) {
+  static_assert((T & (T - 1)) == 0, "tile rows must be a power of two");
+  int t = 0;
+#pragma unroll
+  for (int b = T / 2; b >= 1; b >>= 1)
+    if (off[t + b] <= i) t += b;
+  return t;
+}
+
+// Loads per thread issued together in the gather and scatter loops over a
+// block's dipoles
+constexpr int kGU = 4;
+
 template <typename R, int M1, int M2, int T, bool CONJ>
 __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const typename VecOf<R>::type* __restrict__ x,
                                                           cpx<R>* __restrict__ B1, LatticeDev lat,
@@ -354,6 +371,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const typename VecO
                                                           int bstride, const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_off[T + 1];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* a = s_tw + M;                      // [T][LD]
   // blockIdx.y = 3 * (right-hand side) + component; vectors [rhs][3][n_occ]
@@ -361,22 +379,38 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const typename VecO
   if (skip && skip[cc / 3]) return;
   beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
+  if (threadIdx.x <= T) s_off[threadIdx.x] = lat.row_off[min(r0 + (int)threadIdx.x, nrows)];
   load_tw(s_tw, tw, M, NT);
   for (int i = threadIdx.x; i < T * LD; i += NT) a[i] = zero<R>();
   __syncthreads();
-  const typename VecOf<R>::type* xc = x + (long long)cc * n_occ;
   {
-    // one warp per row: the dipoles of a row are contiguous in x
-    constexpr int NW = NT / 32;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int t = wid; t < T && wid < NW; t += NW) {   // a trailing partial warp idles
-      const int row = r0 + t;
-      if (row >= nrows) break;
-      const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
-      for (long long i = s0 + lane; i < s1; i += 32) {
-        cpx<R> v = vin<R>(xc[i]);
-        if (CONJ) v = conjg(v);
-        a[t * LD + lat.xi[i]] = beta[lat.mat[i] * 3 + c] * v;
+    // all threads over the block's dipoles (contiguous in x: rows r0..r0+T-1),
+    // kGU independent loads of x, xi and mat in flight per thread
+    const typename VecOf<R>::type* __restrict__ xc = x + (long long)cc * n_occ;
+    const uint16_t* __restrict__ xi = lat.xi;
+    const uint8_t* __restrict__ mt = lat.mat;
+    const long long S0 = s_off[0];
+    const int span = (int)(s_off[T] - S0);
+    for (int k0 = threadIdx.x; k0 < span; k0 += kGU * NT) {
+      typename VecOf<R>::type xv[kGU];
+      int xk[kGU], mk_[kGU];
+#pragma unroll
+      for (int u = 0; u < kGU; ++u) {
+        const int k = k0 + u * NT;
+        if (k < span) {
+          xv[u] = xc[S0 + k];
+          xk[u] = xi[S0 + k];
+          mk_[u] = mt[S0 + k];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kGU; ++u) {
+        const int k = k0 + u * NT;
+        if (k < span) {
+          cpx<R> v = vin<R>(xv[u]);
+          if (CONJ) v = conjg(v);
+          a[row_of<T>(s_off, S0 + k) * LD + xk[u]] = beta[mk_[u] * 3 + c] * v;
+        }
       }
     }
   }
@@ -409,17 +443,39 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const typename VecO
     for (int k2 = 0; k2 < M2; ++k2) at[k1 + M1 * k2] = u[k2];
   }
   __syncthreads();
-  cpx<R>* out = B1 + (long long)cc * nrows * M;
-  for (int idx = threadIdx.x; idx < T * M; idx += NT) {
+  // the block's rows are contiguous in B1
+  cpx<R>* out = B1 + ((long long)cc * nrows + r0) * M;
+  const int nel = min(T, nrows - r0) * M;
+  for (int idx = threadIdx.x; idx < nel; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
-    const int row = r0 + tt;
-    if (row < nrows) out[(long long)row * M + m] = a[tt * LD + m];
+    out[idx] = a[tt * LD + m];
   }
+}
+
+// Asynchronous copy of one complex element (8 or 16 bytes) global -> shared;
+// !valid fills zeros without reading.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n)
+               : "memory");
+}
+template <int S>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem, bool valid) {
+  static_assert(S == 8 || S == 16, "8- or 16-byte elements");
+  if constexpr (S == 8) cp_async8(smem, gmem, valid);
+  else cp_async16(smem, gmem, valid);
 }
 
 // ---------------------------------------------------------------- P5: x inverse
 // rows of B1 -> [t][LD] tile, inverse transform, y = x - beta u at the
-// occupied x; grid (ceil(nrows/T), 3)
+// occupied x; grid (ceil(nrows/T), 3).  The tile rows (contiguous in B1) and
+// the block's slice of x are staged by asynchronous copies before the
+// transform, so their latency overlaps; the slice holds up to kXS elements
+// (a row has at most (M + 1) / 2 dipoles when M >= 2 n_x - 1; any excess is
+// read directly).
+template <int M> constexpr int kXRow = (M + 1) / 2;
+
 template <typename R, int M1, int M2, int T, bool CONJ>
 __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __restrict__ B1,
                                                           const typename VecOf<R>::type* __restrict__ x,
@@ -430,21 +486,34 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
                                                           const cpx<R>* __restrict__ tw,
                                                           double* __restrict__ dotp, int bstride,
                                                           const int* __restrict__ skip) {
-  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>, kXS = T * kXRow<M>;
+  using V = typename VecOf<R>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_off[T + 1];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* a = s_tw + M;                      // [T][LD]
+  V* s_x = reinterpret_cast<V*>(a + T * LD); // [kXS]
   const int cc = blockIdx.y, c = cc % 3;     // 3 * (right-hand side) + component
   if (skip && skip[cc / 3]) return;
   beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
-  load_tw(s_tw, tw, M, NT);
-  const cpx<R>* in = B1 + (long long)cc * nrows * M;
+  const int rows = min(T, nrows - r0);
+  const cpx<R>* in = B1 + ((long long)cc * nrows + r0) * M;
   for (int idx = threadIdx.x; idx < T * M; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
-    const int row = r0 + tt;
-    a[tt * LD + m] = row < nrows ? in[(long long)row * M + m] : zero<R>();
+    const bool ok = tt < rows;
+    cp_async_elem<sizeof(cpx<R>)>(a + tt * LD + m, ok ? (const void*)(in + idx) : (const void*)B1, ok);
   }
+  const V* xc = x + (long long)cc * n_occ;
+  V* yc = y + (long long)cc * n_occ;
+  const long long S0 = lat.row_off[r0];
+  const int span = (int)(lat.row_off[r0 + rows] - S0);
+  const int staged = min(span, kXS);
+  for (int k = threadIdx.x; k < staged; k += NT) cp_async_elem<sizeof(V)>(s_x + k, xc + S0 + k, true);
+  cp_async_commit();
+  if (threadIdx.x <= T) s_off[threadIdx.x] = lat.row_off[min(r0 + (int)threadIdx.x, nrows)];
+  load_tw(s_tw, tw, M, NT);
+  cp_async_wait<0>();
   __syncthreads();
   const int t = threadIdx.x % T, q = threadIdx.x / T;
   cpx<R>* at = a + t * LD;
@@ -474,57 +543,71 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
     for (int i = 0; i < M1; ++i) at[j + M2 * i] = v[i];
   }
   __syncthreads();
-  const typename VecOf<R>::type* xc = x + (long long)cc * n_occ;
-  typename VecOf<R>::type* yc = y + (long long)cc * n_occ;
-  constexpr int NW = NT / 32;
+  constexpr int NW = (NT + 31) / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // partial x^T y (bilinear) when dotp is set: per thread and per warp in
   // the arithmetic's precision (FP32 for complex64: no FP64 work per
   // element), across warps in FP64
   R tr = (R)0, ti = (R)0;
-  for (int tt = wid; tt < T && wid < NW; tt += NW) {   // one warp per row; a partial warp idles
-    const int row = r0 + tt;
-    if (row >= nrows) break;
-    const long long s0 = lat.row_off[row], s1 = lat.row_off[row + 1];
-    for (long long i = s0 + lane; i < s1; i += 32) {
-      const cpx<R> xv = vin<R>(xc[i]);
-      cpx<R> v = xv;
-      if (CONJ) v = conjg(v);
-      cpx<R> o = v - beta[lat.mat[i] * 3 + c] * a[tt * LD + lat.xi[i]];
-      if (CONJ) o = conjg(o);
-      yc[i] = vstore(o);
-      if (dotp) {
-        tr = tr + (xv.x * o.x - xv.y * o.y);
-        ti = ti + (xv.x * o.y + xv.y * o.x);
+  {
+    const uint16_t* __restrict__ xi = lat.xi;
+    const uint8_t* __restrict__ mt = lat.mat;
+    for (int k0 = threadIdx.x; k0 < span; k0 += kGU * NT) {
+      int xk[kGU], mk_[kGU];
+#pragma unroll
+      for (int u2 = 0; u2 < kGU; ++u2) {
+        const int k = k0 + u2 * NT;
+        if (k < span) {
+          xk[u2] = xi[S0 + k];
+          mk_[u2] = mt[S0 + k];
+        }
+      }
+#pragma unroll
+      for (int u2 = 0; u2 < kGU; ++u2) {
+        const int k = k0 + u2 * NT;
+        if (k < span) {
+          const cpx<R> xv = vin<R>(k < kXS ? s_x[k] : xc[S0 + k]);
+          cpx<R> v = xv;
+          if (CONJ) v = conjg(v);
+          cpx<R> o = v - beta[mk_[u2] * 3 + c] * a[row_of<T>(s_off, S0 + k) * LD + xk[u2]];
+          if (CONJ) o = conjg(o);
+          yc[S0 + k] = vstore(o);
+          if (dotp) {
+            tr = tr + (xv.x * o.x - xv.y * o.y);
+            ti = ti + (xv.x * o.y + xv.y * o.x);
+          }
+        }
       }
     }
   }
   if (dotp) {
-    // block partial of the product's input times its output, for the solver
-    // (only full warps did work; a trailing partial warp holds zeros and skips)
-    __shared__ double sd[2][NT / 32 + 1];
-    if (wid < NW) {
-      double dre, dim;
-      if constexpr (std::is_same<R, float>::value) {
-        float fr = tr, fi = ti;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          fr += __shfl_down_sync(0xffffffffu, fr, o);
-          fi += __shfl_down_sync(0xffffffffu, fi, o);
-        }
-        dre = fr;
-        dim = fi;
-      } else {
-        dre = to_d(tr);
-        dim = to_d(ti);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          dre += __shfl_down_sync(0xffffffffu, dre, o);
-          dim += __shfl_down_sync(0xffffffffu, dim, o);
-        }
+    // block partial of the product's input times its output, for the solver;
+    // a trailing partial warp (NT % 32 threads, a power of two) reduces over
+    // its own lanes only
+    __shared__ double sd[2][NW];
+    constexpr int kTail = NT % 32;
+    static_assert((kTail & (kTail - 1)) == 0, "partial warp of a power-of-two size");
+    const bool part = kTail != 0 && wid == NW - 1;
+    const unsigned mask = part ? (1u << kTail) - 1u : 0xffffffffu;
+    const int width = part ? kTail : 32;
+    double dre, dim;
+    if constexpr (std::is_same<R, float>::value) {
+      float fr = tr, fi = ti;
+      for (int o = width / 2; o > 0; o >>= 1) {
+        fr += __shfl_down_sync(mask, fr, o, width);
+        fi += __shfl_down_sync(mask, fi, o, width);
       }
-      if (lane == 0) { sd[0][wid] = dre; sd[1][wid] = dim; }
+      dre = fr;
+      dim = fi;
+    } else {
+      dre = to_d(tr);
+      dim = to_d(ti);
+      for (int o = width / 2; o > 0; o >>= 1) {
+        dre += __shfl_down_sync(mask, dre, o, width);
+        dim += __shfl_down_sync(mask, dim, o, width);
+      }
     }
+    if (lane == 0) { sd[0][wid] = dre; sd[1][wid] = dim; }
     __syncthreads();
     if (threadIdx.x == 0) {
       double sr = 0.0, si = 0.0;
@@ -689,9 +772,12 @@ struct Passes {
   static cudaError_t xinv(const cpx<R>* B1, const V* x, V* y, const LatticeDev& lat,
                           const cpx<R>* beta, long long n_occ, int nrows, const cpx<R>* tw, bool adj,
                           double* dotp, int nrhs, int bstride, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
+    const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>) + (size_t)T * kXRow<M> * sizeof(V);
     const dim3 grid((nrows + T - 1) / T, 3 * nrhs);
     cudaError_t e;
+    // three blocks of up to ~56 KB per SM need a large shared-memory carveout
+    if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, T, true>)) != cudaSuccess) return e;
+    if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, T, false>)) != cudaSuccess) return e;
     if (adj) {
       if ((e = set_smem(fk_xinv<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
       fk_xinv<R, M1, M2, T, true><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
