@@ -191,14 +191,26 @@ __device__ __forceinline__ cpx<df> dunpack(df2 p) {
   r.y = df(h.y, l.y);
   return r;
 }
-// componentwise double-float sum and product of the two parts
+// Componentwise double-float sum and difference of the two parts, without
+// the final renormalisation: the result (s, e) is the two-sum of the high
+// words with the low words' sum added to its error term.  It represents the
+// same value as the renormalised sum (which only redistributes s + e between
+// the words), but e may exceed ulp(s) / 2.  Every product renormalises its
+// result, so between two products the low word stays within a few ulp of the
+// operands' magnitude (a DFT codelet chains a few sums at most), and the
+// error stays a small multiple of 2^-46 of the operands' magnitude; long
+// accumulations do not use these.
 __device__ __forceinline__ df2 dadd2(df2 a, df2 b) {
   const unsigned long long s = f2add(a.h, b.h);
   const unsigned long long bb = f2sub(s, a.h);
-  unsigned long long e = f2add(f2sub(a.h, f2sub(s, bb)), f2sub(b.h, bb));
-  e = f2add(e, f2add(a.l, b.l));
-  const unsigned long long h = f2add(s, e);
-  return df2{h, f2sub(e, f2sub(h, s))};
+  const unsigned long long e = f2add(f2sub(a.h, f2sub(s, bb)), f2sub(b.h, bb));
+  return df2{s, f2add(e, f2add(a.l, b.l))};
+}
+__device__ __forceinline__ df2 dsub2(df2 a, df2 b) {
+  const unsigned long long s = f2sub(a.h, b.h);
+  const unsigned long long bb = f2sub(s, a.h);
+  const unsigned long long e = f2sub(f2sub(a.h, f2sub(s, bb)), f2add(b.h, bb));
+  return df2{s, f2add(e, f2sub(a.l, b.l))};
 }
 __device__ __forceinline__ df2 dmul2(df2 a, df2 b) {
   // The rounded product comes from an fma with a zero addend the compiler
@@ -239,9 +251,7 @@ template <> __host__ __device__ __forceinline__ cpx<df> operator+<df>(cpx<df> a,
 }
 template <> __host__ __device__ __forceinline__ cpx<df> operator-<df>(cpx<df> a, cpx<df> b) {
 #ifdef DDA_F32X2
-  const df2 bp = dpack(b);
-  const unsigned long long z = 0ull;
-  return dunpack(dadd2(dpack(a), df2{f2sub(z, bp.h), f2sub(z, bp.l)}));
+  return dunpack(dsub2(dpack(a), dpack(b)));
 #else
   return mk<df>(a.x - b.x, a.y - b.y);
 #endif
