@@ -43,6 +43,7 @@ struct QmrScal {
 struct Scal {
   double bnorm, res, sres, tol;
   int done, status, half, iters;   // iters: steps taken (batched QMR)
+  int cnt;                         // blocks of the current sweep that have finished
   c128 alpha, beta_k, beta_next, inv_beta, t, tau, delta, eps, inv_gamma, s1, s2;
   double c1, c2;
   c128 rho, rho_prev, omega, bstep;
@@ -120,7 +121,7 @@ __device__ void fin_k(const double* p, long long ks, long long is, int nb, doubl
   for (int k = 0; k < K; ++k) v[k] = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] += p[k * ks + i * is];
+    for (int k = 0; k < K; ++k) v[k] += __ldcg(p + k * ks + i * is);   // other blocks' writes
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -135,6 +136,24 @@ __device__ void fin_k(const double* p, long long ks, long long is, int nb, doubl
     out[k] = x;
   }
   __syncthreads();
+}
+
+// True in every thread of the block that finishes last among the gridDim.x
+// blocks working on one right-hand side (counter *cnt, reset here for the
+// next sweep); every block's partials are then visible to it.  A sweep ends
+// with its reduction in that block instead of a separate one-block launch.
+__device__ bool last_block(int* cnt) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    is_last = atomicAdd(cnt, 1) == (int)gridDim.x - 1;
+    if (is_last) *cnt = 0;
+  }
+  __syncthreads();
+  const bool r = is_last != 0;
+  if (r) __threadfence();
+  return r;
 }
 
 // Running sum of the products for complex128 vectors in FP64; for complex64
@@ -290,6 +309,7 @@ __global__ void k_qmr_init(Scal* s, const double* part, int nb, double tol, cons
   QmrScal& q = s->q;
   s->tol = tols ? tols[rr] : tol;
   s->iters = 0;
+  s->cnt = 0;
   s->bnorm = sqrt(bn2);
   s->res = 1.0;
   s->done = 0; s->half = 0;
@@ -327,11 +347,20 @@ __global__ void k_qmr_start(const cpx<R>* __restrict__ b, cpx<R>* __restrict__ v
   }
 }
 
+// End right-hand side rr's solve with `status` (one thread); its products
+// are skipped from then on when a mask is kept
+__device__ __forceinline__ void qmr_stop(Scal* s, int status, int* mask, int rr) {
+  s->status = status;
+  s->done = 1;
+  if (mask) mask[rr] = 1;
+}
+
 // eps_i = p^T A p from partials (entry (k, i) at part[k * ks + i * is],
 // right-hand side r's partials at part + r * rs); beta_i
 __global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is, long long rs,
-                        int nb) {
-  s += blockIdx.x; part += blockIdx.x * rs;
+                        int nb, int* mask) {
+  const int rr = blockIdx.x;
+  s += rr; part += rr * rs;
   if (s->done) return;
   double a[2];
   fin_k<2>(part, ks, is, nb, a);
@@ -339,16 +368,69 @@ __global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is,
   QmrScal& q = s->q;
   const c128 eps = mk<double>(a[0], a[1]);
   const c128 beta = cdivd(eps, q.delta);
-  if (!cfinite(eps) || !cfinite(beta)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
-  if (cabs2(eps) == 0.0 || cabs2(beta) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  if (!cfinite(eps) || !cfinite(beta)) { qmr_stop(s, DDA_ERR_NONFINITE, mask, rr); return; }
+  if (cabs2(eps) == 0.0 || cabs2(beta) == 0.0) { qmr_stop(s, DDA_BREAKDOWN, mask, rr); return; }
   q.eps_new = eps;
   q.beta = beta;
 }
 
-// vt = pt - beta v (into v); partials of vt^T vt and |vt|^2
+// rho_{i+1}, delta_{i+1}, the quasi-minimisation scalars of step i and the
+// coefficients of the update and of the next direction, from the nb partials
+// of the k1 sweep (all threads of one block)
+__device__ void qmr_b_fin(Scal* s, const double* part, int nb, int* mask, int rr) {
+  double f[3];
+  fin_k<3>(part, kNB, 1, nb, f);
+  if (threadIdx.x) return;
+  QmrScal& q = s->q;
+  const c128 vtv = mk<double>(f[0], f[1]);
+  const double rho_n = sqrt(f[2]);
+  const double theta = rho_n / (q.g * sqrt(cabs2(q.beta)));
+  const double g = 1.0 / sqrt(1.0 + theta * theta);
+  const c128 eta = scale<double>(cdivd(q.eta, q.beta), -q.rho * g * g / (q.g * q.g));
+  if (!isfinite(rho_n) || !cfinite(vtv) || !isfinite(theta) || !cfinite(eta)) {
+    qmr_stop(s, DDA_ERR_NONFINITE, mask, rr);
+    return;
+  }
+  q.cd = (q.theta * g) * (q.theta * g);
+  q.eta = eta;
+  q.g = g;
+  q.theta = theta;
+  s->half = 0;
+  if (rho_n == 0.0) {            // invariant subspace: this step's update is exact
+    q.inv_rho = 0.0;
+    q.cp = mk<double>(0.0, 0.0);
+    s->half = 2;
+  } else {
+    const c128 delta = scale<double>(vtv, 1.0 / (rho_n * rho_n));
+    q.inv_rho = 1.0 / rho_n;
+    q.cp = scale<double>(cdivd(delta, q.eps_new), rho_n);
+    q.delta = delta;
+    if (sqrt(cabs2(delta)) < 1e-30) s->half = 1;   // next v^T v vanishes: breakdown after this step
+  }
+  q.rho = rho_n;
+  q.eps = q.eps_new;
+}
+
+// stop test on the nb partials of |r|^2 of the k2 sweep (all threads of one block)
+__device__ void qmr_c_fin(Scal* s, const double* part, int nb, int* mask, int rr) {
+  double f[1];
+  fin_k<1>(part, kNB, 1, nb, f);
+  const double rn2 = f[0];
+  if (threadIdx.x) return;
+  const double res = sqrt(rn2) / s->bnorm;
+  s->res = res;
+  s->iters++;
+  if (!isfinite(res)) { s->status = DDA_ERR_NONFINITE; s->done = 1; }
+  else if (res < s->tol) { s->status = DDA_OK; s->done = 1; }
+  else if (s->half) { s->status = DDA_BREAKDOWN; s->done = 1; }
+  if (mask) mask[rr] = s->done;
+}
+
+// vt = pt - beta v (into v); partials of vt^T vt and |vt|^2, reduced by the
+// last block to finish (qmr_b_fin)
 template <typename R>
 __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, cpx<R>* __restrict__ v,
-                                                long long n, const Scal* s, double* part) {
+                                                long long n, Scal* s, double* part, int* mask) {
   pt += blockIdx.y * n; v += blockIdx.y * n; part += blockIdx.y * kPS; s += blockIdx.y;
   if (s->done) return;
   const cpx<R> be = cs<R>(s->q.beta);
@@ -381,53 +463,18 @@ __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, c
   }
   double acc[3] = {q0.get(), q1.get(), q2.get()};
   block_store<3, R>(acc, part, 0);
-}
-
-// rho_{i+1}, delta_{i+1}, the quasi-minimisation scalars of step i and the
-// coefficients of the update and of the next direction
-__global__ void k_qmr_b(Scal* s, const double* part, int nb) {
-  s += blockIdx.x; part += blockIdx.x * kPS;
-  if (s->done) return;
-  double f[3];
-  fin_k<3>(part, kNB, 1, nb, f);
-  if (threadIdx.x) return;
-  QmrScal& q = s->q;
-  const c128 vtv = mk<double>(f[0], f[1]);
-  const double rho_n = sqrt(f[2]);
-  const double theta = rho_n / (q.g * sqrt(cabs2(q.beta)));
-  const double g = 1.0 / sqrt(1.0 + theta * theta);
-  const c128 eta = scale<double>(cdivd(q.eta, q.beta), -q.rho * g * g / (q.g * q.g));
-  if (!isfinite(rho_n) || !cfinite(vtv) || !isfinite(theta) || !cfinite(eta)) {
-    s->status = DDA_ERR_NONFINITE; s->done = 1; return;
-  }
-  q.cd = (q.theta * g) * (q.theta * g);
-  q.eta = eta;
-  q.g = g;
-  q.theta = theta;
-  s->half = 0;
-  if (rho_n == 0.0) {            // invariant subspace: this step's update is exact
-    q.inv_rho = 0.0;
-    q.cp = mk<double>(0.0, 0.0);
-    s->half = 2;
-  } else {
-    const c128 delta = scale<double>(vtv, 1.0 / (rho_n * rho_n));
-    q.inv_rho = 1.0 / rho_n;
-    q.cp = scale<double>(cdivd(delta, q.eps_new), rho_n);
-    q.delta = delta;
-    if (sqrt(cabs2(delta)) < 1e-30) s->half = 1;   // next v^T v vanishes: breakdown after this step
-  }
-  q.rho = rho_n;
-  q.eps = q.eps_new;
+  if (last_block(&s->cnt)) qmr_b_fin(s, part, gridDim.x, mask, blockIdx.y);
 }
 
 // d = eta p + cd d;  s = eta pt + cd s;  x += d;  r -= s (partial |r|^2);
-// then v_{i+1} = vt / rho_{i+1} and p_{i+1} = v_{i+1} - cp p_i
+// then v_{i+1} = vt / rho_{i+1} and p_{i+1} = v_{i+1} - cp p_i; the last
+// block to finish takes the stop test (qmr_c_fin)
 template <typename R>
 __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* __restrict__ p,
                                                 const cpx<R>* __restrict__ pt, cpx<R>* __restrict__ d,
                                                 cpx<R>* __restrict__ sv, cpx<R>* __restrict__ x,
-                                                cpx<R>* __restrict__ r, long long n, const Scal* s,
-                                                double* part) {
+                                                cpx<R>* __restrict__ r, long long n, Scal* s,
+                                                double* part, int* mask) {
   const long long o = blockIdx.y * n;
   v += o; p += o; pt += o; d += o; sv += o; x += o; r += o;
   part += blockIdx.y * kPS; s += blockIdx.y;
@@ -452,26 +499,7 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* 
   }
   double a[1] = {acc.get()};
   block_store<1, R>(a, part, 0);
-}
-
-__global__ void k_qmr_c(Scal* s, const double* part, int nb, int* mask) {
-  const int rr = blockIdx.x;
-  s += rr; part += rr * kPS;
-  if (s->done) {
-    if (mask && threadIdx.x == 0) mask[rr] = 1;
-    return;
-  }
-  double f[1];
-  fin_k<1>(part, kNB, 1, nb, f);
-  const double rn2 = f[0];
-  if (threadIdx.x) return;
-  const double res = sqrt(rn2) / s->bnorm;
-  s->res = res;
-  s->iters++;
-  if (!isfinite(res)) { s->status = DDA_ERR_NONFINITE; s->done = 1; }
-  else if (res < s->tol) { s->status = DDA_OK; s->done = 1; }
-  else if (s->half) { s->status = DDA_BREAKDOWN; s->done = 1; }
-  if (mask) mask[rr] = s->done;
+  if (last_block(&s->cnt)) qmr_c_fin(s, part, gridDim.x, mask, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- Bi-CG-CS (COCG)
@@ -840,15 +868,13 @@ int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, do
       int dnb = 0;
       RK(matvec<R>(ru, p, pt, false, h->d_mvpart, &dnb));
       if (dnb > 0) {
-        k_qmr_a<<<1, kVT, 0, st>>>(s, h->d_mvpart, 1, 2, 0, dnb); count_launch();
+        k_qmr_a<<<1, kVT, 0, st>>>(s, h->d_mvpart, 1, 2, 0, dnb, nullptr); count_launch();
       } else {
         k_dot<R, false><<<nb, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
-        k_qmr_a<<<1, kVT, 0, st>>>(s, part, kNB, 1, 0, nb); count_launch();
+        k_qmr_a<<<1, kVT, 0, st>>>(s, part, kNB, 1, 0, nb, nullptr); count_launch();
       }
-      k_qmr_k1<R><<<nb, kVT, 0, st>>>(pt, v, n, s, part); count_launch();
-      k_qmr_b<<<1, kVT, 0, st>>>(s, part, nb); count_launch();
-      k_qmr_k2<R><<<nb, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part); count_launch();
-      k_qmr_c<<<1, kVT, 0, st>>>(s, part, nb, nullptr); count_launch();
+      k_qmr_k1<R><<<nb, kVT, 0, st>>>(pt, v, n, s, part, nullptr); count_launch();
+      k_qmr_k2<R><<<nb, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part, nullptr); count_launch();
       LK(h);
       ru.iters++;
       RK(sync_read(ru));
@@ -1338,24 +1364,18 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
       Tracer* tr = h->g.tr;
       tr_begin(tr, st);
       if (dnb > 0) {
-        k_qmr_a<<<nr, kVT, 0, st>>>(s, m->mvpart, 1, 2, 2LL * dnb, dnb); count_launch();
+        k_qmr_a<<<nr, kVT, 0, st>>>(s, m->mvpart, 1, 2, 2LL * dnb, dnb, m->mask); count_launch();
       } else {
         k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
-        k_qmr_a<<<nr, kVT, 0, st>>>(s, part, kNB, 1, kPS, nb); count_launch();
+        k_qmr_a<<<nr, kVT, 0, st>>>(s, part, kNB, 1, kPS, nb, m->mask); count_launch();
       }
       tr_end(tr, st, TR_QMR_SCALARS);
       tr_begin(tr, st);
-      k_qmr_k1<R><<<vg, kVT, 0, st>>>(pt, v, n, s, part); count_launch();
+      k_qmr_k1<R><<<vg, kVT, 0, st>>>(pt, v, n, s, part, m->mask); count_launch();
       tr_end(tr, st, TR_QMR_K1);
       tr_begin(tr, st);
-      k_qmr_b<<<nr, kVT, 0, st>>>(s, part, nb); count_launch();
-      tr_end(tr, st, TR_QMR_SCALARS);
-      tr_begin(tr, st);
-      k_qmr_k2<R><<<vg, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part); count_launch();
+      k_qmr_k2<R><<<vg, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part, m->mask); count_launch();
       tr_end(tr, st, TR_QMR_K2);
-      tr_begin(tr, st);
-      k_qmr_c<<<nr, kVT, 0, st>>>(s, part, nb, m->mask); count_launch();
-      tr_end(tr, st, TR_QMR_SCALARS);
       LK(h);
     }
     RK(bsync(b));

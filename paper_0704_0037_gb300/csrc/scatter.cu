@@ -149,34 +149,39 @@ __global__ void __launch_bounds__(256) k_collapse_y(const c128* __restrict__ P, 
 
 struct Wave2 { double a[3]; double e[6]; };
 
-// per-row-chunk partials of sum Im(E_inc^* . P) and sum w |P|^2
+// per-row-chunk partials of sum Im(E_inc^* . P) and sum w |P|^2.  ptab holds
+// exp(-i kd a_mu r_mu) along x, then y, then z (k_phase_tab for the incidence
+// direction a), so exp(-i kd a.r) is a product of three table entries.
 __global__ void __launch_bounds__(256) k_qsums(const c128* __restrict__ P, LatticeDev lat,
-                                               const c128* __restrict__ beta, long long n_occ, int nx,
-                                               int ny, int nz, int nrows, double kd, Wave2 w,
+                                               const c128* __restrict__ beta, int n_mat,
+                                               long long n_occ, int nx, int ny, int nrows, double kd,
+                                               Wave2 w, const c128* __restrict__ ptab,
                                                double* __restrict__ part) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const double k3 = kd * kd * kd;
+  // absorption weight -Im(1/alpha) - (2/3) kd^3 per material and component
+  __shared__ double wab[3 * 256];
+  for (int i = threadIdx.x; i < 3 * n_mat; i += blockDim.x) {
+    const c128 al = beta[i] * beta[i];
+    wab[i] = al.y / (al.x * al.x + al.y * al.y) - (2.0 / 3.0) * k3;
+  }
+  __syncthreads();
+  // E = e exp(i phi); E^* . P = conj(e) exp(-i phi) P
+  const c128 e0 = mk<double>(w.e[0], -w.e[1]), e1 = mk<double>(w.e[2], -w.e[3]),
+             e2 = mk<double>(w.e[4], -w.e[5]);
   double se = 0.0, sa = 0.0;
   for (int row = blockIdx.x * 8 + wid; row < nrows; row += nwarps) {
     const int iy = row % ny, iz = row / ny;
-    const double ry = 0.5 * (2 * iy + 1 - ny), rz = 0.5 * (2 * iz + 1 - nz);
+    const c128 pyz = ptab[nx + iy] * ptab[nx + ny + iz];
     for (long long i = lat.row_off[row] + lane; i < lat.row_off[row + 1]; i += 32) {
-      const double rx = 0.5 * (2 * (int)lat.xi[i] + 1 - nx);
-      double sn, cn;
-      sincos(kd * (w.a[0] * rx + w.a[1] * ry + w.a[2] * rz), &sn, &cn);
+      const c128 ph = ptab[lat.xi[i]] * pyz;
       const int m = lat.mat[i];
-      for (int c = 0; c < 3; ++c) {
-        const c128 p = P[c * n_occ + i];
-        // E = e exp(i phi); E^* . P = conj(e) exp(-i phi) P
-        const c128 e = mk<double>(w.e[2 * c], -w.e[2 * c + 1]);
-        const c128 t = e * mk<double>(cn, -sn) * p;
-        se += t.y;
-        const c128 b = beta[m * 3 + c];
-        const c128 al = b * b;
-        const double ia = -al.y / (al.x * al.x + al.y * al.y);   // Im(1/alpha)
-        sa += (-ia - (2.0 / 3.0) * k3) * (p.x * p.x + p.y * p.y);
-      }
+      const c128 p0 = P[i], p1 = P[n_occ + i], p2 = P[2 * n_occ + i];
+      const c128 t = (e0 * p0 + e1 * p1 + e2 * p2) * ph;
+      se += t.y;
+      sa += wab[3 * m] * (p0.x * p0.x + p0.y * p0.y) + wab[3 * m + 1] * (p1.x * p1.x + p1.y * p1.y) +
+            wab[3 * m + 2] * (p2.x * p2.x + p2.y * p2.y);
     }
   }
   __shared__ double sh[2][8];
@@ -244,7 +249,9 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
     rows_per_chunk = (fnrows + n_chunks - 1) / n_chunks;
     n_chunks = (fnrows + rows_per_chunk - 1) / rows_per_chunk;
   }
-  const size_t tab_b = (size_t)std::max(n_dir, 1) * L * sizeof(c128) + (size_t)std::max(n_dir, 1) * 3 * sizeof(double);
+  const int Lq = g.nx + g.ny + g.nz;   // incidence phase table of the Q sums
+  const size_t tab_b = (size_t)std::max(n_dir, 1) * L * sizeof(c128) + (size_t)Lq * sizeof(c128) +
+                       (size_t)(std::max(n_dir, 1) + 1) * 3 * sizeof(double);
   const size_t fp_b = std::max((size_t)n_chunks * std::max(n_dir, 1) * 6, (size_t)2 * qblocks) * sizeof(double) +
                       (size_t)std::max(n_dir, 1) * 6 * sizeof(double);
   if (h->tab_bytes < tab_b) {
@@ -258,7 +265,9 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
     h->fpart_bytes = fp_b;
   }
   c128* tab = (c128*)h->d_tab;
-  double* d_dirs = (double*)(tab + (size_t)std::max(n_dir, 1) * L);
+  c128* qtab = tab + (size_t)std::max(n_dir, 1) * L;
+  double* d_dirs = (double*)(qtab + Lq);
+  double* d_qdir = d_dirs + (size_t)std::max(n_dir, 1) * 3;
   double* part = h->d_fpart;
   double* d_F = part + std::max((size_t)n_chunks * std::max(n_dir, 1) * 6, (size_t)2 * qblocks);
   if (n_dir > 0) {
@@ -292,8 +301,11 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
     Wave2 w;
     for (int q = 0; q < 3; ++q) w.a[q] = prop[3 * r + q];
     for (int q = 0; q < 6; ++q) w.e[q] = pol[6 * r + q];
+    DDA_CK(h, cudaMemcpyAsync(d_qdir, prop + 3 * r, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
     tr_begin(g.tr, st);
-    k_qsums<<<qblocks, 256, 0, st>>>(P, h->lat(), beta, g.n_occ, g.nx, g.ny, g.nz, g.nrows, h->kd, w, part); count_launch();
+    k_phase_tab<<<(Lq + 255) / 256, 256, 0, st>>>(d_qdir, 1, h->kd, g.nx, g.ny, g.nz, qtab); count_launch();
+    k_qsums<<<qblocks, 256, 0, st>>>(P, h->lat(), beta, h->n_mat, g.n_occ, g.nx, g.ny, g.nrows, h->kd, w,
+                                     qtab, part); count_launch();
     tr_end(g.tr, st, TR_QSUMS);
     DDA_CK(h, cudaGetLastError());
     DDA_CK(h, cudaMemcpyAsync(qp.data(), part, 2 * qblocks * sizeof(double), cudaMemcpyDeviceToHost, st));
