@@ -119,6 +119,8 @@ __device__ void fin_k(const double* p, long long ks, long long is, int nb, doubl
   double v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) v[k] = 0.0;
+  // four strides' loads in flight per thread (the partials come from L2)
+#pragma unroll 4
   for (int i = threadIdx.x; i < nb; i += blockDim.x)
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] += __ldcg(p + k * ks + i * is);   // other blocks' writes
@@ -142,18 +144,17 @@ __device__ void fin_k(const double* p, long long ks, long long is, int nb, doubl
 // blocks working on one right-hand side (counter *cnt, reset here for the
 // next sweep); every block's partials are then visible to it.  A sweep ends
 // with its reduction in that block instead of a separate one-block launch.
+// Thread 0 wrote the block's partials (block_store), so it alone fences
+// before counting; the last block reads the partials through L2 (fin_k).
 __device__ bool last_block(int* cnt) {
   __shared__ int is_last;
-  __threadfence();
-  __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     is_last = atomicAdd(cnt, 1) == (int)gridDim.x - 1;
     if (is_last) *cnt = 0;
   }
   __syncthreads();
-  const bool r = is_last != 0;
-  if (r) __threadfence();
-  return r;
+  return is_last != 0;
 }
 
 // Running sum of the products for complex128 vectors in FP64; for complex64
@@ -483,19 +484,37 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* 
   const cpx<R> et = cs<R>(q.eta), cp = cs<R>(q.cp);
   const R cd = (R)q.cd, ir = (R)q.inv_rho;
   Acc<R> acc;
-  VLOOP(n) {
-    const cpx<R> pi = p[i];
-    const cpx<R> di = fmas<R>(d[i], cd, et * pi);
-    const cpx<R> si = fmas<R>(sv[i], cd, et * pt[i]);
-    d[i] = di;
-    sv[i] = si;
-    x[i] = x[i] + di;
-    const cpx<R> rr = r[i] - si;
-    r[i] = rr;
-    acc.add(rr.x * rr.x + rr.y * rr.y);
-    const cpx<R> vn = scale<R>(v[i], ir);
-    v[i] = vn;
-    p[i] = vn - cp * pi;
+  // two elements per step with their fourteen loads issued together
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i < n; i += 2 * stride) {
+    const int m = i + stride < n ? 2 : 1;
+    cpx<R> pv[2], dv[2], tv[2], sw[2], xv[2], rv[2], vv[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u < m) {
+        const long long j = i + u * stride;
+        pv[u] = p[j]; dv[u] = d[j]; tv[u] = pt[j]; sw[u] = sv[j];
+        xv[u] = x[j]; rv[u] = r[j]; vv[u] = v[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u < m) {
+        const long long j = i + u * stride;
+        const cpx<R> di = fmas<R>(dv[u], cd, et * pv[u]);
+        const cpx<R> si = fmas<R>(sw[u], cd, et * tv[u]);
+        d[j] = di;
+        sv[j] = si;
+        x[j] = xv[u] + di;
+        const cpx<R> rr = rv[u] - si;
+        r[j] = rr;
+        acc.add(rr.x * rr.x + rr.y * rr.y);
+        const cpx<R> vn = scale<R>(vv[u], ir);
+        v[j] = vn;
+        p[j] = vn - cp * pv[u];
+      }
+    }
   }
   double a[1] = {acc.get()};
   block_store<1, R>(a, part, 0);
