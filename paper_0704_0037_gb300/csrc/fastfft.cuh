@@ -171,6 +171,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Fetch the 128-byte line holding p into L2 (no data returned to the thread)
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
@@ -226,6 +230,25 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict
     }
   }
   (void)col;
+  {
+    // Warm L2 with the octant entries of the Fourier-space product (fy of
+    // this block, its range of fx, every fz and component): they arrive from
+    // HBM while the forward transforms run, so the product's loads hit L2.
+    const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
+    const long long octs = (long long)hx * hy * hz;
+    int nys, na, nb;
+    const int fy = fold_axis(ky, My, nys);
+    const int kxa = blockIdx.x * T, kxb = min(kxa + T, Mx) - 1;
+    const int fa = fold_axis(kxa, Mx, na), fb = fold_axis(kxb, Mx, nb);
+    const int fmin = min(fa, fb);
+    const int fmax = (2 * kxa <= Mx && 2 * kxb >= Mx) ? Mx / 2 : max(fa, fb);
+    for (int k = threadIdx.x; k < 6 * hz; k += NT) {
+      const int c6 = k / hz, fz = k - c6 * hz;
+      const cpx<R>* row = D + c6 * octs + ((long long)fz * hy + fy) * hx;
+      prefetch_l2(row + fmin);
+      if (((size_t)(row + fmax) >> 7) != ((size_t)(row + fmin) >> 7)) prefetch_l2(row + fmax);
+    }
+  }
   load_tw(s_tw, tw, M, NT);
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
