@@ -589,7 +589,8 @@ extern "C" int dda_free(dda_t h) {
   cudaFree(h->d_row_off); cudaFree(h->d_xi); cudaFree(h->d_mat);
   cudaFree(h->sv); cudaFree(h->d_part); cudaFree(h->d_mvpart); cudaFree(h->d_scal); cudaFreeHost(h->h_scal);
   batch_free(h);
-  cudaFree(h->d_tab); cudaFree(h->d_fpart); cudaFree(h->d_coll);
+  cudaFree(h->d_tab); cudaFree(h->d_fpart); cudaFree(h->d_coll); cudaFree(h->d_dscratch);
+  cudaFree(h->d_ptab);
   cudaGetLastError();
   delete h;
   return DDA_OK;

@@ -12,6 +12,7 @@
 // even or odd along axis a (odd iff exactly one of mu, nu is a), and the DFT
 // keeps that parity, which is how Sec. 2's "symmetry of the interaction
 // matrix" reduces the memory of its Fourier transform.  1/(Mx My Mz) is folded in.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -23,39 +24,60 @@ __device__ __forceinline__ c128 store_as(c128 v, c128*) { return v; }
 __device__ __forceinline__ cdf store_as(c128 v, cdf*) { return to_cdf(v); }
 __device__ __forceinline__ c128 neg_of(c128 v) { return mk<double>(-v.x, -v.y); }
 __device__ __forceinline__ cdf neg_of(cdf v) { return mk<df>(-v.x, -v.y); }
+// an integer below 2^24, exactly, in either arithmetic
+__device__ __forceinline__ double from_int(int v, double*) { return (double)v; }
+__device__ __forceinline__ df from_int(int v, df*) { return df((float)v, 0.0f); }
+
+// G depends on the offset d through rho^2 = |d|^2, an integer n, and the
+// products d_mu d_nu: G_mu,nu(d) = A(n) delta_mu,nu - B(n) d_mu d_nu with
+//   A(n) = exp(i kappa rho)/rho^3 (kappa^2 rho^2 - 1 + i kappa rho),
+//   B(n) = exp(i kappa rho)/rho^5 (kappa^2 rho^2 - 3 + 3 i kappa rho).
+// ab[2n], ab[2n+1] = A(n), B(n) for 1 <= n <= nmax (FP64, one sincos per n),
+// stored in the table's arithmetic.
+template <typename T>
+__global__ void k_green_radial(T* __restrict__ ab, double kd, int nmax) {
+  for (int n = 1 + blockIdx.x * blockDim.x + threadIdx.x; n <= nmax; n += gridDim.x * blockDim.x) {
+    const double r2 = (double)n;
+    const double rho = sqrt(r2);
+    const double kr = kd * rho;
+    double sn, cn;
+    sincos(kr, &sn, &cn);
+    const double inv3 = 1.0 / (r2 * rho);
+    const c128 pref = mk<double>(cn * inv3, sn * inv3);
+    ab[2 * n] = store_as(pref * mk<double>(kr * kr - 1.0, kr), (T*)nullptr);
+    ab[2 * n + 1] = store_as(pref * mk<double>((kr * kr - 3.0) / r2, 3.0 * kr / r2), (T*)nullptr);
+  }
+}
 
 // G for every non-negative offset (dx, dy, dz) < (nx, ny, nz), all six
-// components from one evaluation of exp(i kappa rho): table[6][nz][ny][nx].
-template <typename T>
-__global__ void k_green_table(T* __restrict__ table, double kd, int nx, int ny, int nz) {
+// components from A(n), B(n): table[6][nz][ny][nx].  d_mu d_nu is an integer
+// below 2^24, exact in either arithmetic.
+template <typename R>
+__global__ void k_green_table(cpx<R>* __restrict__ table, const cpx<R>* __restrict__ ab, int nx,
+                              int ny, int nz) {
   const long long total = (long long)nx * ny * nz;
   const int rows = ny * nz;
   for (int row = blockIdx.x; row < rows; row += gridDim.x) {     // a block per (y, z) row
     const int iy = row % ny, iz = row / ny;
     for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
       const long long i = (long long)row * nx + ix;
-      const double d[3] = {(double)ix, (double)iy, (double)iz};
-      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      c128 g[6];
-      for (int c = 0; c < 6; ++c) g[c] = mk<double>(0.0, 0.0);
-      if (r2 > 0.0) {
-        const double rho = sqrt(r2);
-        const double kr = kd * rho;
-        double sn, cn;
-        sincos(kr, &sn, &cn);
-        const double inv3 = 1.0 / (r2 * rho);
-        const c128 pref = mk<double>(cn * inv3, sn * inv3);
-        const c128 a = mk<double>(kr * kr - 1.0, kr);
-        const c128 b = mk<double>((kr * kr - 3.0) / r2, 3.0 * kr / r2);
+      const int d[3] = {ix, iy, iz};
+      const int n = ix * ix + iy * iy + iz * iz;
+      cpx<R> g[6];
+      if (n > 0) {
+        const cpx<R> A = ab[2 * n], B = ab[2 * n + 1];
         const int mu_of[6] = {0, 0, 0, 1, 1, 2}, nu_of[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
         for (int k = 0; k < 6; ++k) {
-          const double dd = d[mu_of[k]] * d[nu_of[k]];
-          c128 t = mk<double>(-b.x * dd, -b.y * dd);
-          if (mu_of[k] == nu_of[k]) t = t + a;
-          g[k] = pref * t;
+          const cpx<R> t = scale<R>(B, from_int(d[mu_of[k]] * d[nu_of[k]], (R*)nullptr));
+          g[k] = mu_of[k] == nu_of[k] ? A - t : neg_of(t);
         }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) g[k] = mk<R>(from_int(0, (R*)nullptr), from_int(0, (R*)nullptr));
       }
-      for (int k = 0; k < 6; ++k) table[(long long)k * total + i] = store_as(g[k], (T*)nullptr);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) table[(long long)k * total + i] = g[k];
     }
   }
 }
@@ -278,22 +300,46 @@ int dda_build_D_internal(dda_t h, bool want32) {
     rc = alloc((void**)&h->w64.D, 6 * oct * sizeof(c128), "cannot allocate the FP64 D-matrix octant");
   }
   if (rc != DDA_OK) return rc;
-  void* grid = nullptr;
-  void* grid2 = nullptr;
-  void* table = nullptr;
-  if (cudaMalloc(&grid, full * sizeof(c128)) != cudaSuccess ||
-      cudaMalloc(&table, 6 * tsz * sizeof(c128)) != cudaSuccess ||
-      (fast && cudaMalloc(&grid2, full * sizeof(c128)) != cudaSuccess)) {
-    cudaGetLastError();
-    cudaFree(grid);
-    cudaFree(table);
-    return dda_fail(h, DDA_ERR_OOM, "cannot allocate the Green's tensor grid");
-  }
-  tr_begin(g.tr, st);
-  if (use_df) {
-    k_green_table<cdf><<<rows_grid(g.ny * g.nz), 128, 0, st>>>((cdf*)table, h->kd, g.nx, g.ny, g.nz); count_launch();
+  // scratch: two padded grids, the offset table and the A, B table; kept in
+  // the handle for later builds when it is small (the bench and batch
+  // workloads rebuild per particle), allocated per build otherwise
+  const int nmax = (g.nx - 1) * (g.nx - 1) + (g.ny - 1) * (g.ny - 1) + (g.nz - 1) * (g.nz - 1);
+  const size_t grid_b = (size_t)full * sizeof(c128);
+  const size_t table_b = (size_t)6 * tsz * sizeof(c128);
+  const size_t ab_b = (size_t)2 * (nmax + 1) * sizeof(c128);
+  const size_t need = (fast ? 2 : 1) * grid_b + table_b + ab_b;
+  constexpr size_t kKeepScratch = (size_t)2 << 30;
+  void* scratch = nullptr;
+  if (h->d_dscratch && h->dscratch_bytes >= need) {
+    scratch = h->d_dscratch;
   } else {
-    k_green_table<c128><<<rows_grid(g.ny * g.nz), 128, 0, st>>>((c128*)table, h->kd, g.nx, g.ny, g.nz); count_launch();
+    cudaFree(h->d_dscratch);
+    h->d_dscratch = nullptr;
+    h->dscratch_bytes = 0;
+    if (cudaMalloc(&scratch, need) != cudaSuccess) {
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "cannot allocate the Green's tensor grid");
+    }
+    if (need <= kKeepScratch) {
+      h->d_dscratch = scratch;
+      h->dscratch_bytes = need;
+    }
+  }
+  void* grid = scratch;
+  void* table = (char*)scratch + grid_b;
+  void* ab = (char*)table + table_b;
+  void* grid2 = fast ? (char*)ab + ab_b : nullptr;
+  auto release = [&]() {
+    if (scratch != h->d_dscratch) cudaFree(scratch);
+  };
+  tr_begin(g.tr, st);
+  const int rgrid = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, 152LL * 8));
+  if (use_df) {
+    k_green_radial<cdf><<<rgrid, 256, 0, st>>>((cdf*)ab, h->kd, nmax); count_launch();
+    k_green_table<df><<<rows_grid(g.ny * g.nz), 128, 0, st>>>((cdf*)table, (const cdf*)ab, g.nx, g.ny, g.nz); count_launch();
+  } else {
+    k_green_radial<c128><<<rgrid, 256, 0, st>>>((c128*)ab, h->kd, nmax); count_launch();
+    k_green_table<double><<<rows_grid(g.ny * g.nz), 128, 0, st>>>((c128*)table, (const c128*)ab, g.nx, g.ny, g.nz); count_launch();
   }
   tr_end(g.tr, st, TR_DB_GREEN);
   const int comps[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
@@ -306,9 +352,7 @@ int dda_build_D_internal(dda_t h, bool want32) {
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   tr_flush(g.tr);
-  cudaFree(grid);
-  cudaFree(grid2);
-  cudaFree(table);
+  release();
   if (e != cudaSuccess) return dda_cuda_fail(h, e, "D-matrix build");
   h->w64.have_D = true;
   h->d64_from_df = use_df;

@@ -149,6 +149,9 @@ struct dda_ctx {
   size_t fpart_bytes = 0;
   void* d_coll = nullptr;         // y-collapsed polarization + its lattice
   size_t coll_bytes = 0;
+  void* d_dscratch = nullptr;     // D-matrix build scratch kept between builds (small grids)
+  size_t dscratch_bytes = 0;
+  void* d_ptab = nullptr;         // incident-wave phase per axis (right-hand sides), complex128
   dda::LatticeDev lat() const { return {d_row_off, d_xi, d_mat}; }
 };
 

@@ -247,21 +247,33 @@ __global__ void k_copy(const cpx<R>* __restrict__ a, cpx<R>* __restrict__ b, lon
 // ---------------------------------------------------------------- RHS and P
 struct Wave { double a[3]; double e[6]; };
 
-// b_i = beta_i e exp(i kd a.r_i)  (Eq. (3)), rows in parallel, a warp per row
+// exp(i kd a_mu r_mu) along x (nx entries), then y, then z: the incident
+// phase exp(i kd a.r) of a dipole is the product of three entries
+__global__ void k_axis_phase(c128* __restrict__ tab, double kd, Wave w, int nx, int ny, int nz) {
+  const int L = nx + ny + nz;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
+    int j = k, axis = 0, n = nx;
+    if (j >= nx) { j -= nx; axis = 1; n = ny; if (j >= ny) { j -= ny; axis = 2; n = nz; } }
+    double sn, cn;
+    sincos(kd * w.a[axis] * (0.5 * (2 * j + 1 - n)), &sn, &cn);
+    tab[k] = mk<double>(cn, sn);
+  }
+}
+
+// b_i = beta_i e exp(i kd a.r_i)  (Eq. (3)), rows in parallel, a warp per
+// row; ptab from k_axis_phase
 template <typename R>
 __global__ void k_rhs(cpx<R>* __restrict__ b, LatticeDev lat, const c128* __restrict__ beta,
-                      long long n_occ, int nx, int ny, int nz, int nrows, double kd, Wave w) {
+                      long long n_occ, int nx, int ny, int nrows, const c128* __restrict__ ptab,
+                      Wave w) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int row = warp; row < nrows; row += nwarps) {
     const int iy = row % ny, iz = row / ny;
-    const double ry = 0.5 * (2 * iy + 1 - ny), rz = 0.5 * (2 * iz + 1 - nz);
+    const c128 pyz = ptab[nx + iy] * ptab[nx + ny + iz];
     for (long long i = lat.row_off[row] + lane; i < lat.row_off[row + 1]; i += 32) {
-      const double rx = 0.5 * (2 * (int)lat.xi[i] + 1 - nx);
-      double sn, cn;
-      sincos(kd * (w.a[0] * rx + w.a[1] * ry + w.a[2] * rz), &sn, &cn);
-      const c128 ph = mk<double>(cn, sn);
+      const c128 ph = ptab[lat.xi[i]] * pyz;
       for (int c = 0; c < 3; ++c) {
         const c128 e = mk<double>(w.e[2 * c], w.e[2 * c + 1]);
         const c128 v = beta[lat.mat[i] * 3 + c] * (e * ph);
@@ -269,6 +281,26 @@ __global__ void k_rhs(cpx<R>* __restrict__ b, LatticeDev lat, const c128* __rest
       }
     }
   }
+}
+
+// b = beta e exp(i kd a.r) for one right-hand side on stream st
+int launch_rhs(dda_t h, c128* b, const c128* beta, const Wave& wv, cudaStream_t st) {
+  const Geom& g = h->g;
+  if (!h->d_ptab) {
+    if (cudaMalloc(&h->d_ptab, (size_t)(g.nx + g.ny + g.nz) * sizeof(c128)) != cudaSuccess) {
+      h->d_ptab = nullptr;
+      cudaGetLastError();
+      return dda_fail(h, DDA_ERR_OOM, "incident phase table");
+    }
+  }
+  const int L = g.nx + g.ny + g.nz;
+  c128* ptab = (c128*)h->d_ptab;
+  k_axis_phase<<<(L + 255) / 256, 256, 0, st>>>(ptab, h->kd, wv, g.nx, g.ny, g.nz); count_launch();
+  const int rows_grid = (int)std::min<long long>((g.nrows + 7) / 8, 152LL * 32);
+  k_rhs<double><<<rows_grid, 256, 0, st>>>(b, h->lat(), beta, g.n_occ, g.nx, g.ny, g.nrows, ptab,
+                                           wv); count_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DDA_OK : dda_cuda_fail(h, e, "right-hand side");
 }
 
 // P = beta x (Eq. (3)), FP64 output
@@ -1053,8 +1085,7 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
       for (int i = 0; i < nvec; ++i) vec[i] = base + (size_t)i * n;
       c128* b = base + (size_t)nvec * n;   // b lives after the pool
       c128* x = vec[9];
-      k_rhs<double><<<rows_grid, 256, 0, ru.st>>>(b, h->lat(), beta64, h->g.n_occ, h->g.nx, h->g.ny,
-                                                 h->g.nz, h->g.nrows, h->kd, wv); count_launch();
+      RK(launch_rhs(h, b, beta64, wv, ru.st));
       LK(h);
       RK(run_solver<double>(ru, o->solver, b, x, vec, o->tol, o->maxiter));
       st_rhs = ru.hs->status;
@@ -1082,8 +1113,7 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
       c128* x64 = b64 + n;
       c128* r64 = x64 + n;
       c128* w64 = r64 + n;
-      k_rhs<double><<<rows_grid, 256, 0, ru.st>>>(b64, h->lat(), beta64, h->g.n_occ, h->g.nx, h->g.ny,
-                                                 h->g.nz, h->g.nrows, h->kd, wv); count_launch();
+      RK(launch_rhs(h, b64, beta64, wv, ru.st));
       k_norms<double><<<ru.nb, kVT, 0, ru.st>>>(b64, n, ru.part, nullptr); count_launch();
       k_take_norm<<<1, kVT, 0, ru.st>>>(ru.ds, ru.part, ru.nb); count_launch();
       k_copy<double><<<ru.nb, kVT, 0, ru.st>>>(b64, r64, n); count_launch();
@@ -1494,10 +1524,7 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
     Wave wv;
     for (int q = 0; q < 3; ++q) wv.a[q] = prop[3 * r + q];
     for (int q = 0; q < 6; ++q) wv.e[q] = pol[6 * r + q];
-    k_rhs<double><<<rows_grid, 256, 0, st>>>(b64 + (size_t)r * n, h->lat(),
-                                             h->w64.beta + (long long)r * h->n_mat * 3,
-                                             h->g.n_occ, h->g.nx, h->g.ny, h->g.nz, h->g.nrows,
-                                             h->kd, wv); count_launch();
+    RK(launch_rhs(h, b64 + (size_t)r * n, h->w64.beta + (long long)r * h->n_mat * 3, wv, st));
   }
   LK(h);
   const dim3 vg(b.nb, nrhs);

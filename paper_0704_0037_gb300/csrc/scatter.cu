@@ -125,15 +125,20 @@ __global__ void k_farfield_fin(const double* __restrict__ part, int n_chunks, in
 // are added in y order into a shared [nx][3] accumulator (dipoles of one row
 // have distinct x, so the order of every sum is fixed).  Q is laid out as the
 // dipole vector of a full nx x 1 x nz lattice: [3][nz*nx].
+// Sum of P over y for every (x, z): the far field in a plane with n_y = 0
+// needs only that.  Block (z, gy) sums the rows y of group gy (of G) into
+// shared memory and writes them as a partial; k_collapse_fin adds the G
+// partials in order (deterministic).  part [G][3][nq], Q [3][nq], nq = nx nz.
 __global__ void __launch_bounds__(256) k_collapse_y(const c128* __restrict__ P, LatticeDev lat,
                                                     long long n_occ, int nx, int ny,
-                                                    c128* __restrict__ Q, long long nq) {
+                                                    c128* __restrict__ part, long long nq) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   c128* acc = reinterpret_cast<c128*>(smem_raw);
-  const int z = blockIdx.x;
+  const int z = blockIdx.x, gy = blockIdx.y, G = gridDim.y;
+  const int y0 = (int)((long long)gy * ny / G), y1 = (int)((long long)(gy + 1) * ny / G);
   for (int i = threadIdx.x; i < 3 * nx; i += blockDim.x) acc[i] = mk<double>(0.0, 0.0);
   __syncthreads();
-  for (int y = 0; y < ny; ++y) {
+  for (int y = y0; y < y1; ++y) {
     const int row = z * ny + y;
     for (long long i = lat.row_off[row] + threadIdx.x; i < lat.row_off[row + 1]; i += blockDim.x) {
       const int x = lat.xi[i];
@@ -143,11 +148,23 @@ __global__ void __launch_bounds__(256) k_collapse_y(const c128* __restrict__ P, 
   }
   for (int i = threadIdx.x; i < 3 * nx; i += blockDim.x) {
     const int x = i / 3, c = i - 3 * x;
-    Q[c * nq + (long long)z * nx + x] = acc[i];
+    part[((long long)gy * 3 + c) * nq + (long long)z * nx + x] = acc[i];
+  }
+}
+
+__global__ void k_collapse_fin(const c128* __restrict__ part, int G, long long nq,
+                               c128* __restrict__ Q) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * nq;
+       i += (long long)gridDim.x * blockDim.x) {
+    c128 s = part[i];
+    for (int g = 1; g < G; ++g) s = s + part[(long long)g * 3 * nq + i];
+    Q[i] = s;
   }
 }
 
 struct Wave2 { double a[3]; double e[6]; };
+
+constexpr int kCollapseG = 8;   // y groups of the collapse (partials per (x, z))
 
 // per-row-chunk partials of sum Im(E_inc^* . P) and sum w |P|^2.  ptab holds
 // exp(-i kd a_mu r_mu) along x, then y, then z (k_phase_tab for the incidence
@@ -219,16 +236,18 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
   const long long fnocc = collapse ? (long long)g.nx * g.nz : g.n_occ;
   LatticeDev flat = h->lat();
   c128* Qc = nullptr;
+  c128* Qpart = nullptr;
   if (collapse) {
-    const size_t need = (size_t)fnocc * 3 * sizeof(c128) + (size_t)(g.nz + 1) * sizeof(long long) +
-                        (size_t)fnocc * sizeof(uint16_t) + 64;
+    const size_t need = (size_t)fnocc * 3 * sizeof(c128) * (1 + kCollapseG) +
+                        (size_t)(g.nz + 1) * sizeof(long long) + (size_t)fnocc * sizeof(uint16_t) + 64;
     if (h->coll_bytes < need) {
       cudaFree(h->d_coll); h->d_coll = nullptr; h->coll_bytes = 0;
       if (cudaMalloc(&h->d_coll, need) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter collapse buffer"); }
       h->coll_bytes = need;
     }
     Qc = (c128*)h->d_coll;
-    long long* roff = (long long*)(Qc + (size_t)fnocc * 3);
+    Qpart = Qc + (size_t)fnocc * 3;
+    long long* roff = (long long*)(Qpart + (size_t)fnocc * 3 * kCollapseG);
     uint16_t* xis = (uint16_t*)(roff + g.nz + 1);
     std::vector<long long> ro(g.nz + 1);
     std::vector<uint16_t> xv((size_t)fnocc);
@@ -287,7 +306,9 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
       if (collapse) {
         const size_t sm = (size_t)g.nx * 3 * sizeof(c128);
         DDA_CK(h, cudaFuncSetAttribute(k_collapse_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_collapse_y<<<g.nz, 256, sm, st>>>(P, h->lat(), g.n_occ, g.nx, g.ny, Qc, fnocc); count_launch();
+        const int G = std::min(g.ny, kCollapseG);
+        k_collapse_y<<<dim3(g.nz, G), 256, sm, st>>>(P, h->lat(), g.n_occ, g.nx, g.ny, Qpart, fnocc); count_launch();
+        k_collapse_fin<<<(int)std::min<long long>((3 * fnocc + 255) / 256, 2048), 256, 0, st>>>(Qpart, G, fnocc, Qc); count_launch();
         Pf = Qc;
       }
       k_farfield<<<grid, 256, 0, st>>>(Pf, flat, tab, n_dir, fnx, fny, fnz, fnrows, fnocc,
