@@ -182,7 +182,8 @@ template <> Work<df>& dwork<df>(dda_t h) { return h->wdf; }
 // z, and transforms along the other axes keep that: line y > My/2 is sy times
 // line My - y.  So the x pass runs only on rows y <= My/2, z <= Mz/2, the y
 // pass only on planes z <= Mz/2 and reads rows y <= My/2 (mirroring the rest),
-// and the z pass reads planes z <= Mz/2.
+// and the z pass reads planes z <= Mz/2; the y and z passes transform only the
+// lines the octant keeps (kx <= Mx/2, and ky <= My/2 for z).
 template <typename R>
 cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const cpx<R>* table,
                                  const int comp[2], int c, double inv) {
@@ -211,8 +212,10 @@ cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const cpx
   fa.in = grid2; fa.out = grid; fa.tw = twy; fa.nrows = hx; fa.nz = hz; fa.Mx = g.Mx;
   fa.msign = sy;
   if ((e = fast_pass<R>(g.My, FP_SFULL, fa)) != cudaSuccess) return e;
-  fa.in = grid; fa.out = grid2; fa.tw = twz; fa.nrows = hy * g.Mx; fa.nz = 1;
-  fa.Mx = g.My * g.Mx; fa.msign = sz;
+  // z lines (kx, ky), kx <= Mx/2, ky <= My/2 (the octant's): hx adjacent
+  // lines per ky, the ky groups Mx elements apart
+  fa.in = grid; fa.out = grid2; fa.tw = twz; fa.nrows = hx; fa.nz = hy;
+  fa.Mx = g.My * g.Mx; fa.msign = sz; fa.ostride = g.Mx;
   if ((e = fast_pass<R>(g.Mz, FP_SFULL, fa)) != cudaSuccess) return e;
   tr_end(g.tr, st, TR_DB_LINES);
   tr_begin(g.tr, st);

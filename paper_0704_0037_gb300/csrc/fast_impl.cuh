@@ -28,7 +28,8 @@ cudaError_t run_pass(int pass, const FastArgs& a) {
     case FP_XFULL:
       return P::xfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.ny, a.My, tw, a.st);
     case FP_SFULL:
-      return P::sfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.nz, a.Mx, a.msign, tw, a.st);
+      return P::sfull((const cpx<R>*)a.in, (cpx<R>*)a.out, a.nrows, a.nz, a.Mx, a.msign, tw, a.st,
+                      a.ostride);
   }
   return cudaErrorNotSupported;
 }

@@ -60,11 +60,14 @@ __device__ __forceinline__ void load_tw(cpx<R>* s_tw, const cpx<R>* __restrict__
 // B1 [3][nz][ny][Mx] -> B2 [3][nz][M][Mx]; grid (ceil(Mx/T), nz, 3).
 // msign != 0 (D-matrix build, whole lines): only elements y <= M/2 are read;
 // element y > M/2 is msign times element M - y (the line has that parity).
+// ostr != 0: line group blockIdx.y starts at element blockIdx.y * ostr of
+// both arrays (sub-blocks of whole lines, ny == M).
 template <typename R, int M1, int M2, int T>
 __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restrict__ in,
                                                           cpx<R>* __restrict__ out, int ny, int nz,
                                                           int Mx, const cpx<R>* __restrict__ tw,
-                                                          int msign, const int* __restrict__ skip) {
+                                                          int msign, const int* __restrict__ skip,
+                                                          long long ostr) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
   if (skip && skip[blockIdx.z / 3]) return;     // right-hand side already converged
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -72,8 +75,9 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
   cpx<R>* s = s_tw + M;
   const int t = threadIdx.x % T, q = threadIdx.x / T;
   const int kx = blockIdx.x * T + t;
-  const long long ib = ((long long)blockIdx.z * nz + blockIdx.y) * ny * Mx;
-  const long long ob = ((long long)blockIdx.z * nz + blockIdx.y) * M * Mx;
+  const long long og = (long long)blockIdx.z * nz + blockIdx.y;
+  const long long ib = ostr ? og * ostr : og * ny * Mx;
+  const long long ob = ostr ? og * ostr : og * M * Mx;
   load_tw(s_tw, tw, M, NT);
   __syncthreads();
   if (q < M2) {
@@ -720,7 +724,7 @@ struct Passes {
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
     fk_yfwd<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3 * nrhs), NT, sm, st>>>(in, out, ny, nz,
-                                                                                Mx, tw, 0, skip);
+                                                                                Mx, tw, 0, skip, 0);
     count_launch();
     return cudaGetLastError();
   }
@@ -782,13 +786,13 @@ struct Passes {
   // adjacent in memory, n_outer groups M*stride apart (the y pass kernel with
   // every input present); msign != 0 reads only elements <= M/2 and mirrors
   static cudaError_t sfull(const cpx<R>* in, cpx<R>* out, int nlines, int n_outer, int stride,
-                           int msign, const cpx<R>* tw, cudaStream_t st) {
+                           int msign, const cpx<R>* tw, cudaStream_t st, long long ostride) {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
     if (e != cudaSuccess) return e;
     fk_yfwd<R, M1, M2, T><<<dim3((nlines + T - 1) / T, n_outer, 1), NT, sm, st>>>(in, out, M, n_outer,
                                                                                  stride, tw, msign,
-                                                                                 nullptr);
+                                                                                 nullptr, ostride);
     count_launch();
     return cudaGetLastError();
   }

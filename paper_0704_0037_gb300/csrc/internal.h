@@ -233,6 +233,9 @@ struct FastArgs {
   int nrhs = 1;
   int bstride = 0;
   const int* skip = nullptr;
+  // FP_SFULL: element offset between the outer groups of lines (0: M times
+  // the element stride, i.e. whole line sets one after another)
+  long long ostride = 0;
 };
 // number of (re, im) partials FP_XINV writes to dotp for nrows rows
 inline int fast_xinv_blocks(int nrows, bool fp32) { return 3 * ((nrows + (fp32 ? 16 : 8) - 1) / (fp32 ? 16 : 8)); }
