@@ -161,10 +161,10 @@ def kernel_models(n, M, n_occ):
     out["qmr_k1"] = dict(bytes=3 * vec8, flops=0, bound="hbm")
     out["qmr_k2"] = dict(bytes=13 * vec8, flops=0, bound="hbm")
     # D build, register-resident passes with parity mirroring: x lines for
-    # y, z <= M/2, y lines for kx, z <= M/2, z lines for ky <= M/2 (every kx);
+    # y, z <= M/2, y lines for kx, z <= M/2, z lines for kx, ky <= M/2;
     # all three passes per component
     h = M // 2 + 1
-    lines = h * h + h * h + h * M
+    lines = 3 * h * h
     out["dbuild_lines"] = dict(bytes=2 * lines * M * 16, flops=lines * 5 * M * lg, bound="alu")
     return out
 
@@ -181,7 +181,7 @@ def load_peaks():
 # dram__bytes.sum.per_second x duration) from one ncu capture of the kernel
 # as it is now; profiles/fk_zconv_c64_sphere134.md gives the command.  Only
 # valid for the 134^3 sphere on the 270^3 grid; None elsewhere.
-NCU_TRAFFIC_134 = {"p3_zconv_c64": 647.8e6}
+NCU_TRAFFIC_134 = {"p3_zconv_c64": 647.6e6}
 
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe's nominal 1.25 TFLOP/s)
 

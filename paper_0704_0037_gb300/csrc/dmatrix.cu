@@ -85,23 +85,26 @@ __global__ void k_green_table(cpx<R>* __restrict__ table, const cpx<R>* __restri
 // Component (mu, nu) of G on the padded grid from the table: grid index j
 // stands for offset j (j < n) or j - M (j > M - n), zero otherwise; a
 // negative offset along an axis flips the sign iff exactly one of mu, nu is
-// that axis (G_mu,nu is odd along it).  A block per (y, z) row of the grid.
+// that axis (G_mu,nu is odd along it).  A block per (y, z) row of the grid;
+// only rows y < ry, z < rz are written (the rows the first pass reads).
 template <typename T>
 __global__ void k_green_fill(T* __restrict__ grid, const T* __restrict__ table, int mu,
-                             int nu, int nx, int ny, int nz, int Mx, int My, int Mz) {
+                             int nu, int nx, int ny, int nz, int Mx, int My, int Mz, int ry,
+                             int rz) {
   const long long tsz = (long long)nx * ny * nz;
   const int comp = mu == 0 ? nu : (mu == 1 ? 2 + nu : 5);
   const bool oddx = (mu == 0) != (nu == 0), oddy = (mu == 1) != (nu == 1),
              oddz = (mu == 2) != (nu == 2);
-  const int rows = My * Mz;
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int iy = row % My, iz = row / My;
+  const int rows = ry * rz;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int iy = r % ry, iz = r / ry;
+    const long long row = (long long)iz * My + iy;
     const bool uyz = (iy < ny || iy > My - ny) && (iz < nz || iz > Mz - nz);
     const int ay = iy < ny ? iy : My - iy;
     const int az = iz < nz ? iz : Mz - iz;
     const bool flip_yz = ((iy >= ny) && oddy) != ((iz >= nz) && oddz);
     const T* trow = table + comp * tsz + ((long long)az * ny + ay) * nx;
-    T* out = grid + (long long)row * Mx;
+    T* out = grid + row * Mx;
     T zero;
     zero.x = decltype(zero.x)(0.0);
     zero.y = decltype(zero.y)(0.0);
@@ -195,8 +198,9 @@ cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const cpx
   const cpx<R>* twy = twx + g.Mx;
   const cpx<R>* twz = twy + g.My;
   tr_begin(g.tr, st);
-  k_green_fill<cpx<R>><<<rows_grid(g.My * g.Mz), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
-                                                       g.nz, g.Mx, g.My, g.Mz); count_launch();
+  k_green_fill<cpx<R>><<<rows_grid((g.My / 2 + 1) * (g.Mz / 2 + 1)), 256, 0, st>>>(
+      grid, table, comp[0], comp[1], g.nx, g.ny, g.nz, g.Mx, g.My, g.Mz, g.My / 2 + 1, g.Mz / 2 + 1);
+  count_launch();
   tr_end(g.tr, st, TR_DB_GREEN);
   tr_begin(g.tr, st);
   const int hx = g.Mx / 2 + 1, hy = g.My / 2 + 1, hz = g.Mz / 2 + 1;
@@ -242,7 +246,7 @@ cudaError_t build_component_generic(dda_t h, c128* grid, const c128* table, cons
   const c128* twz = twy + g.My;
   tr_begin(g.tr, st);
   k_green_fill<c128><<<rows_grid(g.My * g.Mz), 256, 0, st>>>(grid, table, comp[0], comp[1], g.nx, g.ny,
-                                                     g.nz, g.Mx, g.My, g.Mz); count_launch();
+                                                     g.nz, g.Mx, g.My, g.Mz, g.My, g.Mz); count_launch();
   tr_end(g.tr, st, TR_DB_GREEN);
   tr_begin(g.tr, st);
   // x lines (contiguous) over the whole grid; then only the octant is
