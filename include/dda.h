@@ -398,6 +398,21 @@ int dda_positions(dda_t h, int* ijk_host);      /* [N_occ][3] lattice indices (i
 const char* dda_last_error(dda_t h);            /* never NULL; "" if no error        */
 int dda_free(dda_t h);                          /* releases all handle memory; NULL ok */
 
+/*
+ * dda_release_cached_memory -- returns to the CUDA driver the device memory
+ * the library keeps for reuse.  Device buffers a handle frees (at dda_free,
+ * or when a buffer grows) go to a per-process cache keyed by device and size,
+ * so that the next handle of a lattice of the same size allocates without
+ * cudaMalloc or a device-synchronising cudaFree; each cached block carries an
+ * event of the stream that last used it and is reused only after that event.
+ * At most 4 GiB stay cached; the cache of a device is also emptied when a
+ * cudaMalloc of the library runs out of memory.  Call this to hand the memory
+ * back to other users of the GPU (e.g. PyTorch's allocator).  Thread-safe;
+ * blocks whose stream work is still pending are waited for before release.
+ * Memory held by live handles is not affected.  Returns DDA_OK.
+ */
+int dda_release_cached_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

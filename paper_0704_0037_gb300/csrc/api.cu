@@ -37,26 +37,27 @@ std::vector<cpx<R>> twiddles(const Geom& g) {
 }
 
 template <typename R>
-int ensure_work(dda_t h, Work<R>& w) {
+int ensure_work(dda_t h, Work<R>& w, bool buffers = true) {
   const Geom& g = h->g;
   if (!w.tw) {
     std::vector<cpx<R>> t = twiddles<R>(g);
-    if (cudaMalloc(&w.tw, t.size() * sizeof(cpx<R>)) != cudaSuccess) {
+    if (dev_malloc(&w.tw, t.size() * sizeof(cpx<R>)) != cudaSuccess) {
       w.tw = nullptr;
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, "cannot allocate twiddle tables");
     }
     DDA_CK(h, cudaMemcpy(w.tw, t.data(), t.size() * sizeof(cpx<R>), cudaMemcpyHostToDevice));
   }
+  if (!buffers) return DDA_OK;
   if (!w.B1) {
-    if (cudaMalloc(&w.B1, g.b1() * sizeof(cpx<R>)) != cudaSuccess) {
+    if (dev_malloc(&w.B1, g.b1() * sizeof(cpx<R>)) != cudaSuccess) {
       w.B1 = nullptr;
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, "cannot allocate FFT work buffer B1");
     }
   }
   if (!w.B2) {
-    if (cudaMalloc(&w.B2, g.b2() * sizeof(cpx<R>)) != cudaSuccess) {
+    if (dev_malloc(&w.B2, g.b2() * sizeof(cpx<R>)) != cudaSuccess) {
       w.B2 = nullptr;
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, "cannot allocate FFT work buffer B2");
@@ -68,8 +69,8 @@ int ensure_work(dda_t h, Work<R>& w) {
 
 
 template <typename R>
-void free_work(Work<R>& w) {
-  cudaFree(w.B1); cudaFree(w.B2); cudaFree(w.tw); cudaFree(w.D); cudaFree(w.beta);
+void free_work(Work<R>& w, cudaStream_t st) {
+  dev_free(w.B1, st); dev_free(w.B2, st); dev_free(w.tw, st); dev_free(w.D, st); dev_free(w.beta, st);
   w = Work<R>();
 }
 
@@ -161,14 +162,14 @@ int ensure_work_cap(dda_t h, Work<R>& w, int want) {
   if (target <= w.cap) return DDA_OK;
   cpx<R>* b1 = nullptr;
   cpx<R>* b2 = nullptr;
-  if (cudaMalloc(&b1, (size_t)target * g.b1() * sizeof(cpx<R>)) != cudaSuccess ||
-      cudaMalloc(&b2, (size_t)target * g.b2() * sizeof(cpx<R>)) != cudaSuccess) {
+  if (dev_malloc(&b1, (size_t)target * g.b1() * sizeof(cpx<R>)) != cudaSuccess ||
+      dev_malloc(&b2, (size_t)target * g.b2() * sizeof(cpx<R>)) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(b1);
+    dev_free(b1, h->stream);
     return DDA_OK;            // keep the current capacity: the product runs in more chunks
   }
-  cudaFree(w.B1);
-  cudaFree(w.B2);
+  dev_free(w.B1, h->stream);
+  dev_free(w.B2, h->stream);
   w.B1 = b1;
   w.B2 = b2;
   w.cap = target;
@@ -188,17 +189,17 @@ int dda_beta_internal(dda_t h, int presc, int nrhs, const double* prop, const do
     return dda_fail(h, DDA_ERR_ARG, "non-finite propagation or polarisation vector");
   const int nb = nrhs * h->n_mat * 3;
   if (h->beta_cap < nrhs) {
-    cudaFree(h->w64.beta); cudaFree(h->w32.beta);
+    dev_free(h->w64.beta, h->stream); dev_free(h->w32.beta, h->stream);
     h->w64.beta = nullptr; h->w32.beta = nullptr; h->beta_cap = 0; h->beta_nrhs = 0;
-    if (cudaMalloc(&h->w64.beta, nb * sizeof(c128)) != cudaSuccess ||
-        cudaMalloc(&h->w32.beta, nb * sizeof(c64)) != cudaSuccess) {
+    if (dev_malloc(&h->w64.beta, nb * sizeof(c128)) != cudaSuccess ||
+        dev_malloc(&h->w32.beta, nb * sizeof(c64)) != cudaSuccess) {
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, "cannot allocate beta tables");
     }
   }
   double* dbuf = nullptr;
   const size_t nd = 2 * h->n_mat + 3 * nrhs + 6 * nrhs;
-  DDA_CK(h, cudaMalloc(&dbuf, nd * sizeof(double)));
+  DDA_CK(h, dev_malloc(&dbuf, nd * sizeof(double)));
   std::vector<double> hb(nd);
   std::memcpy(hb.data(), h->m.data(), 2 * h->n_mat * sizeof(double));
   std::memcpy(hb.data() + 2 * h->n_mat, prop, 3 * nrhs * sizeof(double));
@@ -211,12 +212,42 @@ int dda_beta_internal(dda_t h, int presc, int nrhs, const double* prop, const do
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(dbuf);
+  dev_free(dbuf, h->stream);
   if (e != cudaSuccess) return dda_cuda_fail(h, e, "beta build");
   if (nrhs > h->beta_cap) h->beta_cap = nrhs;
   h->beta_nrhs = nrhs;
   h->beta_presc = presc;
   return DDA_OK;
+}
+
+// DDA_SYM_* flags of the lattice, examined on first use from the host copy
+// of the occupied cells: the rotation by +90 degrees about z maps cell
+// (x = i, y = j) to (x = n - 1 - j, y = i); the lattice is invariant when nx
+// == ny and every occupied cell maps to an occupied cell of the same
+// material (the map is a bijection of the box, so that suffices).
+static int lattice_symmetry(dda_t h) {
+  if (h->sym_flags >= 0) return h->sym_flags;
+  const Geom& g = h->g;
+  int flags = 0;
+  if (g.nx == g.ny) {
+    const int n = g.nx;
+    std::vector<uint8_t> cell((size_t)n * n * g.nz, 0);   // material + 1
+    for (int r = 0; r < g.nrows; ++r)
+      for (long long k = h->row_off_h[r]; k < h->row_off_h[r + 1]; ++k)
+        cell[(size_t)r * n + h->xi_h[k]] = (uint8_t)(h->mat_h[k] + 1);
+    bool sym = true;
+    for (int r = 0; r < g.nrows && sym; ++r) {
+      const int j = r % n, iz = r / n;
+      for (long long k = h->row_off_h[r]; k < h->row_off_h[r + 1]; ++k) {
+        const int i = h->xi_h[k];
+        const size_t rot = ((size_t)iz * n + i) * n + (n - 1 - j);
+        if (cell[rot] != h->mat_h[k] + 1) { sym = false; break; }
+      }
+    }
+    if (sym) flags |= DDA_SYM_ROT90_Z;
+  }
+  h->sym_flags = flags;
+  return flags;
 }
 
 // ---------------------------------------------------------------- C-ABI
@@ -242,31 +273,33 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   g.nx = nx; g.ny = ny; g.nz = nz;
   g.nrows = ny * nz;
   h->row_off_h.assign((size_t)g.nrows + 1, 0);
-  std::vector<uint8_t> mat;
-  for (int r = 0; r < g.nrows; ++r) {
-    const uint8_t* row = occ + (size_t)r * nx;
-    for (int ix = 0; ix < nx; ++ix) {
-      if (row[ix]) {
-        if (row[ix] > n_mat) { delete h; return DDA_ERR_ARG; }
-        h->xi_h.push_back((uint16_t)ix);
-        mat.push_back((uint8_t)(row[ix] - 1));
+  // count first, then fill: one pass each, no reallocation
+  const size_t cells = (size_t)g.nrows * nx;
+  size_t cnt = 0;
+  uint8_t mx = 0;
+  for (size_t i = 0; i < cells; ++i) {
+    cnt += occ[i] != 0;
+    mx = occ[i] > mx ? occ[i] : mx;
+  }
+  if (cnt == 0 || mx > n_mat) { delete h; return DDA_ERR_ARG; }
+  h->xi_h.resize(cnt);
+  h->mat_h.resize(cnt);
+  {
+    size_t k = 0;
+    for (int r = 0; r < g.nrows; ++r) {
+      const uint8_t* row = occ + (size_t)r * nx;
+      for (int ix = 0; ix < nx; ++ix) {
+        if (row[ix]) {
+          h->xi_h[k] = (uint16_t)ix;
+          h->mat_h[k] = (uint8_t)(row[ix] - 1);
+          ++k;
+        }
       }
+      h->row_off_h[r + 1] = (long long)k;
     }
-    h->row_off_h[r + 1] = (long long)h->xi_h.size();
   }
-  g.n_occ = (long long)h->xi_h.size();
-  if (g.n_occ == 0) { delete h; return DDA_ERR_ARG; }
-  // rotation by +90 degrees about z maps cell (x=i, y=j) to (x=n-1-j, y=i)
-  if (nx == ny) {
-    bool sym = true;
-    for (int iz = 0; iz < nz && sym; ++iz) {
-      const uint8_t* pl = occ + (size_t)iz * nx * ny;
-      for (int j = 0; j < ny && sym; ++j)
-        for (int i = 0; i < nx; ++i)
-          if (pl[(size_t)i * nx + (nx - 1 - j)] != pl[(size_t)j * nx + i]) { sym = false; break; }
-    }
-    if (sym) h->sym_flags |= DDA_SYM_ROT90_Z;
-  }
+  g.n_occ = (long long)cnt;
+  const std::vector<uint8_t>& mat = h->mat_h;
   g.Mx = smooth_size(2 * nx - 1);
   g.My = smooth_size(2 * ny - 1);
   g.Mz = smooth_size(2 * nz - 1);
@@ -280,9 +313,9 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   h->kd = volume_corrected ? kd * std::cbrt(4.0 * M_PI / (3.0 * (double)g.n_occ)) : kd;
   h->stream = (cudaStream_t)cuda_stream;
   int rc = DDA_OK;
-  if (cudaMalloc(&h->d_row_off, h->row_off_h.size() * sizeof(long long)) != cudaSuccess ||
-      cudaMalloc(&h->d_xi, h->xi_h.size() * sizeof(uint16_t)) != cudaSuccess ||
-      cudaMalloc(&h->d_mat, mat.size()) != cudaSuccess) {
+  if (dev_malloc(&h->d_row_off, h->row_off_h.size() * sizeof(long long)) != cudaSuccess ||
+      dev_malloc(&h->d_xi, h->xi_h.size() * sizeof(uint16_t)) != cudaSuccess ||
+      dev_malloc(&h->d_mat, mat.size()) != cudaSuccess) {
     cudaGetLastError();
     rc = DDA_ERR_OOM;
   } else if (cudaMemcpy(h->d_row_off, h->row_off_h.data(), h->row_off_h.size() * sizeof(long long),
@@ -303,14 +336,18 @@ extern "C" int dda_build_Dmatrix(dda_t h, int prec) {
   if (prec != DDA_FP64 && prec != DDA_FP32_REFINED) return dda_fail(h, DDA_ERR_ARG, "unknown precision");
   if (h->g.px.nst < 0 || h->g.py.nst < 0 || h->g.pz.nst < 0)
     return dda_fail(h, DDA_ERR_ARG, "padded grid is not 7-smooth");
-  int rc = ensure_work<double>(h, h->w64);
+  // double-float tables when every axis has register-resident passes; the
+  // FP32-refined form then needs no complex128 product buffers (they are
+  // made on the first FP64 product)
+  const Geom& g = h->g;
+  const bool dfok = prec == DDA_FP32_REFINED && g.engine == 0 && fast_supported(g.Mx) &&
+                    fast_supported(g.My) && fast_supported(g.Mz);
+  int rc = ensure_work<double>(h, h->w64, !dfok);
   if (rc != DDA_OK) return rc;
   if (prec == DDA_FP32_REFINED) {
     rc = ensure_work<float>(h, h->w32);
     if (rc != DDA_OK) return rc;
-    // double-float tables when every axis has register-resident passes
-    const Geom& g = h->g;
-    if (g.engine == 0 && fast_supported(g.Mx) && fast_supported(g.My) && fast_supported(g.Mz)) {
+    if (dfok) {
       rc = ensure_work<df>(h, h->wdf);
       if (rc != DDA_OK) return rc;
     }
@@ -499,14 +536,14 @@ extern "C" int dda_asymmetry(int n_dir, const double* dirs, const double* w, con
 
 extern "C" int dda_symmetry(dda_t h, int* flags) {
   if (!h || !flags) return DDA_ERR_ARG;
-  *flags = h->sym_flags;
+  *flags = lattice_symmetry(h);
   return DDA_OK;
 }
 
 extern "C" int dda_mueller_plane_sym(dda_t h, int presc, const void* P_dev, int n_theta,
                                      const double* th, double* M, double* F_out) {
   if (!h) return DDA_ERR_ARG;
-  if (!(h->sym_flags & DDA_SYM_ROT90_Z))
+  if (!(lattice_symmetry(h) & DDA_SYM_ROT90_Z))
     return dda_fail(h, DDA_ERR_ARG, "lattice is not invariant under the 90 degree rotation about z");
   if (n_theta < 1 || !th || !M || !P_dev) return dda_fail(h, DDA_ERR_ARG, "bad arguments");
   std::vector<double> dirs((size_t)6 * n_theta), F((size_t)12 * n_theta);
@@ -583,14 +620,14 @@ extern "C" int dda_free(dda_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   tr_destroy(&h->tracer);
-  free_work(h->w64);
-  free_work(h->w32);
-  free_work(h->wdf);
-  cudaFree(h->d_row_off); cudaFree(h->d_xi); cudaFree(h->d_mat);
-  cudaFree(h->sv); cudaFree(h->d_part); cudaFree(h->d_mvpart); cudaFree(h->d_scal); cudaFreeHost(h->h_scal);
+  free_work(h->w64, h->stream);
+  free_work(h->w32, h->stream);
+  free_work(h->wdf, h->stream);
+  dev_free(h->d_row_off, h->stream); dev_free(h->d_xi, h->stream); dev_free(h->d_mat, h->stream);
+  dev_free(h->sv, h->stream); dev_free(h->d_part, h->stream); dev_free(h->d_mvpart, h->stream); dev_free(h->d_scal, h->stream); cudaFreeHost(h->h_scal);
   batch_free(h);
-  cudaFree(h->d_tab); cudaFree(h->d_fpart); cudaFree(h->d_coll); cudaFree(h->d_dscratch);
-  cudaFree(h->d_ptab);
+  dev_free(h->d_tab, h->stream); dev_free(h->d_fpart, h->stream); dev_free(h->d_coll, h->stream); dev_free(h->d_dscratch, h->stream);
+  dev_free(h->d_ptab, h->stream);
   cudaGetLastError();
   delete h;
   return DDA_OK;

@@ -292,7 +292,7 @@ int dda_build_D_internal(dda_t h, bool want32) {
   const bool use_df = want32 && fast && h->wdf.tw != nullptr;
   auto alloc = [&](void** p, size_t bytes, const char* what) -> int {
     if (*p) return DDA_OK;
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    if (dev_malloc(p, bytes) != cudaSuccess) {
       *p = nullptr;
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, what);
@@ -320,10 +320,10 @@ int dda_build_D_internal(dda_t h, bool want32) {
   if (h->d_dscratch && h->dscratch_bytes >= need) {
     scratch = h->d_dscratch;
   } else {
-    cudaFree(h->d_dscratch);
+    dev_free(h->d_dscratch, h->stream);
     h->d_dscratch = nullptr;
     h->dscratch_bytes = 0;
-    if (cudaMalloc(&scratch, need) != cudaSuccess) {
+    if (dev_malloc(&scratch, need) != cudaSuccess) {
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, "cannot allocate the Green's tensor grid");
     }
@@ -337,7 +337,7 @@ int dda_build_D_internal(dda_t h, bool want32) {
   void* ab = (char*)table + table_b;
   void* grid2 = fast ? (char*)ab + ab_b : nullptr;
   auto release = [&]() {
-    if (scratch != h->d_dscratch) cudaFree(scratch);
+    if (scratch != h->d_dscratch) dev_free(scratch, h->stream);
   };
   tr_begin(g.tr, st);
   const int rgrid = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, 152LL * 8));
@@ -381,7 +381,7 @@ int dda_build_D_internal(dda_t h, bool want32) {
 int ensure_d64(dda_t h) {
   if (!h->d64_from_df) return DDA_OK;
   const long long n = 6 * h->g.oct();
-  if (!h->w64.D && cudaMalloc(&h->w64.D, n * sizeof(c128)) != cudaSuccess) {
+  if (!h->w64.D && dev_malloc(&h->w64.D, n * sizeof(c128)) != cudaSuccess) {
     h->w64.D = nullptr;
     cudaGetLastError();
     return dda_fail(h, DDA_ERR_OOM, "cannot allocate the FP64 D-matrix octant");

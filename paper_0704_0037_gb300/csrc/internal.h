@@ -73,6 +73,16 @@ struct Work {
   int cap_beta = 0;         // entries of beta (double-float tables only)
 };
 
+// Device memory of the library (devmem.cu): blocks come from a cache of
+// freed blocks of (nearly) the same size when one is free, else cudaMalloc;
+// dev_free puts a block back with an event recorded on st (the stream that
+// last used it).
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+cudaError_t dev_free(void* p, cudaStream_t st);
+template <typename T> inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+
 // Grow the product buffers of w to hold min(want, what fits) right-hand
 // sides (api.cu); at least one.
 template <typename R> int ensure_work_cap(dda_t h, Work<R>& w, int want);
@@ -113,7 +123,7 @@ int smooth_size(int lo);
 
 // The handle.
 struct dda_ctx {
-  int sym_flags = 0;        // DDA_SYM_* found at init
+  int sym_flags = -1;       // DDA_SYM_* of the lattice (-1: not yet examined)
   int device = 0;           // CUDA device current at dda_init_lattice
   bool d64_from_df = false; // w64.D not yet derived from the double-float octant
   dda::Geom g{};
@@ -123,6 +133,7 @@ struct dda_ctx {
   cudaStream_t stream = nullptr;
   std::vector<long long> row_off_h;
   std::vector<uint16_t> xi_h;
+  std::vector<uint8_t> mat_h;     // material index of each occupied dipole
   long long* d_row_off = nullptr;
   uint16_t* d_xi = nullptr;
   uint8_t* d_mat = nullptr;

@@ -287,7 +287,7 @@ __global__ void k_rhs(cpx<R>* __restrict__ b, LatticeDev lat, const c128* __rest
 int launch_rhs(dda_t h, c128* b, const c128* beta, const Wave& wv, cudaStream_t st) {
   const Geom& g = h->g;
   if (!h->d_ptab) {
-    if (cudaMalloc(&h->d_ptab, (size_t)(g.nx + g.ny + g.nz) * sizeof(c128)) != cudaSuccess) {
+    if (dev_malloc(&h->d_ptab, (size_t)(g.nx + g.ny + g.nz) * sizeof(c128)) != cudaSuccess) {
       h->d_ptab = nullptr;
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, "incident phase table");
@@ -1012,17 +1012,17 @@ int run_solver(Run& ru, int solver, const cpx<R>* b, cpx<R>* x, cpx<R>** vec, do
 
 int ensure_solver_mem(dda_t h, size_t bytes) {
   if (!h->d_part) {
-    if (cudaMalloc(&h->d_part, kSlots * kNB * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver partials"); }
-    if (cudaMalloc(&h->d_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver scalars"); }
+    if (dev_malloc(&h->d_part, kSlots * kNB * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver partials"); }
+    if (dev_malloc(&h->d_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver scalars"); }
     const size_t mvp = 2 * (size_t)fast_xinv_blocks(h->g.nrows, false);
-    if (cudaMalloc(&h->d_mvpart, mvp * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "product partials"); }
+    if (dev_malloc(&h->d_mvpart, mvp * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "product partials"); }
     if (cudaMallocHost(&h->h_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "pinned scalars"); }
   }
   if (h->sv_bytes < bytes) {
-    cudaFree(h->sv);
+    dev_free(h->sv, h->stream);
     h->sv = nullptr;
     h->sv_bytes = 0;
-    if (cudaMalloc(&h->sv, bytes) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver vectors"); }
+    if (dev_malloc(&h->sv, bytes) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver vectors"); }
     h->sv_bytes = bytes;
   }
   return DDA_OK;
@@ -1043,8 +1043,9 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
                        dda_solve_info* info) {
   int rc = dda_beta_internal(h, o->pol, nrhs, prop, pol);
   if (rc != DDA_OK) return rc;
-  if (o->prec == DDA_FP64 || !h->wdf.have_D) {
+  if (o->prec == DDA_FP64 || !h->wdf.have_D) {   // FP64 products
     rc = ensure_d64(h);
+    if (rc == DDA_OK) rc = ensure_work_cap<double>(h, h->w64, 1);
     if (rc != DDA_OK) return rc;
   }
   const long long n = 3 * h->g.n_occ;
@@ -1294,11 +1295,11 @@ struct BatchMem {
   size_t sv2_bytes = 0;
 };
 
-void bm_release(BatchMem* m) {
-  cudaFree(m->ds); cudaFreeHost(m->hs); cudaFree(m->part); cudaFree(m->mvpart); cudaFree(m->mask);
-  cudaFree(m->off); cudaFree(m->dvals); cudaFreeHost(m->h_off); cudaFreeHost(m->h_vals);
-  cudaFree(m->sv);
-  cudaFree(m->sv2);
+void bm_release(BatchMem* m, cudaStream_t st) {
+  dev_free(m->ds, st); cudaFreeHost(m->hs); dev_free(m->part, st); dev_free(m->mvpart, st); dev_free(m->mask, st);
+  dev_free(m->off, st); dev_free(m->dvals, st); cudaFreeHost(m->h_off); cudaFreeHost(m->h_vals);
+  dev_free(m->sv, st);
+  dev_free(m->sv2, st);
   *m = BatchMem();
 }
 
@@ -1315,28 +1316,28 @@ int bm_ensure(dda_t h, int nrhs, size_t sv_bytes) {
     fresh.sv2 = m->sv2; fresh.sv2_bytes = m->sv2_bytes;
     m->sv = nullptr; m->sv_bytes = 0;
     m->sv2 = nullptr; m->sv2_bytes = 0;
-    bm_release(m);
+    bm_release(m, h->stream);
     *m = fresh;
     const size_t mvp = 2 * (size_t)fast_xinv_blocks(h->g.nrows, false) * nrhs;
-    if (cudaMalloc(&m->ds, nrhs * sizeof(Scal)) != cudaSuccess ||
+    if (dev_malloc(&m->ds, nrhs * sizeof(Scal)) != cudaSuccess ||
         cudaMallocHost(&m->hs, nrhs * sizeof(Scal)) != cudaSuccess ||
-        cudaMalloc(&m->part, (size_t)nrhs * kPS * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&m->mvpart, mvp * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&m->mask, nrhs * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&m->off, nrhs * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&m->dvals, 2 * nrhs * sizeof(double)) != cudaSuccess ||
+        dev_malloc(&m->part, (size_t)nrhs * kPS * sizeof(double)) != cudaSuccess ||
+        dev_malloc(&m->mvpart, mvp * sizeof(double)) != cudaSuccess ||
+        dev_malloc(&m->mask, nrhs * sizeof(int)) != cudaSuccess ||
+        dev_malloc(&m->off, nrhs * sizeof(int)) != cudaSuccess ||
+        dev_malloc(&m->dvals, 2 * nrhs * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&m->h_off, nrhs * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&m->h_vals, 2 * nrhs * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
-      bm_release(m);
+      bm_release(m, h->stream);
       return dda_fail(h, DDA_ERR_OOM, "batched solver state");
     }
     m->cap = nrhs;
   }
   if (m->sv_bytes < sv_bytes) {
-    cudaFree(m->sv);
+    dev_free(m->sv, h->stream);
     m->sv = nullptr; m->sv_bytes = 0;
-    if (cudaMalloc(&m->sv, sv_bytes) != cudaSuccess) {
+    if (dev_malloc(&m->sv, sv_bytes) != cudaSuccess) {
       cudaGetLastError();
       return dda_fail(h, DDA_ERR_OOM, "batched solver vectors");
     }
@@ -1459,7 +1460,7 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
 void batch_free(dda_t h) {
   if (h && h->bm) {
     BatchMem* m = (BatchMem*)h->bm;
-    bm_release(m);
+    bm_release(m, h->stream);
     delete m;
     h->bm = nullptr;
   }
@@ -1483,8 +1484,10 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
                                : (size_t)nrhs * n * (nvec + 2) * sizeof(c128);
   rc = bm_ensure(h, nrhs, bytes);
   if (rc != DDA_OK) return rc;
-  rc = ensure_work_cap<double>(h, h->w64, nrhs);
-  if (rc != DDA_OK) return rc;
+  if (!refined || !h->wdf.have_D) {                // FP64 products
+    rc = ensure_work_cap<double>(h, h->w64, nrhs);
+    if (rc != DDA_OK) return rc;
+  }
   if (refined) {
     rc = ensure_work_cap<float>(h, h->w32, nrhs);
     if (rc != DDA_OK) return rc;
@@ -1653,9 +1656,9 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
         // FP64-class products
         const size_t need = (size_t)nrhs * n * (nvec + 2) * sizeof(c128);
         if (m->sv2_bytes < need) {
-          cudaFree(m->sv2);
+          dev_free(m->sv2, h->stream);
           m->sv2 = nullptr; m->sv2_bytes = 0;
-          if (cudaMalloc(&m->sv2, need) != cudaSuccess) {
+          if (dev_malloc(&m->sv2, need) != cudaSuccess) {
             cudaGetLastError();
             return dda_fail(h, DDA_ERR_OOM, "mixed inner-solve vectors");
           }

@@ -421,10 +421,10 @@ cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, 
   const int bstride = n_mat * 3;
   // beta as double-float, grown with the number of right-hand sides
   if (w.cap_beta < nrhs * bstride) {
-    cudaFree(w.beta);
+    dev_free(w.beta, st);
     w.beta = nullptr;
     w.cap_beta = 0;
-    cudaError_t e = cudaMalloc(&w.beta, (size_t)nrhs * bstride * sizeof(cdf));
+    cudaError_t e = dev_malloc(&w.beta, (size_t)nrhs * bstride * sizeof(cdf));
     if (e != cudaSuccess) return e;
     w.cap_beta = nrhs * bstride;
   }

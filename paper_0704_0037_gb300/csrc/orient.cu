@@ -83,7 +83,7 @@ extern "C" int dda_orientation_average(dda_t h, const dda_solve_opts* o, int n_a
     return dda_fail(h, DDA_ERR_STATE, "D-matrix not built");
   const long long n = 3 * h->g.n_occ;
   void* P = nullptr;
-  if (cudaMalloc(&P, 2 * (size_t)n * sizeof(c128)) != cudaSuccess) {
+  if (dev_malloc(&P, 2 * (size_t)n * sizeof(c128)) != cudaSuccess) {
     cudaGetLastError();
     return dda_fail(h, DDA_ERR_OOM, "orientation-averaging polarisations");
   }
@@ -164,7 +164,7 @@ extern "C" int dda_orientation_average(dda_t h, const dda_solve_opts* o, int n_a
       }
     }
   }
-  cudaFree(P);
+  dev_free(P, h->stream);
   if (rc < 0) return rc;
   q_avg[0] = qe;
   q_avg[1] = qa;

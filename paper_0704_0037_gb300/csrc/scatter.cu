@@ -241,8 +241,8 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
     const size_t need = (size_t)fnocc * 3 * sizeof(c128) * (1 + kCollapseG) +
                         (size_t)(g.nz + 1) * sizeof(long long) + (size_t)fnocc * sizeof(uint16_t) + 64;
     if (h->coll_bytes < need) {
-      cudaFree(h->d_coll); h->d_coll = nullptr; h->coll_bytes = 0;
-      if (cudaMalloc(&h->d_coll, need) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter collapse buffer"); }
+      dev_free(h->d_coll, h->stream); h->d_coll = nullptr; h->coll_bytes = 0;
+      if (dev_malloc(&h->d_coll, need) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter collapse buffer"); }
       h->coll_bytes = need;
     }
     Qc = (c128*)h->d_coll;
@@ -274,13 +274,13 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
   const size_t fp_b = std::max((size_t)n_chunks * std::max(n_dir, 1) * 6, (size_t)2 * qblocks) * sizeof(double) +
                       (size_t)std::max(n_dir, 1) * 6 * sizeof(double);
   if (h->tab_bytes < tab_b) {
-    cudaFree(h->d_tab); h->d_tab = nullptr; h->tab_bytes = 0;
-    if (cudaMalloc(&h->d_tab, tab_b) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter tables"); }
+    dev_free(h->d_tab, h->stream); h->d_tab = nullptr; h->tab_bytes = 0;
+    if (dev_malloc(&h->d_tab, tab_b) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter tables"); }
     h->tab_bytes = tab_b;
   }
   if (h->fpart_bytes < fp_b) {
-    cudaFree(h->d_fpart); h->d_fpart = nullptr; h->fpart_bytes = 0;
-    if (cudaMalloc(&h->d_fpart, fp_b) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter partials"); }
+    dev_free(h->d_fpart, h->stream); h->d_fpart = nullptr; h->fpart_bytes = 0;
+    if (dev_malloc(&h->d_fpart, fp_b) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "scatter partials"); }
     h->fpart_bytes = fp_b;
   }
   c128* tab = (c128*)h->d_tab;

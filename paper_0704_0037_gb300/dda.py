@@ -38,7 +38,7 @@ EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec"
            "dda_orientation_average",
            "dda_farfield_noalloc", "dda_trace",
            "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
-           "dda_free")
+           "dda_free", "dda_release_cached_memory")
 
 
 class DDAError(RuntimeError):
@@ -104,6 +104,7 @@ def lib():
                                      _dp, ctypes.POINTER(SolveInfo)], _ip),
         "dda_farfield_noalloc": ([_vp, _vp, _ip, _vp, _vp], _ip),
         "dda_trace": ([_vp, _ip], _ip),
+        "dda_release_cached_memory": ([], _ip),
         "dda_trace_read": ([_vp, _ip, ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_longlong),
                             ctypes.POINTER(ctypes.c_int)], _ip),
         "dda_n_occ": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
@@ -375,6 +376,11 @@ def dda_farfield_noalloc(h, P, dirs, F):
     return _check(h, lib().dda_farfield_noalloc(h, _dev_ptr(P, torch.complex128), n_dir,
                                                 _dev_ptr(dirs, torch.float64),
                                                 _dev_ptr(F, torch.complex128)))
+
+
+def dda_release_cached_memory():
+    """Return the device memory the library keeps for reuse to the driver."""
+    return lib().dda_release_cached_memory()
 
 
 def dda_trace(h, enable=True):
