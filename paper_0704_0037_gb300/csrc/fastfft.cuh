@@ -233,7 +233,6 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict
       cp_async_commit();
     }
   }
-  (void)col;
   {
     // Warm L2 with the octant entries of the Fourier-space product (fy of
     // this block, its range of fx, every fz and component): they arrive from
