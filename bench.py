@@ -187,6 +187,28 @@ NCU_TRAFFIC_134 = {"p3_zconv_c64": 647.6e6}
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe's nominal 1.25 TFLOP/s)
 
 
+# ---------------------------------------------------------------- ranks
+def reduce_over_ranks(t, counts, device):
+    """Whole-job figures of one timed region over the ranks of the default
+    process group: the slowest rank's time t and the sum of each count.
+    Without a group of more than one rank, the values unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() < 2:
+        return t, list(counts)
+    tt = torch.tensor([float(t)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cc = torch.tensor([float(c) for c in counts], device=device, dtype=torch.float64)
+    dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+    return float(tt.item()), [int(round(v)) for v in cc.tolist()]
+
+
+def deal(items, rank, world):
+    """The items rank `rank` of `world` works on: every world-th one, so the
+    ranks share the work with no exchange (independent particles)."""
+    return items[rank::world]
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -254,15 +276,7 @@ def run_ours(args, rank, world, local_rank):
     trace = dda.dda_trace_read(p.h)
     dda.dda_trace(p.h, False)
     clk = clocks.stop() if rank == 0 else None
-    t_max = ms
-    mv_all = mv
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-        mm = torch.tensor([mv], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(mm, op=torch.distributed.ReduceOp.SUM)
-        mv_all = int(mm.item())
+    t_max, (mv_all,) = reduce_over_ranks(ms, [mv], dev)
     value = mv_all / (t_max / 1e3)
 
     if args.steps_only:     # warm-up and timed steps only (for launch-list profiling)
@@ -402,13 +416,7 @@ def run_e2e(args, occ, opts, prop, pol, dirs, world, dev):
         p.close()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        dt = float(tt.item())
-        mm = torch.tensor([mv], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(mm, op=torch.distributed.ReduceOp.SUM)
-        mv = int(mm.item())
+    dt, (mv,) = reduce_over_ranks(dt, [mv], dev)
     return {"value": mv / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "steps": steps, "s_per_step": dt / steps}
 
@@ -491,7 +499,7 @@ def run_batch(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     inst = inputs.batch_instances(args.batch_count)
-    mine = inst[rank::world]
+    mine = deal(inst, rank, world)
     opts = dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_CLDR, prec=dda.DDA_FP32_REFINED, tol=TOL,
                 maxiter=args.batch_maxiter, inner_tol=INNER_TOL)
     # The batch measures complex64 throughput with a budget of batch_maxiter
@@ -531,12 +539,7 @@ def run_batch(args, rank, world, local_rank):
     for p in parts:
         p.close()
     del Ps
-    if world > 1:
-        tt = torch.tensor([dt, mv, rhs_ok, rhs_all], device="cuda", dtype=torch.float64)
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.SUM)
-        dt, mv, rhs_ok, rhs_all = float(mx[0]), int(tt[1]), int(tt[2]), int(tt[3])
+    dt, (mv, rhs_ok, rhs_all) = reduce_over_ranks(dt, [mv, rhs_ok, rhs_all], "cuda")
     if rank != 0:
         return None
     return {"metric": "aggregate products/s, seeded 128-particle batch (16 RHS each) to 1e-5",
