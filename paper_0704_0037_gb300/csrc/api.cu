@@ -5,8 +5,11 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <thread>
+#include <utility>
 
 #include "internal.h"
 
@@ -26,15 +29,32 @@ int dda_cuda_fail(dda_t h, cudaError_t e, const char* where) {
 namespace {
 
 // exp(-2 pi i m / M) for m < M, in long double, for the three axes.
+// cos and sin of 2 pi m / M, m < M, in long double, computed once per M in
+// the process (long double is software-emulated on some hosts, and every new
+// handle needs the tables of its three padded lengths)
+static const std::vector<std::pair<long double, long double>>& unit_roots(int M) {
+  static std::mutex mu;
+  static std::map<int, std::vector<std::pair<long double, long double>>> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(M);
+  if (it != cache.end()) return it->second;
+  std::vector<std::pair<long double, long double>>& v = cache[M];
+  const long double twopi = 6.283185307179586476925286766559L;
+  v.resize(M);
+  for (int m = 0; m < M; ++m) {
+    const long double a = twopi * (long double)m / (long double)M;
+    v[m] = std::make_pair(cosl(a), sinl(a));
+  }
+  return v;
+}
+
 template <typename R>
 std::vector<cpx<R>> twiddles(const Geom& g) {
   std::vector<cpx<R>> t;
-  const long double twopi = 6.283185307179586476925286766559L;
-  for (int M : {g.Mx, g.My, g.Mz})
-    for (int m = 0; m < M; ++m) {
-      long double a = twopi * (long double)m / (long double)M;
-      t.push_back(mk<R>((R)cosl(a), (R)(-sinl(a))));
-    }
+  for (int M : {g.Mx, g.My, g.Mz}) {
+    const std::vector<std::pair<long double, long double>>& u = unit_roots(M);
+    for (int m = 0; m < M; ++m) t.push_back(mk<R>((R)u[m].first, (R)(-u[m].second)));
+  }
   return t;
 }
 
