@@ -287,7 +287,8 @@ int dda_asymmetry(int n_dir, const double* dirs_host, const double* weights_host
                   const double* F_host, const double* prop_host, double* g_out_host);
 
 /*
- * dda_symmetry -- symmetries of the lattice found at dda_init_lattice.
+ * dda_symmetry -- symmetries of the lattice (examined from the host copy of
+ * the occupied cells on the first call, then remembered by the handle).
  *   flags_out : bit 0 (DDA_SYM_ROT90_Z) set when the occupancy, materials
  *   included, is invariant under the rotation by +90 degrees about z
  *   ((x, y) -> (-y, x); needs nx = ny), e.g. every sphere lattice.
@@ -396,7 +397,9 @@ int dda_kd(dda_t h, double* kd);
 int dda_grid(dda_t h, int* grid3);              /* padded (M_x, M_y, M_z)            */
 int dda_positions(dda_t h, int* ijk_host);      /* [N_occ][3] lattice indices (ix,iy,iz) */
 const char* dda_last_error(dda_t h);            /* never NULL; "" if no error        */
-int dda_free(dda_t h);                          /* releases all handle memory; NULL ok */
+int dda_free(dda_t h);                          /* releases all handle memory (device
+                                                   buffers go to the cache of
+                                                   dda_release_cached_memory); NULL ok */
 
 /*
  * dda_release_cached_memory -- returns to the CUDA driver the device memory
