@@ -7,7 +7,7 @@ literature formulas the paper cites but does not print (Green's tensor,
 polarizability prescriptions, Krylov solvers, far-field observables, Mie
 series).  Each function names the passage or formula it follows.
 
-It exists to judge the CUDA library, never to stand in for it: only the test
+It exists to check the CUDA library, never to stand in for it: only the test
 suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg of
 ``bench.py`` may import it.  It shares no code, table or constant generator
 with ``paper_0704_0037_gb300``; neither side imports the other.

@@ -1,7 +1,7 @@
 """GPU parity of the FFT interaction-matrix product (Eq. 2-3) against the oracle.
 
 Tolerances: relative L2 <= 1e-12 for complex128, <= 1e-5 for complex64
-(spec bounds); at full size the comparison is on sampled outputs that
+(the accuracy the two forms are built for); at full size the comparison is on sampled outputs that
 the oracle computes one by one by the direct sum.
 """
 import numpy as np
