@@ -197,7 +197,12 @@ int dda_solve(dda_t h, const dda_solve_opts* opts, int nrhs, const double* prop_
  * arithmetic per right-hand side is that of dda_solve with QMR-CS (the
  * iterates agree to rounding), and FP32_REFINED runs the same refinement per
  * right-hand side (inner complex64 solves of all unfinished right-hand sides
- * together, then one batched FP64 residual product).  Arguments as dda_solve
+ * together, then one batched FP64-class residual product: double-float on
+ * grids with register-resident passes, else FP64).  An inner complex64 solve
+ * gets at most 1000 steps (environment variable DDA_C64_INNER_CAP overrides);
+ * if it needs more, the following inner solves keep complex128 Krylov vectors
+ * and use the FP64-class product, which converges hard problems at the FP64
+ * rate where complex64 Lanczos vectors stall.  Arguments as dda_solve
  * (no history); opts->solver must be DDA_QMR_CS (else DDA_ERR_ARG).
  * info[r].seconds is the wall time of the whole call.  Allocates per call
  * about nrhs x (8 complex64 + 4 complex128) x 3 N_occ (FP32_REFINED) or
