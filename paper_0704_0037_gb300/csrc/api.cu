@@ -304,10 +304,19 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
     const long long cells = (long long)nrows * nx;
     const int nt = (int)std::max(1LL, std::min<long long>(hw ? hw : 1, cells / (1LL << 18)));
     std::vector<uint8_t> bad(nt, 0);
+    // block t of rows on thread t; blocks whose thread could not be started
+    // run on the calling thread (no exception leaves the C-ABI)
     auto run = [&](auto&& body) {
       std::vector<std::thread> th;
-      for (int t = 1; t < nt; ++t) th.emplace_back(body, t);
+      for (int t = 1; t < nt; ++t) {
+        try {
+          th.emplace_back(body, t);
+        } catch (...) {
+          break;
+        }
+      }
       body(0);
+      for (int t = 1 + (int)th.size(); t < nt; ++t) body(t);
       for (auto& x : th) x.join();
     };
     auto rows_of = [&](int t, int& r0, int& r1) {

@@ -48,7 +48,14 @@ extern "C" int dda_solve_many(int n_part, dda_t const* hs, const dda_solve_opts*
   const int nt = n_threads < n_part ? n_threads : n_part;
   std::vector<std::thread> pool;
   pool.reserve(nt);
-  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (int t = 0; t < nt; ++t) {
+    try {
+      pool.emplace_back(worker);
+    } catch (...) {               // no more threads: the started ones share the work
+      break;
+    }
+  }
+  if (pool.empty()) worker();     // none could be started: this thread does it all
   for (auto& t : pool) t.join();
   int worst = DDA_OK;
   for (int i = 0; i < n_part; ++i) {
