@@ -6,12 +6,13 @@ Workload: sphere x = 40, m = 1.05 (LDR polarizability) on a 134^3 box
 Sec. 3.1), padded FFT grid 270^3, incidence along z with x polarisation.
 
 One step = one whole pass of the path for that particle: beta and the
-right-hand side, the D-matrix (FFT of G, FP64, plus its complex64 copy),
-QMR-CS in the FP32-refined form to a true relative residual of 1e-5, and the
+right-hand side, the D-matrix (FFT of G in double-float, FP64-class, plus its
+complex64 copy), QMR-CS in the FP32-refined form to a true relative residual
+of 1e-5 (complex64 inner solve, double-float residual product), and the
 scattering quantities (F at 181 angles in the xz plane, Q_ext, Q_abs).
 
-value = products with A (complex64 and complex128) per second over the timed
-steps, whole job.  Beside it: the time to residual 1e-5 of the same solve and
+value = products with A (complex64 and double-float) per second over the
+timed steps, whole job.  Beside it: the time to residual 1e-5 of the same solve and
 of the plain FP64 form on the same GPU, per-kernel roofline data, the CPU
 oracle baseline and an end-to-end run through the C-ABI with host buffers.
 
@@ -39,7 +40,7 @@ N_SPHERE, X_SIZE, M_INDEX = 134, 40.0, 1.05
 TOL = 1e-5
 # inner complex64 solves stop at 8e-6 of the current residual: above the
 # complex64 rounding floor of this problem (5e-6 to 7.5e-6 measured), so one
-# FP64 refinement step normally ends the solve below TOL
+# FP64-class refinement step normally ends the solve below TOL
 INNER_TOL = 8e-6
 N_ANGLES = 181
 
