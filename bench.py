@@ -358,7 +358,7 @@ def run_ours(args, rank, world, local_rank):
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64+df+f64",
             "data": "synthetic (sphere occupancy computed from the lattice; no dataset)",
             "config": workload_config(n, "inputs larger than L2: 234 MB complex64 y-pass buffer, "
                                          "315 MB FP64 G grid, 121 MB D octant, per step"),
@@ -546,7 +546,7 @@ def run_batch(args, rank, world, local_rank):
     return {"metric": "aggregate products/s, seeded 128-particle batch (16 RHS each) to 1e-5",
             "value": mv / dt, "unit": "matvec/s", "n_gpus": world, "steps": 1, "warmup": 0,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic (seeded particles)",
+            "vs_baseline": None, "dtype": "c64+df+f64", "data": "synthetic (seeded particles)",
             "config": {"workload": f"{args.batch_count} seeded particles (sphere/ellipsoid/cube, "
                                    "x~U[2,15], m~U[1.05,2], 16-64 dipoles across), CLDR, "
                                    "8 directions x 2 polarisations, batched FP32-refined QMR-CS "
