@@ -67,22 +67,27 @@ cudaError_t dev_malloc_raw(void** p, size_t bytes) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  Cached c{nullptr, nullptr};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.lower_bound(std::make_pair(dev, bytes));
     if (it != g_cache.end() && it->first.first == dev && it->first.second <= bytes + bytes / 8) {
       const size_t sz = it->first.second;
-      Cached c = it->second;
+      c = it->second;
       g_cache.erase(it);
       g_cached -= sz;
-      if (c.ev) {
-        cudaEventSynchronize(c.ev);   // the freeing stream is done with it
-        cudaEventDestroy(c.ev);
-      }
-      *p = c.p;
       g_live[c.p] = Live{sz, dev};
-      return cudaSuccess;
     }
+  }
+  if (c.p) {
+    // the block is this caller's now; wait (outside the lock) until the
+    // stream that freed it is done with it
+    if (c.ev) {
+      cudaEventSynchronize(c.ev);
+      cudaEventDestroy(c.ev);
+    }
+    *p = c.p;
+    return cudaSuccess;
   }
   e = cudaMalloc(p, bytes);
   if (e == cudaErrorMemoryAllocation) {
