@@ -275,3 +275,25 @@ def test_ypol_from_xpol_by_rotation_symmetry():
     M2 = observables.mueller_plane(Fx, Fy, th)
     Ms = observables.mueller_plane(Fx, Fy_sym, th)
     assert np.abs(M2 - Ms).max() < 1e-12 * np.abs(M2).max()
+
+
+def test_mie_golden_file_matches_the_oracle():
+    """tests/golden/mie_spheres.json (read by the benchmark for its errors
+    against Mie) is what tests/golden/make_mie_golden.py computes now."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("make_mie_golden",
+                                                  os.path.join(here, "make_mie_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(here, "mie_spheres.json")) as f:
+        stored = json.load(f)["spheres"]
+    fresh = mod.cases()
+    assert len(stored) == len(fresh)
+    for a, b in zip(stored, fresh):
+        assert (a["x"], a["m"]) == (b["x"], b["m"])
+        for k in ("qext", "qsca", "g"):
+            assert abs(a[k] - b[k]) <= 1e-12 * abs(b[k])
+        assert np.allclose(a["s11"], b["s11"], rtol=1e-12, atol=0)
