@@ -33,6 +33,11 @@
  *   (NULL = legacy default stream).  Calls that return host results
  *   (dda_solve, dda_scatter) synchronise that stream before returning.
  * - A handle is not thread-safe: use one handle per host thread.
+ * - A handle belongs to the device that was current at dda_init_lattice.
+ *   Every call taking a handle makes that device current while it runs and
+ *   gives the calling thread its previous current device back before it
+ *   returns (dda_farfield_noalloc excepted: it switches no device and
+ *   requires the handle's device to be current).
  */
 #ifndef DDA_H
 #define DDA_H
@@ -92,12 +97,25 @@ enum dda_prec { DDA_FP64 = 0, DDA_FP32_REFINED = 1, DDA_FP64_PAIR = 2 };
  *   DDA_ERR_CUDA / DDA_ERR_OOM.  Copies what it needs from the host arrays.
  * The FFT passes use register-resident kernels for padded lengths with a
  * compiled split (32, 64, 128, 256, 270) and shared-memory Stockham kernels
- * otherwise; environment variable DDA_FFT_ENGINE=stockham at this call forces
- * the latter for the handle (both give the same product to rounding).
+ * otherwise; dda_set_fft_engine selects the latter for every length.
  */
 int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_t* occ_host,
                      int n_mat, const double* m_host, double kd, int volume_corrected,
                      void* cuda_stream);
+
+/*
+ * dda_set_fft_engine -- which FFT kernels the handle's products use.
+ *   engine : DDA_ENGINE_AUTO (the default) -- register-resident two-level
+ *            passes for padded lengths with a compiled split, shared-memory
+ *            Stockham passes otherwise; DDA_ENGINE_STOCKHAM -- the Stockham
+ *            passes for every length (both give the same product to rounding;
+ *            the FP32_REFINED build then uses FP64 instead of double-float).
+ * Must precede the first dda_build_Dmatrix of the handle (DDA_ERR_STATE after
+ * it); DDA_ERR_ARG for an unknown value.  No counterpart in the paper (Sec. 2
+ * names the FFT libraries ADDA can use).
+ */
+enum dda_engine { DDA_ENGINE_AUTO = 0, DDA_ENGINE_STOCKHAM = 1 };
+int dda_set_fft_engine(dda_t h, int engine);
 
 /*
  * dda_build_Dmatrix -- FFT of the Green's tensor on the padded grid (Sec. 2:
@@ -153,6 +171,9 @@ typedef struct {
   int maxiter;          /* iterations per RHS (inner iterations summed for FP32)  */
   double inner_tol;     /* FP32_REFINED: relative tolerance of each inner solve   */
   int checkpoint_every; /* reserved, 0                                            */
+  int inner_cap;        /* FP32_REFINED: complex64 steps an inner solve may take
+                           before the later inner solves switch to complex128
+                           vectors and FP64-class products; <= 0: 1000          */
 } dda_solve_opts;
 
 typedef struct {
@@ -199,7 +220,7 @@ int dda_solve(dda_t h, const dda_solve_opts* opts, int nrhs, const double* prop_
  * right-hand side (inner complex64 solves of all unfinished right-hand sides
  * together, then one batched FP64-class residual product: double-float on
  * grids with register-resident passes, else FP64).  An inner complex64 solve
- * gets at most 1000 steps (environment variable DDA_C64_INNER_CAP overrides);
+ * gets at most opts->inner_cap steps (1000 when inner_cap <= 0);
  * if it needs more, the following inner solves keep complex128 Krylov vectors
  * and use the FP64-class product, which converges hard problems at the FP64
  * rate where complex64 Lanczos vectors stall.  Arguments as dda_solve
@@ -231,6 +252,22 @@ int dda_solve_many(int n_part, dda_t const* hs, const dda_solve_opts* opts, cons
                    const double* const* prop_host, const double* const* pol_host,
                    void* const* P_dev, dda_solve_info* const* info, int n_threads,
                    int* status_out);
+
+/*
+ * dda_residual -- the relative residual ||b - A x||_2 / ||b||_2 of Sec. 2's
+ * stopping criterion for given polarizations P, evaluated outside any solver
+ * with the native FP64 (complex128) product: x = P / beta, b = beta E_inc
+ * (Eq. (3)).  Used to check a solution whatever precision produced it.
+ *   pol_prescription, nrhs, prop_host, pol_host : as dda_solve (also leaves
+ *                      beta set for these right-hand sides, as dda_set_beta).
+ *   P_dev        : device [nrhs][3][N_occ] complex128 (read only).
+ *   res_out_host : nrhs doubles (0 where b = 0).
+ * Requires dda_build_Dmatrix (either precision; a FP32_REFINED build derives
+ * its FP64 octant on first use).  Uses 4 x 3 N_occ complex128 of the handle's
+ * solver workspace.  Synchronises the stream.
+ */
+int dda_residual(dda_t h, int pol_prescription, int nrhs, const double* prop_host,
+                 const double* pol_host, const void* P_dev, double* res_out_host);
 
 /*
  * dda_scatter -- scattering quantities of Sec. 3.1 from P (FP64 sums).
@@ -368,7 +405,9 @@ int dda_orientation_average(dda_t h, const dda_solve_opts* opts, int n_alpha, in
  * process exits); a request needing more than that (about n_dir *
  * (nx+ny+nz) * 16 bytes plus the partial sums) returns DDA_ERR_ARG with the
  * size in dda_last_error.  The first call on a device looks up the array's
- * address with that device current: make it before any stream capture.  All
+ * address with that device current: make it before any stream capture.  The
+ * handle's device must be the current device (this call does not switch
+ * devices, so that a capture in progress is left alone): DDA_ERR_ARG if not.  All
  * calls share the array, so calls that overlap on the GPU race; the array
  * keeps the last call's contents, which no call depends on.  Asynchronous on
  * the handle's stream; calls no cudaMalloc or cudaFree.
@@ -420,6 +459,25 @@ int dda_free(dda_t h);                          /* releases all handle memory (d
  * Memory held by live handles is not affected.  Returns DDA_OK.
  */
 int dda_release_cached_memory(void);
+
+/*
+ * dda_set_memory_limit -- caps the device memory held by the library's live
+ * handles (all devices together) at `bytes` (0 = no cap, the default).  An
+ * allocation that would pass the cap fails as if the device were out of
+ * memory: the entry point returns DDA_ERR_OOM with the handle left usable
+ * (a product or solve that needs more memory can be retried after the cap
+ * is raised or other handles are freed).  For services that share a GPU and
+ * give each library a memory budget.  Setting a nonzero cap also releases
+ * the cache of freed blocks (dda_release_cached_memory).  Thread-safe;
+ * returns DDA_OK.
+ */
+int dda_set_memory_limit(unsigned long long bytes);
+
+/*
+ * dda_memory_in_use -- bytes of device memory held by live handles and by
+ * the cache of freed blocks (all devices).  DDA_ERR_ARG on a null pointer.
+ */
+int dda_memory_in_use(unsigned long long* live_bytes, unsigned long long* cached_bytes);
 
 #ifdef __cplusplus
 }

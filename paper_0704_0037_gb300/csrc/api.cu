@@ -368,8 +368,7 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   g.Mz = smooth_size(2 * nz - 1);
   g.px = make_plan(g.Mx); g.py = make_plan(g.My); g.pz = make_plan(g.Mz);
   g.tr = &h->tracer;
-  const char* eng = std::getenv("DDA_FFT_ENGINE");
-  g.engine = (eng && std::strcmp(eng, "stockham") == 0) ? 1 : 0;
+  g.engine = DDA_ENGINE_AUTO;
   h->n_mat = n_mat;
   h->m.assign(m, m + 2 * n_mat);
   // Sec. 3.1 volume correction: N_occ d^3 = (4/3) pi a^3  =>  kd = x (4 pi / (3 N_occ))^(1/3)
@@ -394,8 +393,18 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   return DDA_OK;
 }
 
-extern "C" int dda_build_Dmatrix(dda_t h, int prec) {
+extern "C" int dda_set_fft_engine(dda_t h, int engine) {
   if (!h) return DDA_ERR_ARG;
+  if (engine != DDA_ENGINE_AUTO && engine != DDA_ENGINE_STOCKHAM)
+    return dda_fail(h, DDA_ERR_ARG, "unknown FFT engine");
+  if (h->w64.have_D || h->w32.have_D || h->wdf.have_D)
+    return dda_fail(h, DDA_ERR_STATE, "dda_set_fft_engine must precede dda_build_Dmatrix");
+  h->g.engine = engine;
+  return DDA_OK;
+}
+
+extern "C" int dda_build_Dmatrix(dda_t h, int prec) {
+  DDA_ON_DEVICE(h);
   if (prec != DDA_FP64 && prec != DDA_FP32_REFINED) return dda_fail(h, DDA_ERR_ARG, "unknown precision");
   if (h->g.px.nst < 0 || h->g.py.nst < 0 || h->g.pz.nst < 0)
     return dda_fail(h, DDA_ERR_ARG, "padded grid is not 7-smooth");
@@ -419,12 +428,12 @@ extern "C" int dda_build_Dmatrix(dda_t h, int prec) {
 }
 
 extern "C" int dda_set_beta(dda_t h, int presc, int nrhs, const double* prop, const double* pol) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   return dda_beta_internal(h, presc, nrhs, prop, pol);
 }
 
 static int matvec_common(dda_t h, int prec, const void* x, void* y, int nrhs, bool adjoint) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   if (!x || !y) return dda_fail(h, DDA_ERR_ARG, "x and y must not be NULL");
   if (x == y) return dda_fail(h, DDA_ERR_ARG, "x and y must not alias");
   if (nrhs < 1) return dda_fail(h, DDA_ERR_ARG, "nrhs must be >= 1");
@@ -471,7 +480,7 @@ extern "C" int dda_matvec_adjoint(dda_t h, int prec, const void* x, void* y, int
 extern "C" int dda_solve(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                          const double* pol, void* P_dev, double* hist, int hist_len,
                          dda_solve_info* info) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   if (!o || !prop || !pol || !P_dev || !info || nrhs < 1 || (hist && hist_len < 1))
     return dda_fail(h, DDA_ERR_ARG, "bad dda_solve arguments");
   if (o->solver < DDA_QMR_CS || o->solver > DDA_CGNR) return dda_fail(h, DDA_ERR_ARG, "unknown solver");
@@ -492,7 +501,7 @@ extern "C" int dda_solve(dda_t h, const dda_solve_opts* o, int nrhs, const doubl
 
 extern "C" int dda_solve_batch(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                                const double* pol, void* P_dev, dda_solve_info* info) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   if (!o || !prop || !pol || !P_dev || !info || nrhs < 1)
     return dda_fail(h, DDA_ERR_ARG, "bad dda_solve_batch arguments");
   if (o->solver != DDA_QMR_CS) return dda_fail(h, DDA_ERR_ARG, "dda_solve_batch runs QMR-CS only");
@@ -506,10 +515,22 @@ extern "C" int dda_solve_batch(dda_t h, const dda_solve_opts* o, int nrhs, const
   return dda_solve_batch_internal(h, o, nrhs, prop, pol, P_dev, info);
 }
 
+extern "C" int dda_residual(dda_t h, int presc, int nrhs, const double* prop, const double* pol,
+                            const void* P_dev, double* res) {
+  DDA_ON_DEVICE(h);
+  if (!prop || !pol || !P_dev || !res || nrhs < 1)
+    return dda_fail(h, DDA_ERR_ARG, "bad dda_residual arguments");
+  if (presc < DDA_CM || presc > DDA_CLDR) return dda_fail(h, DDA_ERR_ARG, "unknown polarizability prescription");
+  if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "D-matrix not built");
+  const int rc = dda_residual_internal(h, presc, nrhs, prop, pol, P_dev, res);
+  if (rc == DDA_OK) DDA_CK(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
 extern "C" int dda_scatter(dda_t h, int presc, const void* P_dev, int nrhs, const double* prop,
                            const double* pol, int n_dir, const double* dirs, const double* w,
                            double* F_out, double* q_out) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   if (!P_dev || nrhs < 1 || !prop || !pol || n_dir < 0 || (n_dir > 0 && (!dirs || !F_out)) || !q_out)
     return dda_fail(h, DDA_ERR_ARG, "bad dda_scatter arguments");
   if (presc < DDA_CM || presc > DDA_CLDR) return dda_fail(h, DDA_ERR_ARG, "unknown polarizability prescription");
@@ -605,7 +626,7 @@ extern "C" int dda_symmetry(dda_t h, int* flags) {
 
 extern "C" int dda_mueller_plane_sym(dda_t h, int presc, const void* P_dev, int n_theta,
                                      const double* th, double* M, double* F_out) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   if (!(lattice_symmetry(h) & DDA_SYM_ROT90_Z))
     return dda_fail(h, DDA_ERR_ARG, "lattice is not invariant under the 90 degree rotation about z");
   if (n_theta < 1 || !th || !M || !P_dev) return dda_fail(h, DDA_ERR_ARG, "bad arguments");
@@ -680,6 +701,7 @@ extern "C" const char* dda_last_error(dda_t h) {
 
 extern "C" int dda_free(dda_t h) {
   if (!h) return DDA_OK;
+  dda::DeviceGuard dev_guard(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   tr_destroy(&h->tracer);

@@ -166,11 +166,11 @@ __global__ void k_to32(const c128* __restrict__ a, c64* __restrict__ b, long lon
     b[i] = mk<float>((float)a[i].x, (float)a[i].y);
 }
 
-static int rows_grid(int rows) { return rows < 152 * 64 ? rows : 152 * 64; }
+static int rows_grid(int rows) { return std::min(rows, num_sms() * 64); }
 
 static int grid_for(long long n) {
   long long b = (n + 255) / 256;
-  if (b > 152LL * 16) b = 152LL * 16;
+  if (b > 16LL * num_sms()) b = 16LL * num_sms();
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -340,7 +340,7 @@ int dda_build_D_internal(dda_t h, bool want32) {
     if (scratch != h->d_dscratch) dev_free(scratch, h->stream);
   };
   tr_begin(g.tr, st);
-  const int rgrid = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, 152LL * 8));
+  const int rgrid = (int)std::max<long long>(1, std::min<long long>((nmax + 255) / 256, 8LL * num_sms()));
   if (use_df) {
     k_green_radial<cdf><<<rgrid, 256, 0, st>>>((cdf*)ab, h->kd, nmax); count_launch();
     k_green_table<df><<<rows_grid(g.ny * g.nz), 128, 0, st>>>((cdf*)table, (const cdf*)ab, g.nx, g.ny, g.nz); count_launch();

@@ -12,6 +12,8 @@
 // image: every GPU that loads the library holds it until the process exits.
 //
 // Rules of use:
+//  * The handle's device must be the calling thread's current device (the
+//    entry point does not switch devices); otherwise DDA_ERR_ARG.
 //  * The first call on a device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
 //    before starting any stream capture.
@@ -65,10 +67,22 @@ extern "C" int dda_farfield_noalloc(dda_t h, const void* P_dev, int n_dir, const
   if (!h) return DDA_ERR_ARG;
   if (!P_dev || !dirs_dev || !F_dev || n_dir < 1)
     return dda_fail(h, DDA_ERR_ARG, "dda_farfield_noalloc: NULL buffer or n_dir < 1");
+  // The scratch address and the kernels belong to the current device, which
+  // this entry point does not change (a stream capture in progress on the
+  // caller's thread is left alone): it must be the handle's.
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return dda_fail(h, DDA_ERR_CUDA, "dda_farfield_noalloc: cudaGetDevice failed");
+  }
+  if (cur != h->device)
+    return dda_fail(h, DDA_ERR_ARG,
+                    "dda_farfield_noalloc: the handle's device (" + std::to_string(h->device) +
+                        ") is not the current device (" + std::to_string(cur) + ")");
   const Geom& g = h->g;
   const int L = g.nx + g.ny + g.nz;
   const int dblocks = (n_dir + kFarfieldDB - 1) / kFarfieldDB;
-  int n_chunks = std::max(1, std::min((152 * 4 + dblocks - 1) / dblocks, (g.nrows + 31) / 32));
+  int n_chunks = std::max(1, std::min((4 * num_sms() + dblocks - 1) / dblocks, (g.nrows + 31) / 32));
   const int rows_per_chunk = (g.nrows + n_chunks - 1) / n_chunks;
   n_chunks = (g.nrows + rows_per_chunk - 1) / rows_per_chunk;
   const size_t tab_bytes = ((size_t)n_dir * L * sizeof(c128) + 255) / 256 * 256;

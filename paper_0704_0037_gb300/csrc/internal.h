@@ -186,6 +186,9 @@ int ensure_d64(dda_t h);
 int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                              const double* pol, void* P_dev, dda_solve_info* info);
 void batch_free(dda_t h);
+// ||b - A x|| / ||b|| per right-hand side with x = P / beta, native FP64 product
+int dda_residual_internal(dda_t h, int presc, int nrhs, const double* prop, const double* pol,
+                          const void* P_dev, double* res);
 int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                        const double* pol, void* P_dev, double* hist, int hist_len,
                        dda_solve_info* info);
@@ -261,6 +264,40 @@ cudaError_t fast_pass_256_df(int pass, const FastArgs& a);
 cudaError_t fast_pass_small_df(int M, int pass, const FastArgs& a);
 template <> cudaError_t fast_pass<df>(int M, int pass, const FastArgs& a);
 }  // namespace dda
+
+namespace dda {
+// Makes device dev current for the lifetime of the guard and puts the calling
+// thread's current device back afterwards, so that every entry point runs on
+// the handle's device whatever device the caller had selected.
+struct DeviceGuard {
+  int prev = -1;
+  int dev;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int d) : dev(d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+// Number of multiprocessors of the current device (queried once per device);
+// grid sizes of the grid-stride kernels are multiples of it.
+int num_sms();
+}  // namespace dda
+
+// Entry-point prologue: a null handle is an argument error; otherwise the
+// handle's device is made current until the entry point returns.
+#define DDA_ON_DEVICE(h)                                                        \
+  if (!(h)) return DDA_ERR_ARG;                                                 \
+  dda::DeviceGuard dda_dev_guard_(h->device);                                   \
+  if (dda_dev_guard_.err != cudaSuccess)                                        \
+    return dda_cuda_fail(h, dda_dev_guard_.err, "cudaSetDevice(handle's device)")
 
 namespace dda {
 // Kernel attributes set once per (kernel, device) instead of before every

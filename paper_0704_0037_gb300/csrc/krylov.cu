@@ -296,7 +296,7 @@ int launch_rhs(dda_t h, c128* b, const c128* beta, const Wave& wv, cudaStream_t 
   const int L = g.nx + g.ny + g.nz;
   c128* ptab = (c128*)h->d_ptab;
   k_axis_phase<<<(L + 255) / 256, 256, 0, st>>>(ptab, h->kd, wv, g.nx, g.ny, g.nz); count_launch();
-  const int rows_grid = (int)std::min<long long>((g.nrows + 7) / 8, 152LL * 32);
+  const int rows_grid = (int)std::min<long long>((g.nrows + 7) / 8, 32LL * num_sms());
   k_rhs<double><<<rows_grid, 256, 0, st>>>(b, h->lat(), beta, g.n_occ, g.nx, g.ny, g.nrows, ptab,
                                            wv); count_launch();
   const cudaError_t e = cudaGetLastError();
@@ -1062,7 +1062,7 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
   ru.part = h->d_part;
   ru.ds = (Scal*)h->d_scal;
   ru.hs = (Scal*)h->h_scal;
-  const int rows_grid = (int)std::min<long long>((h->g.nrows + 7) / 8, 152LL * 32);
+  const int rows_grid = (int)std::min<long long>((h->g.nrows + 7) / 8, 32LL * num_sms());
   int worst = DDA_OK;
   for (int r = 0; r < nrhs; ++r) {
     auto t0 = std::chrono::steady_clock::now();
@@ -1126,7 +1126,8 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
       int left = o->maxiter;
       st_rhs = bn > 0 ? DDA_NOT_CONVERGED : DDA_OK;
       res_true = bn > 0 ? 1.0 : 0.0;
-      while (bn > 0 && left > 0 && outer < 64) {
+      if (!std::isfinite(bn)) { st_rhs = DDA_ERR_NONFINITE; res_true = NAN; }  // NaN/Inf in b
+      while (bn > 0 && std::isfinite(bn) && left > 0 && outer < 64) {
         if (rn / bn < o->tol) { st_rhs = DDA_OK; break; }
         const double target = std::max(o->inner_tol, 0.5 * o->tol * bn / rn);
         k_to32s<<<ru.nb, kVT, 0, ru.st>>>(r64, b32, n, 1.0 / rn); count_launch();
@@ -1186,6 +1187,75 @@ int dda_solve_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double*
   return worst;
 }
 
+// ---------------------------------------------------------------- true residual
+namespace dda {
+namespace {
+// x = P / beta (Eq. (3)); a dipole with beta = 0 (m = 1, alpha = 0) has
+// P = 0 and b = 0, and takes x = 0
+__global__ void k_x_from_P(const c128* __restrict__ P, c128* __restrict__ x,
+                           const uint8_t* __restrict__ mat, const c128* __restrict__ beta,
+                           long long n_occ) {
+  VLOOP(3 * n_occ) {
+    const int c = (int)(i / n_occ);
+    const long long j = i - c * n_occ;
+    const c128 b = beta[mat[j] * 3 + c];
+    const double d = b.x * b.x + b.y * b.y;
+    const c128 p = P[i];
+    x[i] = d > 0.0 ? mk<double>((p.x * b.x + p.y * b.y) / d, (p.y * b.x - p.x * b.y) / d)
+                   : mk<double>(0.0, 0.0);
+  }
+}
+}  // namespace
+}  // namespace dda
+
+int dda_residual_internal(dda_t h, int presc, int nrhs, const double* prop, const double* pol,
+                          const void* P_dev, double* res) {
+  int rc = dda_beta_internal(h, presc, nrhs, prop, pol);
+  if (rc != DDA_OK) return rc;
+  rc = ensure_d64(h);
+  if (rc == DDA_OK) rc = ensure_work_cap<double>(h, h->w64, 1);
+  if (rc != DDA_OK) return rc;
+  const long long n = 3 * h->g.n_occ;
+  rc = ensure_solver_mem(h, (size_t)n * 4 * sizeof(c128));
+  if (rc != DDA_OK) return rc;
+  Run ru;
+  ru.h = h; ru.st = h->stream; ru.n = n;
+  const long long nb = (n + 4LL * kVT - 1) / (4LL * kVT);
+  ru.nb = (int)(nb < 1 ? 1 : (nb > kNB ? kNB : nb));
+  ru.part = h->d_part;
+  ru.ds = (Scal*)h->d_scal;
+  ru.hs = (Scal*)h->h_scal;
+  c128* x = (c128*)h->sv;
+  c128* b = x + n;
+  c128* w = b + n;
+  c128* r = w + n;
+  for (int k = 0; k < nrhs; ++k) {
+    Wave wv;
+    for (int q = 0; q < 3; ++q) wv.a[q] = prop[3 * k + q];
+    for (int q = 0; q < 6; ++q) wv.e[q] = pol[6 * k + q];
+    const c128* beta64 = h->w64.beta + (long long)k * h->n_mat * 3;
+    RK(launch_rhs(h, b, beta64, wv, ru.st));
+    k_x_from_P<<<ru.nb, kVT, 0, ru.st>>>((const c128*)P_dev + (size_t)k * n, x, h->d_mat, beta64,
+                                         h->g.n_occ); count_launch();
+    LK(h);
+    k_norms<double><<<ru.nb, kVT, 0, ru.st>>>(b, n, ru.part, nullptr); count_launch();
+    k_take_norm<<<1, kVT, 0, ru.st>>>(ru.ds, ru.part, ru.nb); count_launch();
+    LK(h);
+    RK(sync_read(ru));
+    const double bn = ru.hs->sres;
+    // the FP64 product of this right-hand side's beta table
+    cudaError_t e = launch_matvec<double>(h->g, h->lat(), h->w64, beta64, h->n_mat, x, w, 1,
+                                          false, ru.st);
+    if (e != cudaSuccess) return dda_cuda_fail(h, e, "residual product");
+    k_resid<<<ru.nb, kVT, 0, ru.st>>>(b, w, r, n, ru.part); count_launch();
+    k_take_norm<<<1, kVT, 0, ru.st>>>(ru.ds, ru.part, ru.nb); count_launch();
+    LK(h);
+    RK(sync_read(ru));
+    res[k] = bn > 0 ? ru.hs->sres / bn : 0.0;
+  }
+  return DDA_OK;
+}
+
 // ---------------------------------------------------------------- batched QMR-CS
 // All right-hand sides of one particle advance together: every QMR step is
 // one launch per product pass and per solver kernel for all of them (the
@@ -1207,16 +1277,8 @@ constexpr int kSyncEvery = 8;
 // stall (1.5e-3 after 100,000 steps; the FP64 form needs 50,872), so the
 // product's accuracy, not only the vectors', sets the rate.
 constexpr int kC64InnerCap = 1000;
-// the cap, or DDA_C64_INNER_CAP from the environment (a tuning knob; tests use
-// a small value to exercise the switch on small problems)
-int c64_inner_cap() {
-  const char* v = std::getenv("DDA_C64_INNER_CAP");
-  if (v) {
-    const int c = std::atoi(v);
-    if (c > 0) return c;
-  }
-  return kC64InnerCap;
-}
+// the cap of a solve: dda_solve_opts.inner_cap when positive, else the default
+int c64_inner_cap(const dda_solve_opts* o) { return o->inner_cap > 0 ? o->inner_cap : kC64InnerCap; }
 
 // b32[r] = (complex64)(a64[r] * scl[r]) for right-hand sides with off[r] == 0
 __global__ void k_to32s_b(const c128* __restrict__ a, c64* __restrict__ b, long long n,
@@ -1501,7 +1563,7 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
   b.h = h; b.st = h->stream; b.n = n; b.nrhs = nrhs; b.m = m;
   long long nbl = (n + 4LL * kVT - 1) / (4LL * kVT);
   b.nb = (int)(nbl < 1 ? 1 : (nbl > kNB ? kNB : nbl));
-  const int rows_grid = (int)std::min<long long>((h->g.nrows + 7) / 8, 152LL * 32);
+  const int rows_grid = (int)std::min<long long>((h->g.nrows + 7) / 8, 32LL * num_sms());
   cudaStream_t st = b.st;
   std::vector<int> status(nrhs, DDA_NOT_CONVERGED), iters(nrhs, 0), outer(nrhs, 0);
   std::vector<int> mv64(nrhs, 0);
@@ -1574,7 +1636,8 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
     for (int r = 0; r < nrhs; ++r) {
       bn[r] = m->hs[r].sres;
       rn[r] = bn[r];
-      if (!(bn[r] > 0)) { fin_[r] = 1; status[r] = DDA_OK; res_true[r] = 0.0; }
+      if (!std::isfinite(bn[r])) { fin_[r] = 1; status[r] = DDA_ERR_NONFINITE; res_true[r] = NAN; }
+      else if (!(bn[r] > 0)) { fin_[r] = 1; status[r] = DDA_OK; res_true[r] = 0.0; }
       else res_true[r] = 1.0;
     }
     int left = o->maxiter;
@@ -1600,7 +1663,7 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
       if (!mixed) {
         k_to32s_b<<<vg, kVT, 0, st>>>(r64, rhs32, n, m->dvals + nrhs, m->off); count_launch();
         LK(h);
-        const int cap = std::min(left, c64_inner_cap());
+        const int cap = std::min(left, c64_inner_cap(o));
         RK(run_qmr_batched<float>(b, rhs32, x32, vec, 0.0, m->dvals, m->off, cap, &steps));
         capped = steps >= cap && cap < left;
       } else {

@@ -32,11 +32,8 @@ extern "C" int dda_solve_many(int n_part, dda_t const* hs, const dda_solve_opts*
       const int i = next.fetch_add(1);
       if (i >= n_part) break;
       dda_t h = hs[i];
-      if (cudaSetDevice(h->device) != cudaSuccess) {
-        cudaGetLastError();
-        status_out[i] = dda_fail(h, DDA_ERR_CUDA, "cudaSetDevice");
-        continue;
-      }
+      // the entry points below make the handle's device current themselves
+      // and restore this thread's device afterwards
       int rc = DDA_OK;
       const bool need64 = !h->w64.have_D;
       const bool need32 = o->prec == DDA_FP32_REFINED && !h->w32.have_D;

@@ -67,7 +67,7 @@ Mat3 ry(double t) {
 extern "C" int dda_orientation_average(dda_t h, const dda_solve_opts* o, int n_alpha, int n_beta,
                                        int n_gamma, int n_theta, const double* theta_deg,
                                        double* q_avg, double* M_avg, dda_solve_info* info) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   if (!o || n_alpha < 1 || n_beta < 1 || n_gamma < 1 || n_theta < 1 || !theta_deg || !q_avg ||
       !M_avg)
     return dda_fail(h, DDA_ERR_ARG, "bad dda_orientation_average arguments");

@@ -264,7 +264,7 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
   int n_chunks = 1, rows_per_chunk = fnrows;
   if (n_dir > 0) {
     const int dblocks = (n_dir + kDB - 1) / kDB;
-    n_chunks = std::max(1, std::min((152 * 4 + dblocks - 1) / dblocks, (fnrows + 31) / 32));
+    n_chunks = std::max(1, std::min((4 * num_sms() + dblocks - 1) / dblocks, (fnrows + 31) / 32));
     rows_per_chunk = (fnrows + n_chunks - 1) / n_chunks;
     n_chunks = (fnrows + rows_per_chunk - 1) / rows_per_chunk;
   }

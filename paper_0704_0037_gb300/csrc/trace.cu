@@ -81,7 +81,7 @@ void tr_destroy(Tracer* t) {
 using namespace dda;
 
 extern "C" int dda_trace(dda_t h, int enable) {
-  if (!h) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   tr_reset(&h->tracer);
   h->tracer.on = enable != 0;
   return DDA_OK;
@@ -90,6 +90,7 @@ extern "C" int dda_trace(dda_t h, int enable) {
 extern "C" int dda_trace_read(dda_t h, int max_n, char* names, double* ms, long long* count,
                               int* n_out) {
   if (!h || max_n < 0 || (max_n > 0 && (!names || !ms || !count)) || !n_out) return DDA_ERR_ARG;
+  DDA_ON_DEVICE(h);
   tr_flush(&h->tracer);
   int k = 0;
   if (max_n > 0) {
@@ -145,6 +146,30 @@ cudaError_t ensure_carveout_max(const void* func) {
   e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess) g_carve[key] = true;
   return e;
+}
+
+}  // namespace dda
+
+namespace dda {
+
+int num_sms() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;                       // not cached: asked again next time
+  }
+  cache[dev] = n;
+  return n;
 }
 
 }  // namespace dda

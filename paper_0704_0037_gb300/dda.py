@@ -24,6 +24,7 @@ DDA_ERR_ARG, DDA_ERR_CUDA, DDA_ERR_OOM, DDA_ERR_STATE, DDA_ERR_NONFINITE, DDA_ER
 DDA_CM, DDA_RR, DDA_LDR, DDA_CLDR = 0, 1, 2, 3
 DDA_QMR_CS, DDA_BICG_CS, DDA_BICGSTAB, DDA_CGNR = 0, 1, 2, 3
 DDA_FP64, DDA_FP32_REFINED, DDA_FP64_PAIR = 0, 1, 2
+DDA_ENGINE_AUTO, DDA_ENGINE_STOCKHAM = 0, 1
 
 STATUS_NAMES = {0: "ok", 1: "not_converged", 2: "breakdown", -1: "err_arg", -2: "err_cuda",
                 -3: "err_oom", -4: "err_state", -5: "err_nonfinite", -6: "err_timeout"}
@@ -38,7 +39,8 @@ EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec"
            "dda_orientation_average",
            "dda_farfield_noalloc", "dda_trace",
            "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
-           "dda_free", "dda_release_cached_memory")
+           "dda_free", "dda_release_cached_memory", "dda_set_fft_engine", "dda_set_memory_limit",
+           "dda_memory_in_use", "dda_residual")
 
 
 class DDAError(RuntimeError):
@@ -50,7 +52,7 @@ class DDAError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("pol", ctypes.c_int), ("prec", ctypes.c_int),
                 ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("checkpoint_every", ctypes.c_int)]
+                ("checkpoint_every", ctypes.c_int), ("inner_cap", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -84,6 +86,9 @@ def lib():
         "dda_init_lattice": ([ctypes.POINTER(_vp), _ip, _ip, _ip, ctypes.POINTER(ctypes.c_uint8), _ip,
                               _dp, ctypes.c_double, _ip, _vp], _ip),
         "dda_build_Dmatrix": ([_vp, _ip], _ip),
+        "dda_set_fft_engine": ([_vp, _ip], _ip),
+        "dda_set_memory_limit": ([ctypes.c_ulonglong], _ip),
+        "dda_memory_in_use": ([ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)], _ip),
         "dda_set_beta": ([_vp, _ip, _ip, _dp, _dp], _ip),
         "dda_matvec": ([_vp, _ip, _vp, _vp, _ip], _ip),
         "dda_matvec_adjoint": ([_vp, _ip, _vp, _vp, _ip], _ip),
@@ -95,6 +100,7 @@ def lib():
                             ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_vp),
                             ctypes.POINTER(ctypes.POINTER(SolveInfo)), _ip, ctypes.POINTER(_ip)], _ip),
         "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
+        "dda_residual": ([_vp, _ip, _ip, _dp, _dp, _vp, _dp], _ip),
         "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane_full": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_asymmetry": ([_ip, _dp, _dp, _dp, _dp, _dp], _ip),
@@ -178,6 +184,24 @@ def dda_init_lattice(occ, m_list, kd, volume_corrected=False, stream=None):
     return h
 
 
+def dda_set_fft_engine(h, engine):
+    return _check(h, lib().dda_set_fft_engine(h, int(engine)))
+
+
+def dda_set_memory_limit(nbytes):
+    """Cap on the device bytes held by the library's live handles (0: none)."""
+    return lib().dda_set_memory_limit(int(nbytes))
+
+
+def dda_memory_in_use():
+    """(bytes held by live handles, bytes in the cache of freed blocks)."""
+    a, b = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    rc = lib().dda_memory_in_use(ctypes.byref(a), ctypes.byref(b))
+    if rc < 0:
+        raise DDAError(rc, "dda_memory_in_use")
+    return a.value, b.value
+
+
 def dda_build_Dmatrix(h, prec=DDA_FP64):
     return _check(h, lib().dda_build_Dmatrix(h, int(prec)))
 
@@ -206,7 +230,7 @@ def _opts(opts):
         return SolveOpts(solver=opts.get("solver", DDA_QMR_CS), pol=opts.get("pol", DDA_LDR),
                          prec=opts.get("prec", DDA_FP64), tol=opts.get("tol", 1e-5),
                          maxiter=opts.get("maxiter", 10000), inner_tol=opts.get("inner_tol", 1e-3),
-                         checkpoint_every=0)
+                         checkpoint_every=0, inner_cap=opts.get("inner_cap", 0))
     return opts
 
 
@@ -267,6 +291,17 @@ def dda_solve_many(handles, opts, props, pols, Ps, n_threads=8):
     if rc < 0 and all(s == 0 for s in st):
         raise DDAError(rc, "dda_solve_many arguments")
     return rc, list(st), [[x.as_dict() for x in inf] for inf in infos]
+
+
+def dda_residual(h, pol_prescription, P, prop, pol):
+    """||b - A x|| / ||b|| per right-hand side (x = P / beta), native FP64 product."""
+    import torch
+    nrhs = int(np.asarray(prop).size // 3)
+    a, e = _vecs(prop, pol, nrhs)
+    res = np.zeros(nrhs)
+    _check(h, lib().dda_residual(h, int(pol_prescription), nrhs, _dptr(a), _dptr(e),
+                                 _dev_ptr(P, torch.complex128), _dptr(res)))
+    return res
 
 
 def dda_scatter(h, pol_prescription, P, prop, pol, dirs=None, weights=None):
@@ -439,8 +474,10 @@ def dda_free(h):
 class Particle:
     """Owns one handle; frees it on close / garbage collection."""
 
-    def __init__(self, occ, m_list, kd, volume_corrected=False, stream=None):
+    def __init__(self, occ, m_list, kd, volume_corrected=False, stream=None, engine=None):
         self.h = dda_init_lattice(occ, m_list, kd, volume_corrected, stream)
+        if engine is not None:
+            dda_set_fft_engine(self.h, engine)
         self.n_occ = dda_n_occ(self.h)
         self.kd = dda_kd(self.h)
         self.grid = dda_grid(self.h)

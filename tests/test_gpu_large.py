@@ -6,32 +6,36 @@ x = 160 sphere is solved to 1e-5 and compared with Mie theory (Sec. 3.1)."""
 import numpy as np
 import pytest
 
-from oracle import lattice, mie, observables, system
+from oracle import lattice, mie, observables
 from oracle import dda as odda
 from paper_0704_0037_gb300 import inputs
 
-from gpu_util import need_gpu
+from gpu_util import direct_sum_rows, need_gpu, sample_dipoles
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-def _sampled_check(p, occ, m, prec_name, idx_count, seed):
+def _sampled_reference(p, occ, m, count, seed):
+    """x, sampled dipole indices and the oracle's direct-sum outputs there."""
+    x = inputs.random_vectors(seed, 1, p.n_occ)
+    idx = sample_dipoles(occ, count, seed)
+    prob = odda.Problem(occ, [m], p.kd)
+    beta = prob.beta("ldr", (0, 0, 1), (1, 0, 0))
+    return x, idx, direct_sum_rows(prob.pos, beta, prob.kd, x[0], idx)
+
+
+def _sampled_check(p, ref, prec_name):
     torch, dda = need_gpu()
+    x, idx, yref = ref
     prec = dda.PREC[prec_name]
     dda.dda_set_beta(p.h, dda.DDA_LDR, [(0, 0, 1)], [(1, 0, 0)])
-    x = inputs.random_vectors(seed, 1, p.n_occ)
     dt = torch.complex128 if prec == dda.DDA_FP64 else torch.complex64
     xd = torch.from_numpy(x).to("cuda", dt)
     yd = torch.empty_like(xd)
     dda.dda_matvec(p.h, prec, xd, yd)
-    idx = np.array([0, p.n_occ - 1] + list(np.random.default_rng(seed).integers(0, p.n_occ,
-                                                                              idx_count - 2)))
     y = yd[0][:, torch.from_numpy(idx).cuda()].cpu().numpy()
     del xd, yd
-    prob = odda.Problem(occ, [m], p.kd)
-    beta = prob.beta("ldr", (0, 0, 1), (1, 0, 0))
-    ref = system.matvec_rows(prob.pos, beta, prob.kd, x[0], idx)
-    err = np.abs(y - ref).max() / np.sqrt(np.mean(np.abs(ref) ** 2))
+    err = np.abs(y - yref).max() / np.sqrt(np.mean(np.abs(yref) ** 2))
     assert err <= (1e-12 if prec == dda.DDA_FP64 else 1e-5), err
     return err
 
@@ -43,15 +47,15 @@ def sphere256():
     p = dda.Particle(occ, [2.0], 40.0, volume_corrected=True)
     assert p.n_occ == 8783848 and p.grid == (512, 512, 512)
     dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
-    yield p, occ
+    yield p, occ, _sampled_reference(p, occ, 2.0, 16, 256)
     p.close()
     torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
 def test_matvec_256_sampled(sphere256, prec_name):
-    p, occ = sphere256
-    _sampled_check(p, occ, 2.0, prec_name, 6, 256)
+    p, occ, ref = sphere256
+    _sampled_check(p, ref, prec_name)
 
 
 @pytest.fixture(scope="module")
@@ -64,15 +68,15 @@ def sphere536(sphere256):
     assert p.n_occ == 80630200 and p.grid == (1080, 1080, 1080)
     assert abs(p.kd - lattice.kd_volume_corrected(160.0, 80630200)) < 1e-15
     dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
-    yield p, occ
+    yield p, occ, _sampled_reference(p, occ, 1.05, 16, 536)
     p.close()
     torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
 def test_matvec_536_sampled(sphere536, prec_name):
-    p, occ = sphere536
-    _sampled_check(p, occ, 1.05, prec_name, 3, 536)
+    p, occ, ref = sphere536
+    _sampled_check(p, ref, prec_name)
 
 
 def test_solve_536_against_mie(sphere536):
@@ -83,7 +87,7 @@ def test_solve_536_against_mie(sphere536):
     y-polarised far field comes from the x-polarised solution rotated by 90
     degrees about z (the sphere's lattice is invariant under that rotation)."""
     torch, dda = need_gpu()
-    p, occ = sphere536
+    p, occ, _ = sphere536
     prop = np.array([[0.0, 0.0, 1.0]])
     pol = np.array([[1.0, 0.0, 0.0]])
     P = torch.zeros((1, 3, p.n_occ), dtype=torch.complex128, device="cuda")

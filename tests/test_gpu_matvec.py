@@ -7,10 +7,9 @@ the oracle computes one by one by the direct sum.
 import numpy as np
 import pytest
 
-from oracle import green
 from paper_0704_0037_gb300 import inputs
 
-from gpu_util import need_gpu, rel_l2, twin
+from gpu_util import direct_sum_rows, need_gpu, rel_l2, sample_dipoles, twin
 
 pytestmark = pytest.mark.gpu
 
@@ -136,7 +135,7 @@ ENGINE_CASES = [
 
 @pytest.mark.parametrize("name,occ", ENGINE_CASES, ids=[c[0] for c in ENGINE_CASES])
 @pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
-def test_register_engine_matches_stockham_and_oracle(name, occ, prec_name, monkeypatch):
+def test_register_engine_matches_stockham_and_oracle(name, occ, prec_name):
     """The register-resident passes (compiled lengths 32, 64, 128, 256, 270)
     and the shared-memory Stockham passes give the same product, and both match
     the oracle."""
@@ -146,12 +145,10 @@ def test_register_engine_matches_stockham_and_oracle(name, occ, prec_name, monke
     tol = 1e-12 if prec == dda.DDA_FP64 else 1e-5
     ys = {}
     for engine in ("auto", "stockham"):
-        if engine == "stockham":
-            monkeypatch.setenv("DDA_FFT_ENGINE", "stockham")
-        else:
-            monkeypatch.delenv("DDA_FFT_ENGINE", raising=False)
         p, prob = twin(occ, [1.3 + 0.02j], 0.5)
         with p:
+            dda.dda_set_fft_engine(p.h, dda.DDA_ENGINE_STOCKHAM if engine == "stockham"
+                                   else dda.DDA_ENGINE_AUTO)
             dda.dda_build_Dmatrix(p.h, prec)
             dda.dda_set_beta(p.h, dda.DDA_CLDR, [(0.6, 0.0, 0.8)], [(0.8, 0.0, -0.6)])
             x = inputs.random_vectors(13, 1, p.n_occ)
@@ -161,7 +158,6 @@ def test_register_engine_matches_stockham_and_oracle(name, occ, prec_name, monke
             yd2 = torch.empty_like(xd)
             dda.dda_matvec_adjoint(p.h, prec, xd, yd2)
             ys[engine] = (yd.cpu().numpy()[0], yd2.cpu().numpy()[0])
-    monkeypatch.delenv("DDA_FFT_ENGINE", raising=False)
     from oracle.fft_matvec import matvec_fft
     beta = prob.beta("cldr", (0.6, 0.0, 0.8), (0.8, 0.0, -0.6))
     ref = matvec_fft(prob.occ, beta, prob.dmat(), x[0])
@@ -187,17 +183,6 @@ def test_matvec_is_deterministic():
             assert torch.equal(y1, y2)
 
 
-def _sampled_reference(pos, beta, kd, x, idx):
-    """y_i = x_i - beta_i sum_j G(r_i - r_j) beta_j x_j for the sampled i only."""
-    u = beta * x
-    out = []
-    for i in idx:
-        g = green.green_tensor(pos[i][None, :] - pos, kd)        # (N, 3, 3), G(0) = 0
-        s = np.einsum("jmn,nj->m", g, u)
-        out.append(x[:, i] - beta[:, i] * s)
-    return np.stack(out, axis=1)
-
-
 @pytest.mark.slow
 @pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined", "fp64_pair"])
 def test_matvec_full_size_sampled(prec_name):
@@ -220,9 +205,9 @@ def test_matvec_full_size_sampled(prec_name):
         from oracle import dda as odda
         prob = odda.Problem(occ, [1.05], p.kd)
         beta = prob.beta("ldr", (0, 0, 1), (1, 0, 0))
-        rng = np.random.default_rng(5)
-        idx = np.concatenate([[0, p.n_occ - 1, p.n_occ // 2], rng.integers(0, p.n_occ, 9)])
-        ref = _sampled_reference(prob.pos, beta, prob.kd, x[0], idx)
+        idx = sample_dipoles(occ, 32, 5)
+        assert len(idx) == 32
+        ref = direct_sum_rows(prob.pos, beta, prob.kd, x[0], idx)
         scale = np.sqrt(np.mean(np.abs(ref) ** 2))
         err = np.abs(y[:, idx] - ref).max() / scale
         assert err <= (1e-5 if prec == dda.DDA_FP32_REFINED else 1e-12), err

@@ -30,12 +30,13 @@ def sphere16():
     p.close()
 
 
-def _solve(p, solver, prec, tol, maxiter=2000, inner_tol=1e-3, hist_len=0):
+def _solve(p, solver, prec, tol, maxiter=2000, inner_tol=1e-3, hist_len=0, inner_cap=0):
     torch, dda = need_gpu()
     P = torch.zeros((2, 3, p.n_occ), dtype=torch.complex128, device="cuda")
     st, info, hist = dda.dda_solve(p.h, dict(solver=dda.SOLVER[solver], pol=dda.DDA_LDR,
                                              prec=dda.PREC[prec], tol=tol, maxiter=maxiter,
-                                             inner_tol=inner_tol), PROP, POLS, P, hist_len)
+                                             inner_tol=inner_tol, inner_cap=inner_cap),
+                                   PROP, POLS, P, hist_len)
     return st, info, P, hist
 
 
@@ -246,17 +247,42 @@ def test_solve_is_deterministic(sphere16):
     assert bool((P1 == P2).all())
 
 
-def test_fp32_refined_switches_to_mixed_inner_solves(sphere16, monkeypatch):
+def test_fp32_refined_switches_to_mixed_inner_solves(sphere16):
     """Inner solves with complex64 Krylov vectors are capped per refinement
     step; past the cap the next inner solves keep complex128 vectors with
     double-float products.  A cap of 5 steps forces the switch here; the
     solve still reaches the FP64 tolerance and the exact solution."""
     torch, dda = need_gpu()
     p, prob, exact = sphere16
-    monkeypatch.setenv("DDA_C64_INNER_CAP", "5")
-    st, info, P, _ = _solve(p, "qmr_cs", "fp32_refined", 1e-9, maxiter=3000, inner_tol=1e-10)
+    st, info, P, _ = _solve(p, "qmr_cs", "fp32_refined", 1e-9, maxiter=3000, inner_tol=1e-10,
+                            inner_cap=5)
     assert st == 0, info
     for r in range(2):
         assert info[r]["rel_res_true"] < 1e-9
         assert info[r]["outer"] >= 2
     assert rel_l2(P.cpu().numpy(), exact) < 1e-7
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
+def test_residual_entry_point_against_oracle(sphere16, prec_name):
+    """dda_residual recomputes ||b - A x|| / ||b|| with the FP64 product from P
+    alone; it agrees with the oracle's residual of the same P (its own FFT
+    product, x = P / beta) and with the solver's exit value."""
+    torch, dda = need_gpu()
+    p, prob, exact = sphere16
+    st, info, P, _ = _solve(p, "qmr_cs", prec_name, 1e-5, maxiter=500, inner_tol=1e-3)
+    assert st == 0, info
+    res = dda.dda_residual(p.h, dda.DDA_LDR, P, PROP, POLS)
+    Pn = P.cpu().numpy()
+    for r in range(2):
+        beta = prob.beta("ldr", PROP[r], POLS[r])
+        b = system.rhs(beta, prob.pos, prob.kd, PROP[r], POLS[r])
+        x = Pn[r] / beta
+        ref = np.linalg.norm(b - prob.matvec(beta, "fft")(x)) / np.linalg.norm(b)
+        assert abs(res[r] - ref) <= 1e-6 * ref, (res[r], ref)
+        assert abs(res[r] - info[r]["rel_res_true"]) <= 1e-3 * ref
+        assert res[r] < 1e-5
+    # the exact (dense) solution has a residual at the rounding level
+    Pe = torch.from_numpy(exact).cuda()
+    res_e = dda.dda_residual(p.h, dda.DDA_LDR, Pe, PROP, POLS)
+    assert np.all(res_e < 1e-12)

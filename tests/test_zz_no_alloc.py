@@ -5,14 +5,17 @@ CUDA stream capture, processes that hand out device memory from their own
 fixed pool) use dda_farfield_noalloc instead of dda_scatter to get the
 scattering amplitude F(n).  It keeps its working memory in one fixed device
 array.  These tests call it through the C-ABI and compare it with
-dda_scatter on two calls in a row -- different polarizations and direction
-sets, so stale contents of the shared array would show -- check that repeat
-calls take no device memory, and that a request above the fixed limit is
-refused.  This file is collected last on purpose.
+dda_scatter (the allocating entry point) and with the CPU oracle's far field
+(the definition, summed over the dipoles in complex128) on two calls in a
+row -- different polarizations and direction sets, so stale contents of the
+shared array would show -- check that repeat calls take no device memory,
+and that a request above the fixed limit is refused.  This file is collected
+last on purpose.
 """
 import numpy as np
 import pytest
 
+from oracle import lattice, observables
 from paper_0704_0037_gb300 import inputs
 
 from gpu_util import need_gpu, rel_l2
@@ -24,6 +27,7 @@ def test_farfield_noalloc_matches_scatter_twice():
     torch, dda = need_gpu()
     occ = inputs.ellipsoid(18, 14, 11)
     prop, pol = [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]]
+    pos = lattice.positions(occ > 0)
     with dda.Particle(occ, [1.4 + 0.05j], 0.6) as p:
         free = []
         for call, seed in enumerate((1, 2, 3)):
@@ -38,7 +42,11 @@ def test_farfield_noalloc_matches_scatter_twice():
             dda.dda_farfield_noalloc(p.h, P, d_dev, F)
             torch.cuda.synchronize()
             free.append((free_before, torch.cuda.mem_get_info()[0]))
-            assert rel_l2(F.cpu().numpy(), F_ref[0]) <= 1e-12
+            Fn = F.cpu().numpy()
+            assert rel_l2(Fn, F_ref[0]) <= 1e-12
+            # the definition F(n) = -i kd^3 (I - n n) sum_j P_j exp(-i kd n.r_j)
+            F_or = observables.farfield(P.cpu().numpy().reshape(3, -1), pos, p.kd, dirs)
+            assert rel_l2(Fn, F_or) <= 1e-12
         # after the first call (which looks up the array's address), calls
         # take no device memory
         for before, after in free[1:]:
