@@ -57,10 +57,17 @@ def parse():
                     help="run only the warm-up and timed steps (for profilers)")
     ap.add_argument("--inner-tol", type=float, default=INNER_TOL)
     ap.add_argument("--n", type=int, default=N_SPHERE, help=argparse.SUPPRESS)
-    ap.add_argument("--workload", default="sphere134", choices=["sphere134", "batch128", "sphere"],
+    ap.add_argument("--workload", default="sphere134",
+                    choices=["sphere134", "batch128", "sphere", "baselines", "products"],
                     help="sphere134: the headline line; batch128: the seeded 128-particle "
                          "batch (16 right-hand sides each), all right-hand sides to 1e-5; "
-                         "sphere: one sphere (--n, --x, --m) solved once in each form")
+                         "sphere: one sphere (--n, --x, --m) solved once in each form; "
+                         "baselines (with --impl reference): the CPU oracle's timings; "
+                         "products: --products products of one precision (--prec) on the "
+                         "sphere (--n, --x, --m), for profilers")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df"],
+                    help="products workload: complex64, complex128 or double-float product")
+    ap.add_argument("--products", type=int, default=3, help="products workload: count")
     ap.add_argument("--x", type=float, default=X_SIZE, help="sphere workload: size parameter")
     ap.add_argument("--m", type=float, default=M_INDEX, help="sphere workload: refractive index")
     ap.add_argument("--maxiter", type=int, default=100000, help="sphere workload: iteration cap")
@@ -89,8 +96,10 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.idx = gpu_index
+    def __init__(self, gpu_id):
+        # gpu_id: the UUID ("GPU-...") of the device in use; nvidia-smi does
+        # not follow CUDA_VISIBLE_DEVICES, so an index could name another GPU
+        self.idx = gpu_id
         self.proc = None
         self.f = None
 
@@ -104,7 +113,7 @@ class Clocks:
             self.proc = None
 
     def stop(self):
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "gpu": self.idx}
         if self.proc is None:
             return out
         time.sleep(0.25)
@@ -133,6 +142,52 @@ class Clocks:
             out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
                        samples=len(sm))
         return out
+
+
+def load_mie(x, m):
+    """Mie Q_ext and S11 at 0..180 degrees for a sphere of the workloads from
+    tests/golden/mie_spheres.json (written by tests/golden/make_mie_golden.py
+    from the oracle's Mie code); None for a sphere not in the file."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "mie_spheres.json")) as f:
+            doc = json.load(f)
+    except Exception:
+        return None
+    for c in doc["spheres"]:
+        if abs(c["x"] - x) < 1e-12 and abs(c["m"] - m) < 1e-12:
+            return {"qext": c["qext"], "theta_deg": doc["theta_deg"], "s11": np.asarray(c["s11"])}
+    return None
+
+
+def mie_errors(mie, qext, s11):
+    """Sec. 3.1's error measures: relative Q_ext error, maximum and RMS (uniform
+    over the 181 angles, both ends included) relative S11 error."""
+    if mie is None:
+        return None
+    rel = np.abs(np.asarray(s11) - mie["s11"]) / mie["s11"]
+    return {"qext_mie": mie["qext"], "qext_rel_err": abs(qext - mie["qext"]) / mie["qext"],
+            "s11_max_rel_err": float(rel.max()), "s11_rms_rel_err": float(np.sqrt(np.mean(rel ** 2)))}
+
+
+def working_launches(name, traced, c64_products, df_products):
+    """Launches of a traced kernel that did work.  In the batched solver the
+    right-hand side runs in blocks of 8 steps; the steps after convergence
+    launch the complex64 product passes and QMR sweeps with every block
+    returning at once (device skip mask), so those kernels are averaged over
+    the products actually made; the double-float passes over the FP64-class
+    products; everything else over its traced launches."""
+    if name.endswith("_c64") or name.startswith("qmr_"):
+        return min(traced, c64_products) if c64_products > 0 else traced
+    if name.endswith("_df"):
+        return min(traced, df_products) if df_products > 0 else traced
+    return traced
+
+
+def gpu_uuid(device_index):
+    """nvidia-smi's id of a torch device: its UUID as 'GPU-<uuid>'."""
+    import torch
+    u = str(torch.cuda.get_device_properties(device_index).uuid)
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 # ---------------------------------------------------------------- roofline models
@@ -179,11 +234,11 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, or
-# dram__bytes.sum.per_second x duration) from one ncu capture of the kernel
-# as it is now; profiles/fk_zconv_c64_sphere134.md gives the command.  Only
-# valid for the 134^3 sphere on the 270^3 grid; None elsewhere.
-NCU_TRAFFIC_134 = {"p3_zconv_c64": 647.6e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# stored ncu capture of the kernel as it is now (not measured by this run),
+# with the capture it comes from.  Only valid for the 134^3 sphere on the
+# 270^3 grid; None elsewhere, and removed whenever the kernel changes.
+NCU_TRAFFIC_134 = {}
 
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe's nominal 1.25 TFLOP/s)
 
@@ -251,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = Clocks(local_rank if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0)
+    clocks = Clocks(gpu_uuid(local_rank))
     if rank == 0:
         clocks.start()
     dda.dda_trace(p.h, True)
@@ -269,6 +324,9 @@ def run_ours(args, rank, world, local_rank):
         mv64 += info["matvecs_fp64"]
         iters += info["iters"]
         last = (st, info, q)
+    # products that did work in the timed steps: complex64 (inner iterations)
+    # and FP64-class (double-float residual products)
+    c64_products, df_products = iters, mv64
     ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -285,16 +343,31 @@ def run_ours(args, rank, world, local_rank):
         return {"metric": METRIC, "value": value, "unit": UNIT, "steps_only": True,
                 "gpu_launches": int(trace.get("all_launches", (0, 0))[1])} if rank == 0 else None
 
-    # plain FP64 form on the same GPU (the comparison base of the metric)
+    # accuracy of the last timed step's solution, outside the timed region:
+    # the native FP64 residual of P (the refined form's own exit residual
+    # comes from the double-float product) and the errors against Mie
+    mie = load_mie(X_SIZE, M_INDEX) if n == N_SPHERE else None
+    res32_fp64 = float(dda.dda_residual(p.h, dda.DDA_LDR, P, prop, pol)[0])
+    M32, _, _ = dda.dda_mueller_plane_sym(p.h, dda.DDA_LDR, P, th)
+    acc32 = mie_errors(mie, float(last[2][0, 0]), M32[:, 0, 0])
+
+    # plain FP64 form on the same GPU (the comparison base of the metric),
+    # median of three solves
     opts64 = dict(opts, prec=dda.DDA_FP64)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    st64, info64, _ = dda.dda_solve(p.h, opts64, prop, pol, P)
-    e1.record(stream)
-    e1.synchronize()
-    fp64_ms = e0.elapsed_time(e1)
+    fp64_runs = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64, info64, _ = dda.dda_solve(p.h, opts64, prop, pol, P)
+        e1.record(stream)
+        e1.synchronize()
+        fp64_runs.append(e0.elapsed_time(e1))
+    fp64_ms = statistics.median(fp64_runs)
     F64, q64 = dda.dda_scatter(p.h, dda.DDA_LDR, P, prop, pol, dirs[:1])
+    res64_fp64 = float(dda.dda_residual(p.h, dda.DDA_LDR, P, prop, pol)[0])
+    M64, _, _ = dda.dda_mueller_plane_sym(p.h, dda.DDA_LDR, P, th)
+    acc64 = mie_errors(mie, float(q64[0, 0]), M64[:, 0, 0])
 
     # matvec-only rates (CUDA events, 10 products each, inputs > L2)
     rates = {}
@@ -325,14 +398,17 @@ def run_ours(args, rank, world, local_rank):
         ker = {k: v for k, v in trace.items() if k != "all_launches"}
         tot = sum(v[0] for v in ker.values())
         dom = max(ker, key=lambda k: ker[k][0])
-        dms, dcnt = ker[dom]
+        dms, dtraced = ker[dom]
+        dcnt = working_launches(dom, dtraced, c64_products, df_products)
         avg_s = dms / dcnt / 1e3
         md = models.get(dom)
         if md and md.get("bound") == "hbm":
             achieved = md["bytes"] / avg_s / 1e9
             tr = NCU_TRAFFIC_134.get(dom) if n == N_SPHERE else None
             roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": tr[0] if tr else None,
+                    "traffic_source": tr[1] if tr else "no stored capture of the current kernel",
                     "algorithmic_bytes": md["bytes"], "peak_note": f"hbm_gbs {peak_note}"}
         else:
             achieved = md["flops"] / avg_s / 1e12 if md else None
@@ -341,10 +417,13 @@ def run_ours(args, rank, world, local_rank):
                     "traffic": None, "peak_note": "FP64 ALU peak derived from unit counts and clock"}
         roof["share"] = dms / tot
         roof["avg_launch_ms"] = dms / dcnt
+        roof["launches_traced"] = dtraced
+        roof["launches_working"] = dcnt
         per_kernel = {}
-        for k, (kms, kc) in sorted(ker.items(), key=lambda kv: -kv[1][0]):
-            e = {"ms": round(kms, 3), "launches": kc, "share": round(kms / tot, 4),
-                 "avg_ms": round(kms / kc, 4)}
+        for k, (kms, kt) in sorted(ker.items(), key=lambda kv: -kv[1][0]):
+            kc = working_launches(k, kt, c64_products, df_products)
+            e = {"ms": round(kms, 3), "launches": kt, "working_launches": kc,
+                 "share": round(kms / tot, 4), "avg_ms": round(kms / kc, 4)}
             md = models.get(k)
             if md and md.get("bound") == "hbm":
                 e["hbm_gbs"] = round(md["bytes"] / (kms / kc / 1e3) / 1e9, 1)
@@ -363,14 +442,24 @@ def run_ours(args, rank, world, local_rank):
             "config": workload_config(n, "inputs larger than L2: 234 MB complex64 y-pass buffer, "
                                          "315 MB FP64 G grid, 121 MB D octant, per step"),
             "time_to_residual_s": t2r,
-            "fp64_form": {"time_to_residual_s": fp64_ms / 1e3, "status": info64[0]["status_name"],
+            "fp64_form": {"time_to_residual_s": fp64_ms / 1e3,
+                          "runs_s": [round(v / 1e3, 5) for v in fp64_runs],
+                          "status": info64[0]["status_name"],
                           "iters": info64[0]["iters"], "matvecs": info64[0]["matvecs"],
-                          "rel_res_true": info64[0]["rel_res_true"], "qext": float(q64[0, 0])},
+                          "rel_res_true": info64[0]["rel_res_true"],
+                          "rel_res_fp64_check": res64_fp64, "qext": float(q64[0, 0]),
+                          "vs_mie": acc64},
             "speedup_vs_fp64_form": (fp64_ms / 1e3) / t2r,
             "solve": {"status": info["status_name"], "iters_inner": info["iters"],
                       "outer": info["outer"], "matvecs": info["matvecs"],
                       "matvecs_fp64": info["matvecs_fp64"], "rel_res_true": info["rel_res_true"],
-                      "qext": float(q[0, 0]), "qabs": float(q[0, 1])},
+                      "rel_res_fp64_check": res32_fp64,
+                      "qext": float(q[0, 0]), "qabs": float(q[0, 1]), "vs_mie": acc32,
+                      "vs_fp64_form": {"qext_rel": abs(float(q[0, 0]) - float(q64[0, 0]))
+                                       / abs(float(q64[0, 0])),
+                                       "qabs_abs": abs(float(q[0, 1]) - float(q64[0, 1])),
+                                       "s11_max_rel": float(np.max(np.abs(M32[:, 0, 0] - M64[:, 0, 0])
+                                                                   / M64[:, 0, 0]))}},
             "matvec_only": {"c64_per_s": rates["c64"], "c128_per_s": rates["c128"],
                             "double_float_per_s": rates["df"],
                             "c64_effective_hbm_frac": c64_matvec_bytes * rates["c64"] / 1e9 / peaks["hbm_gbs"]},
@@ -454,9 +543,74 @@ def cpu_baseline(n):
                       f"on the {n}^3 sphere after one D build ({t_d:.1f} s, not in the rate)"}
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "processor\t: arm")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_reference_baselines(args):
+    """The CPU oracle's measured baseline: FFT products per second on spheres
+    of n = 16, 64, 128 and 134 (median of 5 after one warm-up; D built before),
+    and its time to a true residual of 1e-5 for the 16^3 sphere (x = 3, m = 1.5,
+    both polarisations; dense LU and QMR-CS) and the 134^3 sphere (x = 40,
+    m = 1.05, x-polarised; QMR-CS with the FFT product).  The 128^3 m = 2
+    sphere (tens of thousands of iterations) and the 536^3 sphere (host
+    memory) are products only."""
+    from oracle import dda as odda
+    from oracle import lattice, solvers, system
+    from oracle.fft_matvec import _WORKERS
+    from paper_0704_0037_gb300 import inputs
+    out = {"cores": _WORKERS, "cpu": cpu_model(), "products": {}, "time_to_1e-5": {}}
+    for n, xs, m in ((16, 3.0, 1.5), (64, 10.0, 1.5), (128, 20.0, 2.0), (134, 40.0, 1.05)):
+        occ = inputs.sphere(n)
+        prob = odda.Problem(occ, [m], lattice.kd_volume_corrected(xs, int((occ > 0).sum())))
+        t0 = time.perf_counter()
+        prob.dmat()
+        t_d = time.perf_counter() - t0
+        beta = prob.beta("ldr", (0, 0, 1), (1, 0, 0))
+        mv = prob.matvec(beta, "fft")
+        x = inputs.random_vectors(3, 1, prob.n_occ)[0]
+        mv(x)
+        ts = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            mv(x)
+            ts.append(time.perf_counter() - t0)
+        out["products"][str(n)] = {"n_occ": prob.n_occ, "grid": list(prob.grid),
+                                   "products_per_s": 1.0 / statistics.median(ts),
+                                   "d_build_s": t_d}
+    # 16^3 sphere: dense LU and QMR-CS, both polarisations
+    occ = inputs.sphere(16)
+    prob = odda.Problem(occ, [1.5], lattice.kd_volume_corrected(3.0, int((occ > 0).sum())))
+    for method in ("dense", "fft"):
+        t0 = time.perf_counter()
+        res = odda.simulate(prob, 3.0, "ldr", solver="qmr_cs", tol=TOL, method=method)
+        out["time_to_1e-5"][f"sphere16_{'dense_lu' if method == 'dense' else 'qmr_cs'}"] = {
+            "s": time.perf_counter() - t0, "rhs": 2,
+            "iters": [i.get("iters") for i in res["info"]], "qext": [float(v) for v in res["qext"]]}
+    # 134^3 sphere, x-polarised, QMR-CS
+    occ = inputs.sphere(134)
+    prob = odda.Problem(occ, [1.05], lattice.kd_volume_corrected(40.0, int((occ > 0).sum())))
+    t0 = time.perf_counter()
+    res = odda.simulate(prob, 40.0, "ldr", pols=((1, 0, 0),), solver="qmr_cs", tol=TOL)
+    out["time_to_1e-5"]["sphere134_qmr_cs"] = {
+        "s": time.perf_counter() - t0, "rhs": 1, "iters": res["info"][0].get("iters"),
+        "qext": float(res["qext"][0]), "note": "includes the D build"}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    if args.workload == "baselines":
+        return run_reference_baselines(args)
     n = args.n
     from oracle import dda as odda
     from oracle import lattice
@@ -510,7 +664,7 @@ def run_batch(args, rank, world, local_rank):
     # which converges the hard right-hand sides at several times the cost
     # per step; the --workload sphere runs measure that.)
     if args.batch_c64_only:
-        os.environ["DDA_C64_INNER_CAP"] = str(args.batch_maxiter)
+        opts["inner_cap"] = args.batch_maxiter
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -588,9 +742,14 @@ def run_sphere(args):
         e1.synchronize()
         F, q = dda.dda_scatter(p.h, dda.DDA_LDR, P, prop, pol, np.array([[0.0, 0.0, 1.0]]))
         i = info[0]
+        th = inputs.angles_deg(N_ANGLES)
+        Mm, _, _ = dda.dda_mueller_plane_sym(p.h, dda.DDA_LDR, P, th)
         out[name] = {"time_to_residual_s": e0.elapsed_time(e1) / 1e3, "status": i["status_name"],
                      "iters": i["iters"], "matvecs": i["matvecs"], "matvecs_fp64": i["matvecs_fp64"],
-                     "outer": i["outer"], "rel_res_true": i["rel_res_true"], "qext": float(q[0, 0])}
+                     "outer": i["outer"], "rel_res_true": i["rel_res_true"],
+                     "rel_res_fp64_check": float(dda.dda_residual(p.h, dda.DDA_LDR, P, prop, pol)[0]),
+                     "qext": float(q[0, 0]), "qabs": float(q[0, 1]),
+                     "vs_mie": mie_errors(load_mie(args.x, args.m), float(q[0, 0]), Mm[:, 0, 0])}
     p.close()
     r = (out["fp64"]["time_to_residual_s"] / out["fp32_refined"]["time_to_residual_s"]
          if "fp64" in out and "fp32_refined" in out else None)
@@ -602,6 +761,38 @@ def run_sphere(args):
                                    "QMR-CS to 1e-5", "n_box": args.n, "x": args.x, "m": args.m,
                        "n_occ": int(p.n_occ), "grid": list(p.grid), "maxiter": args.maxiter},
             "forms": out, "speedup_vs_fp64_form": r}
+
+
+def run_products(args):
+    """args.products interaction-matrix products (Eq. (3)) of one precision
+    on the sphere (n^3 box, x, m; LDR, incidence +z) applied to a seeded
+    random vector, after the D-matrix build and one untimed product; prints
+    the mean time per product (CUDA events).  A small, fixed launch sequence
+    for ncu captures of the product kernels."""
+    import torch
+    from paper_0704_0037_gb300 import build, dda, inputs
+    build.build()
+    occ = inputs.sphere(args.n)
+    p = dda.Particle(occ, [args.m], args.x, volume_corrected=True)
+    prec = {"fp32": dda.DDA_FP32_REFINED, "fp64": dda.DDA_FP64, "df": dda.DDA_FP64_PAIR}[args.prec]
+    dda.dda_build_Dmatrix(p.h, dda.DDA_FP64 if prec == dda.DDA_FP64 else dda.DDA_FP32_REFINED)
+    dda.dda_set_beta(p.h, dda.DDA_LDR, [(0.0, 0.0, 1.0)], [(1.0, 0.0, 0.0)])
+    dt = torch.complex64 if prec == dda.DDA_FP32_REFINED else torch.complex128
+    x = torch.from_numpy(inputs.random_vectors(1, 1, p.n_occ)).to("cuda", dt)
+    y = torch.empty_like(x)
+    dda.dda_matvec(p.h, prec, x, y)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.products):
+        dda.dda_matvec(p.h, prec, x, y)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / max(1, args.products)
+    p.close()
+    return {"workload": "products", "n_box": args.n, "grid": list(p.grid), "prec": args.prec,
+            "products": args.products, "ms_per_product": ms}
 
 
 def main():
@@ -618,6 +809,9 @@ def main():
     if world > 1:
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group(backend="nccl")
+    if args.workload == "products":
+        print(json.dumps(run_products(args)))
+        return
     if args.workload == "sphere":
         if rank == 0:
             print(json.dumps(run_sphere(args)))
