@@ -20,6 +20,10 @@ recurrence residual history (relative) and the true relative residual at exit.
 import numpy as np
 
 OK, NOT_CONVERGED, BREAKDOWN = "ok", "not_converged", "breakdown"
+# The paper's solvers have no look-ahead (Sec. 2), so a vanishing bilinear
+# form u^T u stops QMR-CS and Bi-CG-CS.  In floating point an exact zero shows
+# up as rounding noise: |u^T u| <= BREAK ||u||^2 counts as zero.
+BREAK = 1e-12
 
 
 def dotu(a, b):
@@ -79,7 +83,7 @@ def qmr_cs(matvec, b, tol=1e-5, maxiter=10000):
     for k in range(1, maxiter + 1):
         v = vt / rho
         delta = dotu(v, v)
-        if abs(delta) < 1e-30:
+        if abs(delta) <= BREAK * norm2(v) ** 2:
             status = BREAKDOWN
             break
         p = v if k == 1 else v - (rho * delta / eps_prev) * p
@@ -128,7 +132,7 @@ def bicg_cs(matvec, b, tol=1e-5, maxiter=10000):
     for k in range(1, maxiter + 1):
         q = matvec(p); nmv += 1
         mu = dotu(p, q)
-        if mu == 0 or rho == 0:
+        if mu == 0 or abs(rho) <= BREAK * norm2(r) ** 2:
             status = BREAKDOWN
             hist.append(hist[-1])
             break

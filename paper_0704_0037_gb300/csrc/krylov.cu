@@ -26,6 +26,10 @@
 namespace dda {
 
 constexpr int kNB = 1024;     // max blocks of a vector kernel (partials per slot)
+// Breakdown of the bilinear-form solvers (QMR-CS, Bi-CG-CS; no look-ahead):
+// a bilinear form u^T u at the rounding level of the Hermitian one,
+// |u^T u| <= 1e-12 ||u||^2, counts as zero (kBreak2 is the square of 1e-12)
+constexpr double kBreak2 = 1e-24;
 constexpr int kSlots = 8;     // doubles per block in the partials array
 constexpr int kVT = 256;      // threads of vector kernels
 constexpr long long kPS = (long long)kSlots * kNB;   // partials per right-hand side
@@ -357,7 +361,7 @@ __global__ void k_qmr_init(Scal* s, const double* part, int nb, double tol, cons
   q.beta = mk<double>(0.0, 0.0);
   if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
   else if (!isfinite(bn2) || !cfinite(bb)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
-  else if (sqrt(cabs2(q.delta)) < 1e-30) { s->done = 1; s->status = DDA_BREAKDOWN; }
+  else if (cabs2(q.delta) <= kBreak2) { s->done = 1; s->status = DDA_BREAKDOWN; }
   if (off && off[rr]) { s->done = 1; s->status = DDA_OK; }
   if (mask) mask[rr] = s->done;
 }
@@ -438,7 +442,7 @@ __device__ void qmr_b_fin(Scal* s, const double* part, int nb, int* mask, int rr
     q.inv_rho = 1.0 / rho_n;
     q.cp = scale<double>(cdivd(delta, q.eps_new), rho_n);
     q.delta = delta;
-    if (sqrt(cabs2(delta)) < 1e-30) s->half = 1;   // next v^T v vanishes: breakdown after this step
+    if (cabs2(delta) <= kBreak2) s->half = 1;      // next v^T v vanishes: breakdown after this step
   }
   q.rho = rho_n;
   q.eps = q.eps_new;
@@ -563,7 +567,7 @@ __global__ void k_bicg_init(Scal* s, const double* part, int nb, double tol) {
   s->rho = bb;
   if (bn2 == 0.0) { s->done = 1; s->status = DDA_OK; s->res = 0.0; }
   else if (!isfinite(bn2)) { s->done = 1; s->status = DDA_ERR_NONFINITE; }
-  else if (cabs2(bb) == 0.0) { s->done = 1; s->status = DDA_BREAKDOWN; }
+  else if (cabs2(bb) <= kBreak2 * bn2 * bn2) { s->done = 1; s->status = DDA_BREAKDOWN; }
 }
 
 template <typename R>
@@ -609,7 +613,7 @@ __global__ void k_bicg_b(Scal* s, const double* part, int nb) {
   s->res = res;
   if (!isfinite(res) || !cfinite(rn)) { s->status = DDA_ERR_NONFINITE; s->done = 1; return; }
   if (res < s->tol) { s->status = DDA_OK; s->done = 1; return; }
-  if (cabs2(rn) == 0.0) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
+  if (cabs2(rn) <= kBreak2 * r2 * r2) { s->status = DDA_BREAKDOWN; s->done = 1; return; }
   s->bstep = cdivd(rn, s->rho);
   s->rho = rn;
 }

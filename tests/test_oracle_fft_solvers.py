@@ -184,3 +184,18 @@ def test_identity_system_converges_in_one_step():
     for name in solvers.SOLVERS:
         x, info = solvers.SOLVERS[name](lambda v: v, b, tol=1e-12)
         assert np.allclose(x, b, rtol=1e-15) and info["iters"] == 1
+
+
+def test_bilinear_breakdown_single_dipole_circular_polarisation():
+    """One dipole (A = I) under circular polarisation along z: b^T b = 0, so
+    QMR-CS and Bi-CG-CS break down at their first step (no look-ahead, Sec. 2);
+    Bi-CGSTAB (Hermitian products) solves it, x = b."""
+    e = np.array([1.0, 1j, 0.0]) / np.sqrt(2.0)
+    b = (0.7 + 0.2j) * e.reshape(3, 1)
+    ident = lambda v: v.copy()          # noqa: E731
+    for name in ("qmr_cs", "bicg_cs"):
+        _, info = solvers.SOLVERS[name](ident, b, tol=1e-10, maxiter=10)
+        assert info["status"] == solvers.BREAKDOWN, (name, info)
+    x, info = solvers.SOLVERS["bicgstab"](ident, b, tol=1e-10, maxiter=10)
+    assert info["status"] == solvers.OK
+    assert np.allclose(x, b, rtol=0, atol=1e-15)
