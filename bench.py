@@ -544,11 +544,16 @@ def cpu_baseline(n):
 
 
 def cpu_model():
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu part", "processor\t: arm")):
+                key = line.lower()
+                if key.startswith("model name"):
                     return line.split(":", 1)[1].strip()
+                if key.startswith("cpu part"):
+                    part = line.split(":", 1)[1].strip()
+                    return f"{arm_parts.get(part, 'Arm')} (CPU part {part})"
     except OSError:
         pass
     import platform
