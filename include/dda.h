@@ -170,11 +170,38 @@ typedef struct {
   double tol;           /* stop when ||b - A x||_2 / ||b||_2 < tol (Sec. 2: 1e-5) */
   int maxiter;          /* iterations per RHS (inner iterations summed for FP32)  */
   double inner_tol;     /* FP32_REFINED: relative tolerance of each inner solve   */
-  int checkpoint_every; /* reserved, 0                                            */
+  int checkpoint_every; /* > 0: save the solve's state into checkpoint_host
+                           every this many iterations (QMR-CS without a
+                           residual history only; FP64: at the first host
+                           synchronisation, every 8 steps, at or after each
+                           multiple; FP32_REFINED: between refinement steps,
+                           at the first one after each multiple of inner
+                           iterations); 0: none                                */
   int inner_cap;        /* FP32_REFINED: complex64 steps an inner solve may take
                            before the later inner solves switch to complex128
                            vectors and FP64-class products; <= 0: 1000          */
+  void* checkpoint_host;       /* host buffer of the solver state (or NULL)      */
+  long long checkpoint_bytes;  /* its size, >= dda_checkpoint_bytes()            */
+  int checkpoint_stop;  /* nonzero: return right after the first save; the
+                           right-hand sides not yet converged report
+                           DDA_NOT_CONVERGED and P holds the current iterate   */
+  int resume;           /* nonzero: continue the solve saved in checkpoint_host
+                           (same handle lattice, precision, right-hand sides
+                           and incidences, else DDA_ERR_ARG) instead of starting
+                           from x0 = 0; maxiter counts the iterations before the
+                           save too, and the continued solve is the one an
+                           uninterrupted solve would have done, bit for bit    */
 } dda_solve_opts;
+
+/*
+ * dda_checkpoint_bytes -- size of the host buffer that dda_solve_opts'
+ * checkpoints of a QMR-CS solve of nrhs right-hand sides in precision prec
+ * need on this handle (ADDA's checkpoints, Sec. 2, let a long solve be
+ * stopped and resumed; here the caller owns the buffer and may write it to
+ * a file).  FP64: about 8 x nrhs x 3 N_occ x 16 bytes; FP32_REFINED: about
+ * 3 x nrhs x 3 N_occ x 16 bytes.  DDA_ERR_ARG on bad arguments.
+ */
+int dda_checkpoint_bytes(dda_t h, int prec, int nrhs, long long* bytes);
 
 typedef struct {
   int status;           /* enum dda_status of this RHS                           */

@@ -477,6 +477,27 @@ extern "C" int dda_matvec_adjoint(dda_t h, int prec, const void* x, void* y, int
   return matvec_common(h, prec, x, y, nrhs, true);
 }
 
+// checkpoint options: a host buffer large enough, and only where the
+// batched QMR-CS driver runs
+static int check_ckpt_opts(dda_t h, const dda_solve_opts* o, int nrhs, bool batched) {
+  if (o->checkpoint_every < 0) return dda_fail(h, DDA_ERR_ARG, "checkpoint_every must be >= 0");
+  if (o->checkpoint_every == 0 && !o->resume) return DDA_OK;
+  if (!batched)
+    return dda_fail(h, DDA_ERR_ARG, "checkpoints are taken by QMR-CS without a residual history");
+  if (!o->checkpoint_host ||
+      o->checkpoint_bytes < dda_checkpoint_bytes_internal(h, o->prec, nrhs))
+    return dda_fail(h, DDA_ERR_ARG, "checkpoint buffer missing or smaller than dda_checkpoint_bytes");
+  return DDA_OK;
+}
+
+extern "C" int dda_checkpoint_bytes(dda_t h, int prec, int nrhs, long long* bytes) {
+  if (!h) return DDA_ERR_ARG;
+  if (!bytes || nrhs < 1 || (prec != DDA_FP64 && prec != DDA_FP32_REFINED))
+    return dda_fail(h, DDA_ERR_ARG, "bad dda_checkpoint_bytes arguments");
+  *bytes = dda_checkpoint_bytes_internal(h, prec, nrhs);
+  return DDA_OK;
+}
+
 extern "C" int dda_solve(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                          const double* pol, void* P_dev, double* hist, int hist_len,
                          dda_solve_info* info) {
@@ -494,8 +515,10 @@ extern "C" int dda_solve(dda_t h, const dda_solve_opts* o, int nrhs, const doubl
   // QMR-CS without a residual history runs on the batched driver (same
   // arithmetic; the host reads the scalars every 8 steps instead of every
   // step, and converged right-hand sides skip their products)
-  if (o->solver == DDA_QMR_CS && !hist)
-    return dda_solve_batch_internal(h, o, nrhs, prop, pol, P_dev, info);
+  const bool batched = o->solver == DDA_QMR_CS && !hist;
+  const int rc = check_ckpt_opts(h, o, nrhs, batched);
+  if (rc != DDA_OK) return rc;
+  if (batched) return dda_solve_batch_internal(h, o, nrhs, prop, pol, P_dev, info);
   return dda_solve_internal(h, o, nrhs, prop, pol, P_dev, hist, hist_len, info);
 }
 
@@ -512,6 +535,8 @@ extern "C" int dda_solve_batch(dda_t h, const dda_solve_opts* o, int nrhs, const
   if (!h->w64.have_D) return dda_fail(h, DDA_ERR_STATE, "FP64 D-matrix not built");
   if (o->prec == DDA_FP32_REFINED && !h->w32.have_D)
     return dda_fail(h, DDA_ERR_STATE, "FP32 D-matrix not built");
+  const int rc = check_ckpt_opts(h, o, nrhs, true);
+  if (rc != DDA_OK) return rc;
   return dda_solve_batch_internal(h, o, nrhs, prop, pol, P_dev, info);
 }
 

@@ -186,6 +186,8 @@ int ensure_d64(dda_t h);
 int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                              const double* pol, void* P_dev, dda_solve_info* info);
 void batch_free(dda_t h);
+// bytes of the host image of a batched QMR-CS solve (krylov.cu)
+long long dda_checkpoint_bytes_internal(dda_t h, int prec, int nrhs);
 // ||b - A x|| / ||b|| per right-hand side with x = P / beta, native FP64 product
 int dda_residual_internal(dda_t h, int presc, int nrhs, const double* prop, const double* pol,
                           const void* P_dev, double* res);

@@ -18,6 +18,8 @@
 // also the true residual the stop test uses.
 #include <chrono>
 #include <cmath>
+#include <cstring>
+#include <functional>
 
 #include <cstdlib>
 
@@ -1438,7 +1440,12 @@ int bsync(BRun& b) {
 template <typename R>
 int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double tol,
                     const double* tols_dev, const int* off_dev, int maxiter, int* steps_out,
-                    bool df_products = false) {
+                    bool df_products = false, int resume_k = -1,
+                    const std::function<int(int)>* on_sync = nullptr) {
+  // resume_k >= 0: the vectors, x, the scalars and the skip mask hold a
+  // saved state after resume_k steps; continue from there.  on_sync(k) runs
+  // at every host synchronisation (every kSyncEvery steps): a negative
+  // status aborts, 1 stops the solve after a checkpoint.
   // df_products (R = double): the products in double-float from the
   // double-float D-matrix (FP64-class accuracy), Krylov vectors and scalars in
   // complex128
@@ -1451,10 +1458,12 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
   double* part = m->part;
   cpx<R>*v = vec[0], *p = vec[1], *pt = vec[2], *d = vec[3], *sv = vec[4], *r = vec[5];
   const dim3 vg(nb, nr);
-  k_norms<R><<<vg, kVT, 0, st>>>(rhs, n, part, nullptr); count_launch();
-  k_qmr_init<<<nr, kVT, 0, st>>>(s, part, nb, tol, tols_dev, off_dev, m->mask); count_launch();
-  k_qmr_start<R><<<vg, kVT, 0, st>>>(rhs, v, p, r, x, d, sv, n, s); count_launch();
-  LK(h);
+  if (resume_k < 0) {
+    k_norms<R><<<vg, kVT, 0, st>>>(rhs, n, part, nullptr); count_launch();
+    k_qmr_init<<<nr, kVT, 0, st>>>(s, part, nb, tol, tols_dev, off_dev, m->mask); count_launch();
+    k_qmr_start<R><<<vg, kVT, 0, st>>>(rhs, v, p, r, x, d, sv, n, s); count_launch();
+    LK(h);
+  }
   RK(bsync(b));
   if (b.stall) {
     b.best.assign(nr, 1e300);
@@ -1462,7 +1471,7 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
   }
   Work<R>& w = work<R>(h);
   const cpx<R>* beta = w.beta;
-  int k = 0;
+  int k = resume_k > 0 ? resume_k : 0;
   bool active = false;
   for (int i = 0; i < nr; ++i) active = active || !m->hs[i].done;
   while (active && k < maxiter) {
@@ -1515,13 +1524,52 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
       }
       active = true;
     }
+    if (on_sync && active) {
+      const int rc = (*on_sync)(k);
+      if (rc < 0) return rc;
+      if (rc == 1) break;
+    }
   }
   *steps_out = k;
   return DDA_OK;
 }
 
+// ---------------------------------------------------------------- checkpoints
+// Host image of a batched QMR-CS solve (dda_solve_opts.checkpoint_*): a
+// header, the incidence of every right-hand side, then
+//   FP64: the six QMR vectors, b and x ([8][nrhs][3 N_occ] complex128), the
+//         device scalars of each right-hand side and the skip mask;
+//   FP32_REFINED (saved between refinement steps): b, x, r ([3][nrhs][3 N_occ]
+//         complex128) and the per-right-hand-side counters and norms.
+struct CkptHead {
+  char magic[8];
+  int prec, nrhs, k, it_out, left, mixed;
+  long long n;
+  long long bytes;
+};
+constexpr char kCkptMagic[8] = {'D', 'D', 'A', 'C', 'K', 'P', 'T', '1'};
+
+long long ckpt_bytes(int prec, int nrhs, long long n) {
+  long long b = (long long)sizeof(CkptHead) + (long long)nrhs * 9 * sizeof(double);
+  if (prec == DDA_FP64) b += 8LL * nrhs * n * (long long)sizeof(c128) + (long long)nrhs * (sizeof(Scal) + sizeof(int));
+  else b += 3LL * nrhs * n * (long long)sizeof(c128) + (long long)nrhs * (5 * sizeof(int) + 3 * sizeof(double));
+  return b;
+}
+
+// Sequential reader/writer over the caller's host buffer.
+struct CkptCursor {
+  unsigned char* p;
+  long long at = 0;
+  void put(const void* src, size_t nbytes) { std::memcpy(p + at, src, nbytes); at += (long long)nbytes; }
+  void get(void* dst, size_t nbytes) { std::memcpy(dst, p + at, nbytes); at += (long long)nbytes; }
+};
+
 }  // namespace
 }  // namespace dda
+
+long long dda_checkpoint_bytes_internal(dda_t h, int prec, int nrhs) {
+  return ckpt_bytes(prec, nrhs, 3 * h->g.n_occ);
+}
 
 void batch_free(dda_t h) {
   if (h && h->bm) {
@@ -1589,7 +1637,7 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
     r64 = x64 + (size_t)nrhs * n;
     w64 = r64 + (size_t)nrhs * n;
   }
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = 0; r < nrhs && !(o->resume && !refined); ++r) {
     Wave wv;
     for (int q = 0; q < 3; ++q) wv.a[q] = prop[3 * r + q];
     for (int q = 0; q < 6; ++q) wv.e[q] = pol[6 * r + q];
@@ -1598,12 +1646,68 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
   LK(h);
   const dim3 vg(b.nb, nrhs);
   std::vector<double> bn(nrhs, 0.0);
+  // checkpoint image: header and incidences, checked on resume
+  const long long ck_need = ckpt_bytes(o->prec, nrhs, n);
+  CkptHead ck_head{};
+  CkptCursor ck{(unsigned char*)o->checkpoint_host};
+  if (o->resume) {
+    ck.get(&ck_head, sizeof(ck_head));
+    std::vector<double> inc((size_t)9 * nrhs);
+    ck.get(inc.data(), inc.size() * sizeof(double));
+    bool same = std::memcmp(ck_head.magic, kCkptMagic, 8) == 0 && ck_head.prec == o->prec &&
+                ck_head.nrhs == nrhs && ck_head.n == n && ck_head.bytes == ck_need;
+    for (int r = 0; same && r < nrhs; ++r)
+      same = std::memcmp(inc.data() + 9 * r, prop + 3 * r, 3 * sizeof(double)) == 0 &&
+             std::memcmp(inc.data() + 9 * r + 3, pol + 6 * r, 6 * sizeof(double)) == 0;
+    if (!same)
+      return dda_fail(h, DDA_ERR_ARG, "checkpoint does not match this handle, precision or incidence");
+  }
+  auto ck_begin = [&](int k, int it_out, int left, int mixed) {
+    ck.at = 0;
+    CkptHead hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.prec = o->prec; hd.nrhs = nrhs; hd.k = k; hd.it_out = it_out; hd.left = left; hd.mixed = mixed;
+    hd.n = n; hd.bytes = ck_need;
+    ck.put(&hd, sizeof(hd));
+    for (int r = 0; r < nrhs; ++r) {
+      ck.put(prop + 3 * r, 3 * sizeof(double));
+      ck.put(pol + 6 * r, 6 * sizeof(double));
+    }
+  };
+  int ck_next = o->checkpoint_every > 0 ? o->checkpoint_every : 0;
+  bool ck_stopped = false;
   if (!refined) {
     c128* base = (c128*)m->sv;
     c128* vec[nvec];
     for (int i = 0; i < nvec; ++i) vec[i] = base + (size_t)i * nrhs * n;
     int steps = 0;
-    RK(run_qmr_batched<double>(b, b64, x64, vec, o->tol, nullptr, nullptr, o->maxiter, &steps));
+    const size_t vbytes = (size_t)(nvec + 2) * nrhs * n * sizeof(c128);   // vectors, b, x
+    int resume_k = -1;
+    if (o->resume) {
+      DDA_CK(h, cudaMemcpyAsync(base, ck.p + ck.at, vbytes, cudaMemcpyHostToDevice, st));
+      ck.at += (long long)vbytes;
+      DDA_CK(h, cudaMemcpyAsync(m->ds, ck.p + ck.at, nrhs * sizeof(Scal), cudaMemcpyHostToDevice, st));
+      ck.at += (long long)(nrhs * sizeof(Scal));
+      DDA_CK(h, cudaMemcpyAsync(m->mask, ck.p + ck.at, nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+      DDA_CK(h, cudaStreamSynchronize(st));
+      resume_k = ck_head.k;
+      while (ck_next > 0 && ck_next <= resume_k) ck_next += o->checkpoint_every;
+    }
+    std::function<int(int)> save = [&](int k) -> int {
+      if (ck_next <= 0 || k < ck_next) return 0;
+      while (ck_next <= k) ck_next += o->checkpoint_every;
+      ck_begin(k, 0, 0, 0);
+      DDA_CK(h, cudaMemcpyAsync(ck.p + ck.at, base, vbytes, cudaMemcpyDeviceToHost, st));
+      ck.at += (long long)vbytes;
+      DDA_CK(h, cudaMemcpyAsync(ck.p + ck.at, m->ds, nrhs * sizeof(Scal), cudaMemcpyDeviceToHost, st));
+      ck.at += (long long)(nrhs * sizeof(Scal));
+      DDA_CK(h, cudaMemcpyAsync(ck.p + ck.at, m->mask, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+      DDA_CK(h, cudaStreamSynchronize(st));
+      if (o->checkpoint_stop) { ck_stopped = true; return 1; }
+      return 0;
+    };
+    RK(run_qmr_batched<double>(b, b64, x64, vec, o->tol, nullptr, nullptr, o->maxiter, &steps, false,
+                               resume_k, ck_next > 0 ? &save : nullptr));
     for (int r = 0; r < nrhs; ++r) {
       status[r] = m->hs[r].status;
       iters[r] = m->hs[r].iters;
@@ -1649,7 +1753,57 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
     bool mixed = false;
     c128* mvec[nvec] = {};
     c128 *xm = nullptr, *rhsm = nullptr;
-    for (int it_out = 0; it_out < 64 && left > 0; ++it_out) {
+    // inner solves with complex128 Krylov vectors and FP64-class products
+    auto make_mixed = [&]() -> int {
+      const size_t need = (size_t)nrhs * n * (nvec + 2) * sizeof(c128);
+      if (m->sv2_bytes < need) {
+        dev_free(m->sv2, h->stream);
+        m->sv2 = nullptr; m->sv2_bytes = 0;
+        if (dev_malloc(&m->sv2, need) != cudaSuccess) {
+          cudaGetLastError();
+          return dda_fail(h, DDA_ERR_OOM, "mixed inner-solve vectors");
+        }
+        m->sv2_bytes = need;
+      }
+      c128* b2 = (c128*)m->sv2;
+      for (int i = 0; i < nvec; ++i) mvec[i] = b2 + (size_t)i * nrhs * n;
+      xm = b2 + (size_t)nvec * nrhs * n;
+      rhsm = xm + (size_t)nrhs * n;
+      mixed = true;
+      return DDA_OK;
+    };
+    // the refinement state between outer steps: b, x, r on the device, the
+    // per-right-hand-side counters and norms on the host
+    const size_t sbytes = (size_t)3 * nrhs * n * sizeof(c128);
+    std::vector<int> fin_i(nrhs);
+    auto ck_ints = [&](bool save) {
+      for (int r = 0; r < nrhs; ++r) fin_i[r] = fin_[r];
+      int* arr[5] = {fin_i.data(), status.data(), iters.data(), outer.data(), mv64.data()};
+      for (int* a : arr) {
+        if (save) ck.put(a, nrhs * sizeof(int));
+        else ck.get(a, nrhs * sizeof(int));
+      }
+      double* dar[3] = {rn.data(), bn.data(), res_true.data()};
+      for (double* a : dar) {
+        if (save) ck.put(a, nrhs * sizeof(double));
+        else ck.get(a, nrhs * sizeof(double));
+      }
+      for (int r = 0; r < nrhs; ++r) fin_[r] = (char)fin_i[r];
+    };
+    int it_out0 = 0;
+    if (o->resume) {
+      DDA_CK(h, cudaMemcpyAsync(b64, ck.p + ck.at, sbytes, cudaMemcpyHostToDevice, st));
+      ck.at += (long long)sbytes;
+      DDA_CK(h, cudaStreamSynchronize(st));
+      ck_ints(false);
+      left = ck_head.left;
+      it_out0 = ck_head.it_out;
+      if (ck_head.mixed) RK(make_mixed());
+      int kmax = 0;
+      for (int r = 0; r < nrhs; ++r) kmax = std::max(kmax, iters[r]);
+      while (ck_next > 0 && ck_next <= kmax) ck_next += o->checkpoint_every;
+    }
+    for (int it_out = it_out0; it_out < 64 && left > 0; ++it_out) {
       bool any = false;
       for (int r = 0; r < nrhs; ++r) {
         if (!fin_[r] && rn[r] / bn[r] < o->tol) { fin_[r] = 1; status[r] = DDA_OK; }
@@ -1721,21 +1875,20 @@ int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const d
       if (!mixed && capped && unfinished) {
         // switch the remaining inner solves to complex128 Krylov vectors and
         // FP64-class products
-        const size_t need = (size_t)nrhs * n * (nvec + 2) * sizeof(c128);
-        if (m->sv2_bytes < need) {
-          dev_free(m->sv2, h->stream);
-          m->sv2 = nullptr; m->sv2_bytes = 0;
-          if (dev_malloc(&m->sv2, need) != cudaSuccess) {
-            cudaGetLastError();
-            return dda_fail(h, DDA_ERR_OOM, "mixed inner-solve vectors");
-          }
-          m->sv2_bytes = need;
-        }
-        c128* b2 = (c128*)m->sv2;
-        for (int i = 0; i < nvec; ++i) mvec[i] = b2 + (size_t)i * nrhs * n;
-        xm = b2 + (size_t)nvec * nrhs * n;
-        rhsm = xm + (size_t)nrhs * n;
-        mixed = true;
+        RK(make_mixed());
+      }
+      // checkpoint between refinement steps, at the first boundary after
+      // every checkpoint_every inner iterations
+      int kmax = 0;
+      for (int r = 0; r < nrhs; ++r) kmax = std::max(kmax, iters[r]);
+      if (ck_next > 0 && kmax >= ck_next) {
+        while (ck_next <= kmax) ck_next += o->checkpoint_every;
+        ck_begin(0, it_out + 1, left, mixed ? 1 : 0);
+        DDA_CK(h, cudaMemcpyAsync(ck.p + ck.at, b64, sbytes, cudaMemcpyDeviceToHost, st));
+        ck.at += (long long)sbytes;
+        DDA_CK(h, cudaStreamSynchronize(st));
+        ck_ints(true);
+        if (o->checkpoint_stop) { ck_stopped = true; break; }
       }
     }
     for (int r = 0; r < nrhs; ++r) res_recur[r] = res_true[r];

@@ -23,6 +23,7 @@ extern "C" int dda_solve_many(int n_part, dda_t const* hs, const dda_solve_opts*
     return DDA_ERR_ARG;
   for (int i = 0; i < n_part; ++i)
     if (!hs[i] || nrhs[i] < 1 || !prop[i] || !pol[i] || !P[i] || !info[i]) return DDA_ERR_ARG;
+  if (o->checkpoint_every != 0 || o->resume) return DDA_ERR_ARG;   // one buffer cannot hold many solves
   for (int i = 0; i < n_part; ++i)
     for (int j = 0; j < i; ++j)
       if (hs[i] == hs[j]) return DDA_ERR_ARG;          // a handle is not thread-safe

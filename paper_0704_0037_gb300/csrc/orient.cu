@@ -75,6 +75,8 @@ extern "C" int dda_orientation_average(dda_t h, const dda_solve_opts* o, int n_a
     return dda_fail(h, DDA_ERR_ARG, "orientation averaging needs a polarisation-independent "
                                     "polarizability (CM, RR or CLDR); LDR depends on it");
   if (o->pol < DDA_CM || o->pol > DDA_CLDR) return dda_fail(h, DDA_ERR_ARG, "unknown prescription");
+  if (o->checkpoint_every != 0 || o->resume)
+    return dda_fail(h, DDA_ERR_ARG, "orientation averaging takes no checkpoints");
   if (o->solver < DDA_QMR_CS || o->solver > DDA_CGNR || !(o->tol > 0.0) || o->maxiter < 1 ||
       (o->prec != DDA_FP64 && o->prec != DDA_FP32_REFINED) ||
       (o->prec == DDA_FP32_REFINED && !(o->inner_tol > 0.0 && o->inner_tol < 1.0)))

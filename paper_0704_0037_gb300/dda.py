@@ -40,7 +40,7 @@ EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec"
            "dda_farfield_noalloc", "dda_trace",
            "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
            "dda_free", "dda_release_cached_memory", "dda_set_fft_engine", "dda_set_memory_limit",
-           "dda_memory_in_use", "dda_residual")
+           "dda_memory_in_use", "dda_residual", "dda_checkpoint_bytes")
 
 
 class DDAError(RuntimeError):
@@ -52,7 +52,9 @@ class DDAError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("pol", ctypes.c_int), ("prec", ctypes.c_int),
                 ("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("checkpoint_every", ctypes.c_int), ("inner_cap", ctypes.c_int)]
+                ("checkpoint_every", ctypes.c_int), ("inner_cap", ctypes.c_int),
+                ("checkpoint_host", ctypes.c_void_p), ("checkpoint_bytes", ctypes.c_longlong),
+                ("checkpoint_stop", ctypes.c_int), ("resume", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -101,6 +103,7 @@ def lib():
                             ctypes.POINTER(ctypes.POINTER(SolveInfo)), _ip, ctypes.POINTER(_ip)], _ip),
         "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
         "dda_residual": ([_vp, _ip, _ip, _dp, _dp, _vp, _dp], _ip),
+        "dda_checkpoint_bytes": ([_vp, _ip, _ip, ctypes.POINTER(ctypes.c_longlong)], _ip),
         "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane_full": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_asymmetry": ([_ip, _dp, _dp, _dp, _dp, _dp], _ip),
@@ -227,10 +230,19 @@ def dda_matvec_adjoint(h, prec, x, y, nrhs=1):
 
 def _opts(opts):
     if isinstance(opts, dict):
-        return SolveOpts(solver=opts.get("solver", DDA_QMR_CS), pol=opts.get("pol", DDA_LDR),
+        o = SolveOpts(solver=opts.get("solver", DDA_QMR_CS), pol=opts.get("pol", DDA_LDR),
                          prec=opts.get("prec", DDA_FP64), tol=opts.get("tol", 1e-5),
                          maxiter=opts.get("maxiter", 10000), inner_tol=opts.get("inner_tol", 1e-3),
-                         checkpoint_every=0, inner_cap=opts.get("inner_cap", 0))
+                         checkpoint_every=opts.get("checkpoint_every", 0),
+                         inner_cap=opts.get("inner_cap", 0))
+        buf = opts.get("checkpoint")
+        if buf is not None:
+            # a writable numpy uint8 array owned by the caller
+            o.checkpoint_host = buf.ctypes.data_as(ctypes.c_void_p)
+            o.checkpoint_bytes = int(buf.nbytes)
+        o.checkpoint_stop = int(bool(opts.get("checkpoint_stop", False)))
+        o.resume = int(bool(opts.get("resume", False)))
+        return o
     return opts
 
 
@@ -291,6 +303,13 @@ def dda_solve_many(handles, opts, props, pols, Ps, n_threads=8):
     if rc < 0 and all(s == 0 for s in st):
         raise DDAError(rc, "dda_solve_many arguments")
     return rc, list(st), [[x.as_dict() for x in inf] for inf in infos]
+
+
+def dda_checkpoint_bytes(h, prec, nrhs):
+    """Size of the host buffer for checkpoints of a QMR-CS solve."""
+    v = ctypes.c_longlong()
+    _check(h, lib().dda_checkpoint_bytes(h, int(prec), int(nrhs), ctypes.byref(v)))
+    return v.value
 
 
 def dda_residual(h, pol_prescription, P, prop, pol):
