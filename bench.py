@@ -795,9 +795,17 @@ def run_products(args):
     b.record()
     b.synchronize()
     ms = a.elapsed_time(b) / max(1, args.products)
+    # per-pass times of the same products (CUDA events inside the library)
+    dda.dda_trace(p.h, True)
+    for _ in range(args.products):
+        dda.dda_matvec(p.h, prec, x, y)
+    torch.cuda.synchronize()
+    trace = {k: round(v[0] / max(1, v[1]), 4) for k, v in dda.dda_trace_read(p.h).items()
+             if k != "all_launches"}
+    dda.dda_trace(p.h, False)
     p.close()
     return {"workload": "products", "n_box": args.n, "grid": list(p.grid), "prec": args.prec,
-            "products": args.products, "ms_per_product": ms}
+            "products": args.products, "ms_per_product": ms, "ms_per_pass": trace}
 
 
 def main():

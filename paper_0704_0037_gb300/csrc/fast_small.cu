@@ -16,10 +16,15 @@ template cudaError_t fast_pass_small<float>(int, int, const FastArgs&);
 template cudaError_t fast_pass_small<double>(int, int, const FastArgs&);
 
 bool fast_supported(int M) { return M == 32 || M == 64 || M == 128 || M == 256 || M == 270; }
+bool fast_supported_c64(int M) { return fast_supported(M) || M == 512 || M == 1080; }
 
 template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a) {
   if (M == 270) return fast_pass_270<R>(pass, a);
   if (M == 256) return fast_pass_256<R>(pass, a);
+  if constexpr (std::is_same<R, float>::value) {
+    if (M == 512) return fast_pass_512_c64(pass, a);
+    if (M == 1080) return fast_pass_1080_c64(pass, a);
+  }
   return fast_pass_small<R>(M, pass, a);
 }
 template cudaError_t fast_pass<float>(int, int, const FastArgs&);

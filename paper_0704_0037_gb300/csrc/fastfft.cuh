@@ -28,6 +28,15 @@ namespace dda {
 namespace fast {
 
 template <int M1, int M2> constexpr int kQ = M1 > M2 ? M1 : M2;
+// Blocks per SM a launch bound asks for: `want` for blocks of up to 288
+// threads, one for the larger blocks of the long lines (512 and 1080), and
+// never more than smem_bytes of shared memory per block lets reside
+constexpr int kMinB(int nt, int want, long long smem_bytes) {
+  const int by_smem = (int)((227LL * 1024) / (smem_bytes > 0 ? smem_bytes : 1));
+  const int w = nt <= 288 ? want : 1;
+  const int r = w < by_smem ? w : by_smem;
+  return r >= 1 ? r : 1;
+}
 
 template <typename R>
 __device__ __forceinline__ cpx<R> zero() { return mk<R>((R)0, (R)0); }
@@ -174,6 +183,20 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n)
                : "memory");
 }
+// Asynchronous copy of one complex element (8 or 16 bytes) global -> shared;
+// !valid fills zeros without reading.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n)
+               : "memory");
+}
+template <int S>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem, bool valid) {
+  static_assert(S == 8 || S == 16, "8- or 16-byte elements");
+  if constexpr (S == 8) cp_async8(smem, gmem, valid);
+  else cp_async16(smem, gmem, valid);
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // Fetch the 128-byte line holding p into L2 (no data returned to the thread)
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -194,7 +217,9 @@ __device__ __forceinline__ int fold_axis(int k, int M, int& neg) {
 }
 
 template <typename R, int M1, int M2, int T>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict__ B2,
+__global__ void __launch_bounds__(T * kQ<M1, M2>,
+                                  kMinB(T * kQ<M1, M2>, 2, (M1 * M2 + 3LL * M1 * M2 * T) * sizeof(cpx<R>)))
+    fk_zconv(cpx<R>* __restrict__ B2,
                                                            const cpx<R>* __restrict__ D, int nz,
                                                            int Mx, int My,
                                                            const cpx<R>* __restrict__ tw,
@@ -216,19 +241,31 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 2) fk_zconv(cpx<R>* __restrict
     // that component's own region of s: asynchronous 16-byte copies, all
     // three components in flight at once (the region is free until the
     // component's phase 1 overwrites it).  Chunks past the last column are
-    // zero-filled without reading (padded lengths with register-resident
-    // passes are even, so a chunk never straddles the end of a row).
+    // zero-filled without reading.  Rows of an odd number of complex64
+    // elements (x padded to an odd length: this z pass runs whenever the z
+    // length has a compiled split) do not start on 16-byte boundaries, so
+    // their elements are copied one by one.
     constexpr int E = 16 / (int)sizeof(cpx<R>);   // elements per chunk
     constexpr int CPR = T / E;                     // chunks per tile row
     const int kx0 = blockIdx.x * T;
+    const bool by_elem = E > 1 && (Mx % E) != 0;
     for (int c = 0; c < 3; ++c) {
       cpx<R>* tile = s + c * M * T;
       const cpx<R>* src = B2 + c * comp + (long long)ky * Mx + kx0;
-      for (int k = threadIdx.x; k < nz * CPR; k += NT) {
-        const int z = k / CPR, u = k - z * CPR;
-        const bool ok = kx0 + u * E < Mx;
-        cp_async16(tile + z * T + u * E, ok ? (const void*)(src + z * plane + u * E) : (const void*)B2,
-                   ok);
+      if (by_elem) {
+        for (int k = threadIdx.x; k < nz * T; k += NT) {
+          const int z = k / T, u = k - z * T;
+          const bool ok = kx0 + u < Mx;
+          cp_async_elem<sizeof(cpx<R>)>(tile + z * T + u,
+                                        ok ? (const void*)(src + z * plane + u) : (const void*)B2, ok);
+        }
+      } else {
+        for (int k = threadIdx.x; k < nz * CPR; k += NT) {
+          const int z = k / CPR, u = k - z * CPR;
+          const bool ok = kx0 + u * E < Mx;
+          cp_async16(tile + z * T + u * E, ok ? (const void*)(src + z * plane + u * E) : (const void*)B2,
+                     ok);
+        }
       }
       cp_async_commit();
     }
@@ -389,7 +426,7 @@ __device__ __forceinline__ int row_of(const long long* off, long long i) {
 constexpr int kGU = 4;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const typename VecOf<R>::type* __restrict__ x,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) fk_xfwd(const typename VecOf<R>::type* __restrict__ x,
                                                           cpx<R>* __restrict__ B1, LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
@@ -478,20 +515,6 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfwd(const typename VecO
   }
 }
 
-// Asynchronous copy of one complex element (8 or 16 bytes) global -> shared;
-// !valid fills zeros without reading.
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int n = valid ? 8 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n)
-               : "memory");
-}
-template <int S>
-__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem, bool valid) {
-  static_assert(S == 8 || S == 16, "8- or 16-byte elements");
-  if constexpr (S == 8) cp_async8(smem, gmem, valid);
-  else cp_async16(smem, gmem, valid);
-}
 
 // ---------------------------------------------------------------- P5: x inverse
 // rows of B1 -> [t][LD] tile, inverse transform, y = x - beta u at the
@@ -503,7 +526,7 @@ __device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem, bool
 template <int M> constexpr int kXRow = (M + 1) / 2;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __restrict__ B1,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) fk_xinv(const cpx<R>* __restrict__ B1,
                                                           const typename VecOf<R>::type* __restrict__ x,
                                                           typename VecOf<R>::type* __restrict__ y,
                                                           LatticeDev lat,
@@ -651,7 +674,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xinv(const cpx<R>* __res
 // memory row (r / rows_y) * plane_rows + r % rows_y, so a sub-block of rows
 // (y < rows_y in every plane) can be transformed.
 template <typename R, int M1, int M2, int T>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, 3) fk_xfull(const cpx<R>* __restrict__ in,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) fk_xfull(const cpx<R>* __restrict__ in,
                                                            cpx<R>* __restrict__ out, long long nrows,
                                                            int rows_y, long long plane_rows,
                                                            const cpx<R>* __restrict__ tw) {
@@ -717,6 +740,11 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename R, int M1, int M2>
 struct Passes {
   static constexpr int M = M1 * M2, T = kT<R>, NT = T * kQ<M1, M2>;
+  // columns per block of the fused z pass: the three spectra of TZ columns
+  // must fit in shared memory (two blocks per SM where they can)
+  static constexpr int TZ = (size_t)(M + 3 * M * T) * sizeof(cpx<R>) <= 113 * 1024 ? T
+                           : (size_t)(M + 3 * M * (T / 2)) * sizeof(cpx<R>) <= 226 * 1024 ? T / 2
+                           : T / 4;
   static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
                           const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
@@ -739,14 +767,14 @@ struct Passes {
   }
   static cudaError_t zconv(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
                            int nrhs, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + 3 * M * T) * sizeof(cpx<R>);
-    cudaError_t e = set_smem(fk_zconv<R, M1, M2, T>, sm);
+    const size_t sm = (size_t)(M + 3 * M * TZ) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_zconv<R, M1, M2, TZ>, sm);
     if (e != cudaSuccess) return e;
     // two ~106 KB blocks per SM need the largest shared-memory carveout
-    e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, T>);
+    e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TZ>);
     if (e != cudaSuccess) return e;
-    fk_zconv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, My, nrhs), NT, sm, st>>>(B2, D, nz, Mx, My, tw,
-                                                                              skip);
+    fk_zconv<R, M1, M2, TZ><<<dim3((Mx + TZ - 1) / TZ, My, nrhs), TZ * kQ<M1, M2>, sm, st>>>(
+        B2, D, nz, Mx, My, tw, skip);
     count_launch();
     return cudaGetLastError();
   }

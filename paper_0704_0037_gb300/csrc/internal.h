@@ -255,7 +255,10 @@ struct FastArgs {
 };
 // number of (re, im) partials FP_XINV writes to dotp for nrows rows
 inline int fast_xinv_blocks(int nrows, bool fp32) { return 3 * ((nrows + (fp32 ? 16 : 8) - 1) / (fp32 ? 16 : 8)); }
-bool fast_supported(int M);
+bool fast_supported(int M);          // complex64, complex128 and double-float passes
+bool fast_supported_c64(int M);      // complex64 passes (also 512 and 1080)
+cudaError_t fast_pass_512_c64(int pass, const FastArgs& a);
+cudaError_t fast_pass_1080_c64(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_270(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_256(int pass, const FastArgs& a);

@@ -323,9 +323,10 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
   const int bstride = n_mat * 3;
   // per axis: the register-resident passes when the padded length has a
   // compile-time split, the shared-memory Stockham passes otherwise
-  const bool fx = g.engine == 0 && fast_supported(g.Mx);
-  const bool fy = g.engine == 0 && fast_supported(g.My);
-  const bool fz = g.engine == 0 && fast_supported(g.Mz);
+  auto has_fast = [](int M) { return sizeof(R) == 4 ? fast_supported_c64(M) : fast_supported(M); };
+  const bool fx = g.engine == 0 && has_fast(g.Mx);
+  const bool fy = g.engine == 0 && has_fast(g.My);
+  const bool fz = g.engine == 0 && has_fast(g.Mz);
   const int dnb = fast_xinv_blocks(g.nrows, sizeof(R) == 4);
   if (dotp && dot_nb && fx) *dot_nb = dnb;
   // right-hand sides in chunks of the work buffers' capacity, each chunk in

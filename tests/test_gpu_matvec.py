@@ -130,14 +130,25 @@ ENGINE_CASES = [
     ("ellipsoid70x128x100", inputs.ellipsoid(70, 128, 100)),  # y fast (256), x and z Stockham
     ("ellipsoid20x24x128", inputs.ellipsoid(20, 24, 128)),    # z fast (256)
     ("ellipsoid134x12x134", inputs.ellipsoid(134, 12, 134)),  # x and z fast (270)
+    # complex64 register-resident passes of the large grids (512 and 1080) on
+    # each axis, the other axes Stockham
+    ("ellipsoid256x6x5", inputs.ellipsoid(256, 6, 5)),
+    ("ellipsoid5x256x6", inputs.ellipsoid(5, 256, 6)),
+    ("ellipsoid6x5x256", inputs.ellipsoid(6, 5, 256)),
+    ("ellipsoid540x4x3", inputs.ellipsoid(540, 4, 3)),
+    ("ellipsoid3x540x4", inputs.ellipsoid(3, 540, 4)),
+    ("ellipsoid4x3x540", inputs.ellipsoid(4, 3, 540)),
+    # z fast (256) under rows of an odd padded x length (7): element-wise staging
+    ("ellipsoid4x3x128", inputs.ellipsoid(4, 3, 128)),
 ]
 
 
 @pytest.mark.parametrize("name,occ", ENGINE_CASES, ids=[c[0] for c in ENGINE_CASES])
 @pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
 def test_register_engine_matches_stockham_and_oracle(name, occ, prec_name):
-    """The register-resident passes (compiled lengths 32, 64, 128, 256, 270)
-    and the shared-memory Stockham passes give the same product, and both match
+    """The register-resident passes (compiled lengths 32, 64, 128, 256, 270;
+    complex64 also 512 and 1080) and the shared-memory Stockham passes give
+    the same product, and both match
     the oracle."""
     torch, dda = need_gpu()
     prec = dda.PREC[prec_name]
