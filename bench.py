@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--maxiter", type=int, default=100000, help="sphere workload: iteration cap")
     ap.add_argument("--forms", default="fp32_refined,fp64",
                     help="sphere workload: the forms to run (comma separated)")
+    ap.add_argument("--inner-cap", type=int, default=0,
+                    help="sphere workload: complex64 steps per inner solve before the switch to "
+                         "complex128 vectors (0: the library's default)")
     ap.add_argument("--batch-count", type=int, default=128, help=argparse.SUPPRESS)
     ap.add_argument("--batch-threads", type=int, default=16,
                     help="host threads (particles in flight) of the batch workload")
@@ -737,7 +740,7 @@ def run_sphere(args):
              if f[0] in args.forms.split(",")]
     for name, prec in forms:
         opts = dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_LDR, prec=prec, tol=TOL,
-                    maxiter=args.maxiter, inner_tol=INNER_TOL)
+                    maxiter=args.maxiter, inner_tol=INNER_TOL, inner_cap=args.inner_cap)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -764,7 +767,8 @@ def run_sphere(args):
             "vs_baseline": None, "dtype": "c64+df", "data": "synthetic (sphere occupancy)",
             "config": {"workload": f"sphere x={args.x:g} m={args.m:g} LDR, {args.n}^3 box, "
                                    "QMR-CS to 1e-5", "n_box": args.n, "x": args.x, "m": args.m,
-                       "n_occ": int(p.n_occ), "grid": list(p.grid), "maxiter": args.maxiter},
+                       "n_occ": int(p.n_occ), "grid": list(p.grid), "maxiter": args.maxiter,
+                       "inner_cap": args.inner_cap},
             "forms": out, "speedup_vs_fp64_form": r}
 
 
