@@ -58,13 +58,17 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=INNER_TOL)
     ap.add_argument("--n", type=int, default=N_SPHERE, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="sphere134",
-                    choices=["sphere134", "batch128", "sphere", "baselines", "products"],
+                    choices=["sphere134", "batch128", "sphere", "baselines", "products", "precond"],
                     help="sphere134: the headline line; batch128: the seeded 128-particle "
                          "batch (16 right-hand sides each), all right-hand sides to 1e-5; "
                          "sphere: one sphere (--n, --x, --m) solved once in each form; "
                          "baselines (with --impl reference): the CPU oracle's timings; "
                          "products: --products products of one precision (--prec) on the "
                          "sphere (--n, --x, --m), for profilers")
+    ap.add_argument("--train-count", type=int, default=128,
+                    help="precond workload: training particles (64^3 boxes)")
+    ap.add_argument("--pc-maxiter", type=int, default=1500,
+                    help="precond workload: Bi-CGSTAB iterations of each evaluation solve")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df"],
                     help="products workload: complex64, complex128 or double-float product")
     ap.add_argument("--products", type=int, default=3, help="products workload: count")
@@ -812,6 +816,65 @@ def run_products(args):
             "products": args.products, "ms_per_product": ms, "ms_per_pass": trace}
 
 
+def run_precond(args):
+    """The learned right preconditioner on the 128^3 sphere (x = 20, m = 2,
+    LDR, 1,099,136 dipoles): train the network on args.train_count particles
+    (ellipsoids and sphere clusters at 64^3, m in [1.5, 2.0]), then solve the
+    sphere with flexible Bi-CGSTAB with and without it (double-float products,
+    complex128 vectors, args.pc_maxiter iterations at most), and with the
+    FP32-refined QMR-CS for the same number of products; report iterations,
+    products, time, true residual and the errors against Mie of each."""
+    import torch
+    from paper_0704_0037_gb300 import build, dda, inputs, learned
+    build.build()
+    net = dda.PcNet(seed=704037)
+    tr = learned.train(net, count=args.train_count,
+                       log=lambda m: print(m, file=sys.stderr, flush=True))
+    occ = inputs.sphere(128)
+    prop, pol = [(0.0, 0.0, 1.0)], [(1.0, 0.0, 0.0)]
+    th = inputs.angles_deg(N_ANGLES)
+    mie = load_mie(20.0, 2.0)
+    out = {}
+    with dda.Particle(occ, [2.0], 20.0, volume_corrected=True) as p:
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+        P = torch.zeros((3, p.n_occ), dtype=torch.complex128, device="cuda")
+
+        def report(name, info, secs):
+            F, q = dda.dda_scatter(p.h, dda.DDA_LDR, P[None], prop, pol, np.zeros((0, 3)))
+            Mm, _, _ = dda.dda_mueller_plane_sym(p.h, dda.DDA_LDR, P[None], th)
+            out[name] = {"status": info["status_name"], "iters": info["iters"],
+                         "products": info["matvecs"], "seconds": secs,
+                         "rel_res_true": info["rel_res_true"],
+                         "rel_res_fp64_check": float(dda.dda_residual(p.h, dda.DDA_LDR, P[None], prop, pol)[0]),
+                         "network_dropped_at": info.get("outer", 0) if name == "learned" else None,
+                         "qext": float(q[0, 0]), "vs_mie": mie_errors(mie, float(q[0, 0]), Mm[:, 0, 0])}
+
+        for name, nn in (("plain_bicgstab", None), ("learned", net)):
+            P.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, info, _ = dda.dda_solve_pc(p.h, nn, dict(pol=dda.DDA_LDR, tol=TOL, maxiter=args.pc_maxiter),
+                                           prop, pol, P)
+            torch.cuda.synchronize()
+            report(name, info, time.perf_counter() - t0)
+        # QMR-CS (FP32-refined, the library's default solver) for the same product budget
+        P.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info, _ = dda.dda_solve(p.h, dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_LDR,
+                                              prec=dda.DDA_FP32_REFINED, tol=TOL,
+                                              maxiter=2 * args.pc_maxiter, inner_tol=INNER_TOL),
+                                    prop, pol, P[None])
+        torch.cuda.synchronize()
+        report("qmr_cs_fp32_refined", info[0], time.perf_counter() - t0)
+    net.close()
+    return {"metric": "learned right preconditioner: true residual and time, 128^3 sphere x=20 m=2",
+            "unit": "s", "n_gpus": 1, "data": "synthetic (seeded particles and sphere)",
+            "config": {"workload": "sphere x=20 m=2 LDR, 128^3 box (1,099,136 dipoles), tol 1e-5",
+                       "pc_maxiter": args.pc_maxiter, "network_parameters": 1033430},
+            "training": tr, "solves": out}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -828,6 +891,9 @@ def main():
         torch.distributed.init_process_group(backend="nccl")
     if args.workload == "products":
         print(json.dumps(run_products(args)))
+        return
+    if args.workload == "precond":
+        print(json.dumps(run_precond(args)))
         return
     if args.workload == "sphere":
         if rank == 0:

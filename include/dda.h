@@ -443,6 +443,81 @@ int dda_farfield_noalloc(dda_t h, const void* P_dev, int n_dir, const double* di
                          void* F_dev);
 
 /*
+ * Learned right preconditioner (no counterpart in the paper, which traces the
+ * slow convergence for large m to the system itself, Sec. 4, and names
+ * better preconditioning as the way forward, Sec. 5).  A 3D convolutional
+ * network N maps a residual r of Eq. (3) to an approximation of the error
+ * A^-1 r: features are the 2x2x2 averages of (Re, Im) of the three components
+ * of r / rms(r) and the occupied fraction at half resolution; a three-level
+ * encoder-decoder of 3x3x3 convolutions with ReLU (7-16-32-160-160 channels,
+ * 1,033,430 parameters, BF16 weights in the products, FP32 master weights,
+ * activations and accumulation) returns six channels that each dipole
+ * reads from its half-resolution cell, times rms(r).  Training, inference
+ * and the solver run in the library's own kernels; every reduction has a
+ * fixed order (deterministic).
+ */
+typedef struct dda_pcnet* dda_pcnet_t;
+
+/* dda_pcnet_create -- a new network on the current device, He-normal weights
+ * from a seeded generator (the last layer scaled by 0.1), zero biases.
+ * Errors: DDA_ERR_ARG (out NULL), DDA_ERR_CUDA, DDA_ERR_OOM. */
+int dda_pcnet_create(dda_pcnet_t* out, unsigned long long seed);
+int dda_pcnet_free(dda_pcnet_t net);                        /* NULL ok */
+int dda_pcnet_params(dda_pcnet_t net, long long* n);        /* parameter count */
+const char* dda_pcnet_last_error(dda_pcnet_t net);
+/* weights and biases as one host array of dda_pcnet_params floats, layer by
+ * layer ([cout][cin][k][k][k] weights, then [cout] biases); set_weights also
+ * resets the optimiser state. */
+int dda_pcnet_get_weights(dda_pcnet_t net, float* host);
+int dda_pcnet_set_weights(dda_pcnet_t net, const float* host);
+/* gradients of the last training step, same layout (host) */
+int dda_pcnet_get_grads(dda_pcnet_t net, float* host);
+
+/* dda_pcnet_apply -- z = N(v) on the lattice of handle h (same device).
+ * v_dev, z_dev: device [3][N_occ] complex128 (caller-owned, may not alias).
+ * Asynchronous on the handle's stream; the network keeps activation memory
+ * for the largest lattice it has seen. */
+int dda_pcnet_apply(dda_pcnet_t net, dda_t h, const void* v_dev, void* z_dev);
+
+/* dda_pcnet_train_step -- one Adam step (lr, betas 0.9 / 0.999) on the pair
+ * (r, e) of the handle's lattice: loss = |N(r) - e|^2 / |e|^2 over the
+ * dipoles.  z_dev (device [3][N_occ] complex128) receives N(r) before the
+ * step; *loss_out (host, may be NULL) the loss.  Synchronises the stream.
+ * DDA_ERR_NONFINITE for a non-finite loss. */
+int dda_pcnet_train_step(dda_pcnet_t net, dda_t h, const void* r_dev, const void* e_dev,
+                         void* z_dev, float lr, double* loss_out);
+
+/* dda_pcnet_pair -- a training pair from two solutions of the same
+ * right-hand side: e = x* - x_k with x = P / beta (beta of the given
+ * incidence), and r = A e (the residual of x_k), with the exact product
+ * (double-float where available, else FP64).  P_star, P_k: device [3][N_occ]
+ * complex128 in; r_out, e_out: device [3][N_occ] complex128 out.
+ * Synchronises the stream. */
+int dda_pcnet_pair(dda_t h, int pol_prescription, const double* prop_host, const double* pol_host,
+                   const void* P_star, const void* P_k, void* r_out, void* e_out);
+
+/*
+ * dda_solve_pc -- one right-hand side of Eq. (3) by flexible Bi-CGSTAB with
+ * the network as right preconditioner (net = NULL: plain Bi-CGSTAB with
+ * the same kernels), complex128 vectors and the exact product: double-float
+ * when the handle has the double-float D-matrix (a DDA_FP32_REFINED build on
+ * a grid with register-resident passes), else FP64.  Convergence is declared
+ * on the true residual ||b - A x|| / ||b|| < opts->tol; when the
+ * preconditioned iteration has not improved its residual by 1 % in 50
+ * iterations (or breaks down) the solve continues from its current x without
+ * the network.  Uses opts->pol, tol, maxiter (iterations; two products each).
+ *   prop_host, pol_host : one incidence (3 and 6 doubles).
+ *   P_dev    : device [3][N_occ] complex128, the polarizations (out).
+ *   res_hist : optional host [hist_len] recurrence residuals per iteration.
+ *   info     : one entry; info->outer is the iteration at which the network
+ *              was dropped (0: it never was); matvecs counts the products.
+ * Allocates 10 x 3 N_occ complex128 for the call.  Synchronises the stream.
+ */
+int dda_solve_pc(dda_t h, dda_pcnet_t net, const dda_solve_opts* opts, const double* prop_host,
+                 const double* pol_host, void* P_dev, double* res_hist, int hist_len,
+                 dda_solve_info* info);
+
+/*
  * dda_trace -- per-kernel timing (the paper reports only whole-run times,
  * Fig. 3; this is the library's own tracing).  enable != 0 starts recording a
  * CUDA event pair around each launch of the product passes P1..P5, the

@@ -2,6 +2,7 @@
 // Equation and section references are to Yurkin, Maltsev & Hoekstra,
 // arXiv:0704.0037.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -290,6 +291,8 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   }
   dda_ctx* h = new (std::nothrow) dda_ctx();
   if (!h) return DDA_ERR_OOM;
+  static std::atomic<long long> next_uid{1};
+  h->uid = next_uid.fetch_add(1);
   if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); h->device = 0; }
   Geom& g = h->g;
   g.nx = nx; g.ny = ny; g.nz = nz;

@@ -123,6 +123,7 @@ int smooth_size(int lo);
 
 // The handle.
 struct dda_ctx {
+  long long uid = 0;        // unique in the process (caches keyed by handle use it, not the address)
   int sym_flags = -1;       // DDA_SYM_* of the lattice (-1: not yet examined)
   int device = 0;           // CUDA device current at dda_init_lattice
   bool d64_from_df = false; // w64.D not yet derived from the double-float octant
@@ -186,6 +187,12 @@ int ensure_d64(dda_t h);
 int dda_solve_batch_internal(dda_t h, const dda_solve_opts* o, int nrhs, const double* prop,
                              const double* pol, void* P_dev, dda_solve_info* info);
 void batch_free(dda_t h);
+// incident plane wave of one right-hand side: propagation a, polarisation e
+// (complex, re/im pairs), and b = beta e exp(i kd a.r) on the handle's stream
+namespace dda {
+struct Wave { double a[3]; double e[6]; };
+int launch_rhs(dda_t h, c128* b, const c128* beta, const Wave& wv, cudaStream_t st);
+}  // namespace dda
 // bytes of the host image of a batched QMR-CS solve (krylov.cu)
 long long dda_checkpoint_bytes_internal(dda_t h, int prec, int nrhs);
 // ||b - A x|| / ||b|| per right-hand side with x = P / beta, native FP64 product

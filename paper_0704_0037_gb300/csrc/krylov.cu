@@ -251,7 +251,6 @@ __global__ void k_copy(const cpx<R>* __restrict__ a, cpx<R>* __restrict__ b, lon
 }
 
 // ---------------------------------------------------------------- RHS and P
-struct Wave { double a[3]; double e[6]; };
 
 // exp(i kd a_mu r_mu) along x (nx entries), then y, then z: the incident
 // phase exp(i kd a.r) of a dipole is the product of three entries

@@ -40,7 +40,10 @@ EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec"
            "dda_farfield_noalloc", "dda_trace",
            "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
            "dda_free", "dda_release_cached_memory", "dda_set_fft_engine", "dda_set_memory_limit",
-           "dda_memory_in_use", "dda_residual", "dda_checkpoint_bytes")
+           "dda_memory_in_use", "dda_residual", "dda_checkpoint_bytes", "dda_pcnet_create",
+           "dda_pcnet_free", "dda_pcnet_params", "dda_pcnet_last_error", "dda_pcnet_get_weights",
+           "dda_pcnet_set_weights", "dda_pcnet_get_grads", "dda_pcnet_apply", "dda_pcnet_train_step",
+           "dda_solve_pc", "dda_pcnet_pair")
 
 
 class DDAError(RuntimeError):
@@ -104,6 +107,18 @@ def lib():
         "dda_scatter": ([_vp, _ip, _vp, _ip, _dp, _dp, _ip, _dp, _dp, _dp, _dp], _ip),
         "dda_residual": ([_vp, _ip, _ip, _dp, _dp, _vp, _dp], _ip),
         "dda_checkpoint_bytes": ([_vp, _ip, _ip, ctypes.POINTER(ctypes.c_longlong)], _ip),
+        "dda_pcnet_create": ([ctypes.POINTER(_vp), ctypes.c_ulonglong], _ip),
+        "dda_pcnet_free": ([_vp], _ip),
+        "dda_pcnet_params": ([_vp, ctypes.POINTER(ctypes.c_longlong)], _ip),
+        "dda_pcnet_last_error": ([_vp], ctypes.c_char_p),
+        "dda_pcnet_get_weights": ([_vp, ctypes.POINTER(ctypes.c_float)], _ip),
+        "dda_pcnet_set_weights": ([_vp, ctypes.POINTER(ctypes.c_float)], _ip),
+        "dda_pcnet_get_grads": ([_vp, ctypes.POINTER(ctypes.c_float)], _ip),
+        "dda_pcnet_apply": ([_vp, _vp, _vp, _vp], _ip),
+        "dda_pcnet_train_step": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_float, _dp], _ip),
+        "dda_solve_pc": ([_vp, _vp, ctypes.POINTER(SolveOpts), _dp, _dp, _vp, _dp, _ip,
+                          ctypes.POINTER(SolveInfo)], _ip),
+        "dda_pcnet_pair": ([_vp, _ip, _dp, _dp, _vp, _vp, _vp, _vp], _ip),
         "dda_mueller_plane": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_mueller_plane_full": ([_ip, _dp, _dp, _dp, _dp], _ip),
         "dda_asymmetry": ([_ip, _dp, _dp, _dp, _dp, _dp], _ip),
@@ -488,6 +503,97 @@ def dda_last_error(h):
 
 def dda_free(h):
     return lib().dda_free(h)
+
+
+# ---------------------------------------------------------------- learned preconditioner
+# (layer, cin, cout, kernel) of the network, in the order of its parameters
+PCNET_LAYERS = ((7, 16, 3), (16, 32, 3), (32, 160, 3), (160, 160, 3), (192, 32, 3), (48, 16, 3),
+                (16, 6, 1))
+
+
+class PcNet:
+    """The learned right preconditioner (dda_pcnet_*): owns one network."""
+
+    def __init__(self, seed=0):
+        self.p = _vp()
+        rc = lib().dda_pcnet_create(ctypes.byref(self.p), ctypes.c_ulonglong(seed))
+        if rc < 0:
+            raise DDAError(rc, "dda_pcnet_create failed")
+        n = ctypes.c_longlong()
+        lib().dda_pcnet_params(self.p, ctypes.byref(n))
+        self.nparam = n.value
+
+    def _check(self, rc):
+        if rc < 0:
+            raise DDAError(rc, lib().dda_pcnet_last_error(self.p).decode())
+        return rc
+
+    def weights(self):
+        w = np.zeros(self.nparam, dtype=np.float32)
+        self._check(lib().dda_pcnet_get_weights(self.p, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+        if w.size != self.nparam:
+            raise ValueError("wrong parameter count")
+        self._check(lib().dda_pcnet_set_weights(self.p, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def grads(self):
+        g = np.zeros(self.nparam, dtype=np.float32)
+        self._check(lib().dda_pcnet_get_grads(self.p, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return g
+
+    def apply(self, h, v, z):
+        """z = N(v): CUDA complex128 [3][N_occ] tensors on the handle's lattice."""
+        import torch
+        return self._check(lib().dda_pcnet_apply(self.p, h, _dev_ptr(v, torch.complex128),
+                                                 _dev_ptr(z, torch.complex128)))
+
+    def train_step(self, h, r, e, z, lr):
+        """One Adam step on (r, e); z receives N(r); returns the loss."""
+        import torch
+        loss = ctypes.c_double()
+        self._check(lib().dda_pcnet_train_step(self.p, h, _dev_ptr(r, torch.complex128),
+                                               _dev_ptr(e, torch.complex128),
+                                               _dev_ptr(z, torch.complex128), ctypes.c_float(lr),
+                                               ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.p is not None and self.p.value:
+            lib().dda_pcnet_free(self.p)
+        self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dda_pcnet_pair(h, pol_prescription, prop, pol, P_star, P_k, r, e):
+    """Training pair: e = (P* - P_k) / beta, r = A e (device complex128 [3][N_occ])."""
+    import torch
+    a, ev = _vecs(prop, pol, 1)
+    return _check(h, lib().dda_pcnet_pair(h, int(pol_prescription), _dptr(a), _dptr(ev),
+                                          _dev_ptr(P_star, torch.complex128),
+                                          _dev_ptr(P_k, torch.complex128),
+                                          _dev_ptr(r, torch.complex128), _dev_ptr(e, torch.complex128)))
+
+
+def dda_solve_pc(h, net, opts, prop, pol, P, hist_len=0):
+    """Flexible Bi-CGSTAB with the network as right preconditioner (net None:
+    plain Bi-CGSTAB).  Returns (status, info dict, hist or None)."""
+    import torch
+    o = _opts(opts)
+    a, e = _vecs(prop, pol, 1)
+    info = (SolveInfo * 1)()
+    hist = np.full(hist_len, -1.0) if hist_len > 0 else None
+    rc = lib().dda_solve_pc(h, net.p if net is not None else None, ctypes.byref(o), _dptr(a), _dptr(e),
+                            _dev_ptr(P, torch.complex128), _dptr(hist), int(hist_len), info)
+    _check(h, rc)
+    return rc, info[0].as_dict(), hist
 
 
 class Particle:

@@ -139,3 +139,38 @@ def size_rule_n(x, m, per_wavelength=10.0):
     """Dipoles across the diameter for a given number per wavelength in the
     medium: n = per_wavelength * x * |m| / pi (3.18 x m at 10 per wavelength)."""
     return int(math.ceil(per_wavelength * x * abs(m) / math.pi))
+
+
+def sphere_cluster(n, count, seed, material=1):
+    """uint8 (n, n, n): the union of `count` spheres with random diameters
+    between n/3 and n/2, centres drawn so that each sphere lies inside the
+    box and touches or overlaps the cluster's first sphere's neighbourhood
+    (centres within one diameter of the box centre)."""
+    rng = np.random.default_rng(seed)
+    c = (np.arange(n) + 0.5)
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    occ = np.zeros((n, n, n), dtype=bool)
+    for _ in range(count):
+        d = rng.uniform(n / 3.0, n / 2.0)
+        r = d / 2.0
+        ctr = n / 2.0 + rng.uniform(-1.0, 1.0, size=3) * min(d, n / 2.0 - r)
+        occ |= (xx - ctr[0]) ** 2 + (yy - ctr[1]) ** 2 + (zz - ctr[2]) ** 2 <= r * r
+    return (occ * material).astype(np.uint8)
+
+
+def training_particles(count, n=64, seed=704037):
+    """(occupancy, m, kd) of the learned preconditioner's training runs:
+    ellipsoids with random axis ratios in [1, 3] and clusters of 2 to 4
+    spheres, in boxes of up to n cells per axis, real m uniform in [1.5, 2.0],
+    10 dipoles per wavelength in the material (kd = 2 pi / (10 m))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = float(rng.uniform(1.5, 2.0))
+        if rng.random() < 0.5:
+            r1, r2 = rng.uniform(1.0, 3.0, size=2)
+            occ = ellipsoid(n, max(8, int(round(n / r1))), max(8, int(round(n / r2))))
+        else:
+            occ = sphere_cluster(n, int(rng.integers(2, 5)), int(rng.integers(1 << 31)))
+        out.append((occ, m, 2.0 * math.pi / (10.0 * m)))
+    return out
