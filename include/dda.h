@@ -452,7 +452,8 @@ int dda_farfield_noalloc(dda_t h, const void* P_dev, int n_dir, const double* di
  * encoder-decoder of 3x3x3 convolutions with ReLU (7-16-32-160-160 channels,
  * 1,033,430 parameters, BF16 weights in the products, FP32 master weights,
  * activations and accumulation) returns six channels that each dipole
- * reads from its half-resolution cell, times rms(r).  Training, inference
+ * reads from its half-resolution cell, times rms(r), and adds to r
+ * (N(r) = r + correction: identity plus what was learned).  Training, inference
  * and the solver run in the library's own kernels; every reduction has a
  * fixed order (deterministic).
  */

@@ -14,7 +14,9 @@
 //   -> pool2 -> L2 conv3 32->160 relu, L3 conv3 160->160 relu [s2]
 //   -> up2, concat L1 -> L4 conv3 192->32 relu [s1]
 //   -> up2, concat L0 -> L5 conv3 48->16 relu [s0] -> L6 conv1 16->6 [s0]
-//   output: the value of each dipole's half-resolution cell, times rms(r).
+//   output: r plus the value of each dipole's half-resolution cell times
+//   rms(r) (identity plus a learned correction: an untrained network with
+//   its small last layer is close to no preconditioner at all).
 // conv3 = 3x3x3, zero padding 1; pool2 = average of the existing children;
 // up2 = nearest.  Loss: |N(r) - e|^2 / |e|^2 over the dipoles; Adam.
 // Every reduction has a fixed order (per-block partials, then one block), so
@@ -298,10 +300,11 @@ __global__ void k_feat_in(const c128* __restrict__ v, long long n_occ, const int
     f[6 * d0.n() + p] = occ * 0.125f;
   }
 }
-// z_i = rms * out6[.][cell(i)] for every dipole (complex128 output)
+// z_i = v_i + rms * out6[.][cell(i)] for every dipole (complex128): the
+// identity plus the learned correction
 __global__ void k_feat_out(const float* __restrict__ o6, Dims d0, LatticeDev lat, int nx, int ny,
                            int nrows, long long n_occ, const double* __restrict__ scl,
-                           c128* __restrict__ z) {
+                           const c128* __restrict__ v, c128* __restrict__ z) {
   const double s = scl[0];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -310,7 +313,8 @@ __global__ void k_feat_out(const float* __restrict__ o6, Dims d0, LatticeDev lat
     for (long long i = lat.row_off[row] + lane; i < lat.row_off[row + 1]; i += 32) {
       const long long p = ((long long)(zz / 2) * d0.y + y / 2) * d0.x + lat.xi[i] / 2;
       for (int c = 0; c < 3; ++c)
-        z[c * n_occ + i] = mk<double>(s * o6[(2 * c) * d0.n() + p], s * o6[(2 * c + 1) * d0.n() + p]);
+        z[c * n_occ + i] = v[c * n_occ + i] +
+                           mk<double>(s * o6[(2 * c) * d0.n() + p], s * o6[(2 * c + 1) * d0.n() + p]);
     }
   }
 }
@@ -609,7 +613,7 @@ int forward(dda_pcnet_t net, dda_t h, const c128* v, c128* z, Acts& A) {
   conv_fwd(net, 5, A.cat0, A.a5, A.d0, st);
   conv_fwd(net, 6, A.a5, A.o6, A.d0, st);
   k_feat_out<<<std::min(4096, (h->g.nrows + 7) / 8), 256, 0, st>>>(A.o6, A.d0, h->lat(), h->g.nx, h->g.ny,
-                                                                  h->g.nrows, h->g.n_occ, net->scal, z);
+                                                                  h->g.nrows, h->g.n_occ, net->scal, v, z);
   count_launch();
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? DDA_OK : pc_fail(net, DDA_ERR_CUDA, cudaGetErrorString(e));

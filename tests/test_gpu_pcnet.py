@@ -78,7 +78,7 @@ def _reference(torch, w, occ, v):
     o6 = conv(a5, 6, relu=False)
     cz, cy, cx = idx[:, 0] // 2, idx[:, 1] // 2, idx[:, 2] // 2
     z = torch.stack([torch.complex(o6[2 * c, cz, cy, cx], o6[2 * c + 1, cz, cy, cx]) for c in range(3)])
-    return z * scale, params
+    return vt + z * scale, params
 
 
 @pytest.fixture(scope="module")
