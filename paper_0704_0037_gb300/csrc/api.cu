@@ -366,9 +366,9 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   }
   g.n_occ = h->row_off_h[g.nrows];
   const std::vector<uint8_t>& mat = h->mat_h;
-  g.Mx = smooth_size(2 * nx - 1);
-  g.My = smooth_size(2 * ny - 1);
-  g.Mz = smooth_size(2 * nz - 1);
+  g.Mx = padded_length(2 * nx - 1, DDA_ENGINE_AUTO);
+  g.My = padded_length(2 * ny - 1, DDA_ENGINE_AUTO);
+  g.Mz = padded_length(2 * nz - 1, DDA_ENGINE_AUTO);
   g.px = make_plan(g.Mx); g.py = make_plan(g.My); g.pz = make_plan(g.Mz);
   g.tr = &h->tracer;
   g.engine = DDA_ENGINE_AUTO;
@@ -402,7 +402,26 @@ extern "C" int dda_set_fft_engine(dda_t h, int engine) {
     return dda_fail(h, DDA_ERR_ARG, "unknown FFT engine");
   if (h->w64.have_D || h->w32.have_D || h->wdf.have_D)
     return dda_fail(h, DDA_ERR_STATE, "dda_set_fft_engine must precede dda_build_Dmatrix");
-  h->g.engine = engine;
+  // the padded lengths follow the engine: compiled lengths for the
+  // register-resident passes, the smallest 7-smooth ones for Stockham; work
+  // memory sized for the old lengths (a failed build) is released
+  auto drop_grid_buffers = [&](auto& w) {
+    dev_free(w.B1, h->stream); dev_free(w.B2, h->stream); dev_free(w.tw, h->stream);
+    dev_free(w.D, h->stream);
+    w.B1 = nullptr; w.B2 = nullptr; w.tw = nullptr; w.D = nullptr; w.cap = 0;
+  };
+  drop_grid_buffers(h->w64);
+  drop_grid_buffers(h->w32);
+  drop_grid_buffers(h->wdf);
+  dev_free(h->d_dscratch, h->stream);
+  h->d_dscratch = nullptr;
+  h->dscratch_bytes = 0;
+  Geom& g = h->g;
+  g.engine = engine;
+  g.Mx = padded_length(2 * g.nx - 1, engine);
+  g.My = padded_length(2 * g.ny - 1, engine);
+  g.Mz = padded_length(2 * g.nz - 1, engine);
+  g.px = make_plan(g.Mx); g.py = make_plan(g.My); g.pz = make_plan(g.Mz);
   return DDA_OK;
 }
 

@@ -15,7 +15,10 @@ template <typename R> cudaError_t fast_pass_small(int M, int pass, const FastArg
 template cudaError_t fast_pass_small<float>(int, int, const FastArgs&);
 template cudaError_t fast_pass_small<double>(int, int, const FastArgs&);
 
-bool fast_supported(int M) { return M == 32 || M == 64 || M == 128 || M == 256 || M == 270; }
+bool fast_supported(int M) {
+  return M == 32 || M == 40 || M == 48 || M == 64 || M == 80 || M == 96 || M == 128 || M == 256 ||
+         M == 270;
+}
 bool fast_supported_c64(int M) { return fast_supported(M) || M == 512 || M == 1080; }
 
 template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a) {
@@ -25,6 +28,7 @@ template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a) 
     if (M == 512) return fast_pass_512_c64(pass, a);
     if (M == 1080) return fast_pass_1080_c64(pass, a);
   }
+  if (M == 40 || M == 48 || M == 80 || M == 96) return fast_pass_mid<R>(M, pass, a);
   return fast_pass_small<R>(M, pass, a);
 }
 template cudaError_t fast_pass<float>(int, int, const FastArgs&);
@@ -32,6 +36,7 @@ template cudaError_t fast_pass<double>(int, int, const FastArgs&);
 template <> cudaError_t fast_pass<df>(int M, int pass, const FastArgs& a) {
   if (M == 270) return fast_pass_270_df(pass, a);
   if (M == 256) return fast_pass_256_df(pass, a);
+  if (M == 40 || M == 48 || M == 80 || M == 96) return fast_pass_mid_df(M, pass, a);
   return fast_pass_small_df(M, pass, a);
 }
 

@@ -212,6 +212,7 @@ namespace dda {
 // Process-wide count of kernel launches made by this library (dda_trace_read
 // reports the increase since tracing was enabled).
 void count_launch();
+void count_launches(long long n);   // n kernels of a replayed CUDA graph (may be negative)
 long long launch_total();
 }  // namespace dda
 
@@ -270,6 +271,12 @@ template <typename R> cudaError_t fast_pass(int M, int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_270(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_256(int pass, const FastArgs& a);
 template <typename R> cudaError_t fast_pass_small(int M, int pass, const FastArgs& a);
+template <typename R> cudaError_t fast_pass_mid(int M, int pass, const FastArgs& a);
+cudaError_t fast_pass_mid_df(int M, int pass, const FastArgs& a);
+// padded length of an axis: the smallest compiled length >= lo when it is at
+// most 1.35 times the smallest 7-smooth one (engine DDA_ENGINE_AUTO), else
+// the smallest 7-smooth length (api.cu)
+int padded_length(int lo, int engine);
 // double-float passes (fast_df_*.cu); fast_pass<df> dispatches to them
 cudaError_t fast_pass_270_df(int pass, const FastArgs& a);
 cudaError_t fast_pass_256_df(int pass, const FastArgs& a);

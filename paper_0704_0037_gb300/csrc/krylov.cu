@@ -1473,8 +1473,74 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
   int k = resume_k > 0 ? resume_k : 0;
   bool active = false;
   for (int i = 0; i < nr; ++i) active = active || !m->hs[i].done;
+  // Blocks of kSyncEvery steps after the first (which sets the kernels'
+  // attributes) are captured once into a CUDA graph and replayed: every
+  // argument of the block's launches is a device buffer or a value fixed for
+  // the whole call, so one graph serves every block.  Not while tracing
+  // (its events are host bookkeeping per launch).
+  cudaGraphExec_t gexec = nullptr;
+  long long glaunches = 0;
+  bool graphs_ok = !(h->g.tr && h->g.tr->on);
+  int blocks = 0;
   while (active && k < maxiter) {
-    for (int j = 0; j < kSyncEvery && k < maxiter; ++j, ++k) {
+    const bool full = k + kSyncEvery <= maxiter;
+    if (graphs_ok && full && blocks >= 1 && !gexec) {
+      // capture one block
+      const long long l0 = launch_total();
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      int kk = k;
+      if (ok) {
+        for (int j = 0; j < kSyncEvery; ++j, ++kk) {
+          int dnb = 0;
+          cudaError_t e;
+          if (df_products) {
+            e = launch_matvec_df(h->g, h->lat(), h->wdf, h->w64.beta, h->n_mat, (const c128*)p,
+                                 (c128*)pt, nr, st, m->mask);
+          } else {
+            e = launch_matvec<R>(h->g, h->lat(), w, beta, h->n_mat, p, pt, nr, false, st, m->mvpart,
+                                 &dnb, m->mask);
+          }
+          if (e != cudaSuccess) { ok = false; break; }
+          if (dnb > 0) {
+            k_qmr_a<<<nr, kVT, 0, st>>>(s, m->mvpart, 1, 2, 2LL * dnb, dnb, m->mask); count_launch();
+          } else {
+            k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
+            k_qmr_a<<<nr, kVT, 0, st>>>(s, part, kNB, 1, kPS, nb, m->mask); count_launch();
+          }
+          k_qmr_k1<R><<<vg, kVT, 0, st>>>(pt, v, n, s, part, m->mask); count_launch();
+          k_qmr_k2<R><<<vg, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part, m->mask); count_launch();
+        }
+        const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+        ok = ok && ec == cudaSuccess && graph &&
+             cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      glaunches = launch_total() - l0;
+      if (!ok) {
+        // the block was not launched: run it the ordinary way from now on
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        graphs_ok = false;
+        count_launches(-glaunches);
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+          cudaGraph_t g2 = nullptr;
+          cudaStreamEndCapture(st, &g2);
+          if (g2) cudaGraphDestroy(g2);
+        }
+        cudaGetLastError();
+      } else {
+        count_launches(-glaunches);   // counted again as they run
+      }
+    }
+    if (gexec && full) {
+      DDA_CK(h, cudaGraphLaunch(gexec, st));
+      count_launches(glaunches);
+      k += kSyncEvery;
+    }
+    for (int j = 0; !(gexec && full) && j < kSyncEvery && k < maxiter; ++j, ++k) {
       int dnb = 0;
       cudaError_t e;
       if (df_products) {
@@ -1502,7 +1568,14 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
       tr_end(tr, st, TR_QMR_K2);
       LK(h);
     }
-    RK(bsync(b));
+    ++blocks;
+    {
+      const int rc = bsync(b);
+      if (rc != DDA_OK) {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        return rc;
+      }
+    }
     active = false;
     for (int i = 0; i < nr; ++i) {
       Scal& q = m->hs[i];
@@ -1525,10 +1598,14 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
     }
     if (on_sync && active) {
       const int rc = (*on_sync)(k);
-      if (rc < 0) return rc;
+      if (rc < 0) {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        return rc;
+      }
       if (rc == 1) break;
     }
   }
+  if (gexec) cudaGraphExecDestroy(gexec);
   *steps_out = k;
   return DDA_OK;
 }

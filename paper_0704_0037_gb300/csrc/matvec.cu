@@ -501,6 +501,16 @@ FftPlan make_plan(int M) {
   return p;
 }
 
+int padded_length(int lo, int engine) {
+  const int smooth = smooth_size(lo);
+  if (engine != 0) return smooth;
+  // compiled lengths, ascending (complex64 passes also exist for 512 and 1080)
+  static const int kFast[] = {32, 40, 48, 64, 80, 96, 128, 256, 270, 512, 1080};
+  for (int M : kFast)
+    if (M >= lo) return (double)M <= 1.35 * smooth ? M : smooth;
+  return smooth;
+}
+
 int smooth_size(int lo) {
   int m = lo < 1 ? 1 : lo;
   for (;; ++m) {

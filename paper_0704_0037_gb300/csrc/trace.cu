@@ -19,6 +19,7 @@ const char* trace_name(int id) { return (id >= 0 && id < TR_COUNT) ? kNames[id] 
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 static cudaEvent_t take(Tracer* t) {

@@ -603,6 +603,7 @@ class Particle:
         self.h = dda_init_lattice(occ, m_list, kd, volume_corrected, stream)
         if engine is not None:
             dda_set_fft_engine(self.h, engine)
+            self.grid = dda_grid(self.h)
         self.n_occ = dda_n_occ(self.h)
         self.kd = dda_kd(self.h)
         self.grid = dda_grid(self.h)

@@ -129,3 +129,31 @@ def test_solve_many_equals_one_by_one():
             P = torch.zeros((2, 3, q.n_occ), dtype=torch.complex128, device="cuda")
             dda.dda_solve_many([q.h, q.h], opts, [props[0], props[0]], [pols[0], pols[0]], [P, P])
 
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32_refined"])
+def test_graph_replayed_blocks_equal_launched_ones(prec_name):
+    """On a stream of its own a handle's batched QMR-CS runs its blocks of 8
+    steps as a replayed CUDA graph; on the legacy default stream (which cannot
+    be captured) it launches them one by one.  Both give the same
+    polarizations, bit for bit, and the same iteration counts."""
+    torch, dda = need_gpu()
+    occ = inputs.sphere(16)
+    prop, pol = _orientations(2, 11)
+    prec = dda.PREC[prec_name]
+    opts = dict(solver=dda.DDA_QMR_CS, pol=dda.DDA_CLDR, prec=prec, tol=1e-9, maxiter=400,
+                inner_tol=1e-3)
+    out = []
+    s = torch.cuda.Stream()
+    for stream in (0, s):
+        p = dda.Particle(occ, [1.6 + 0.05j], 0.5, stream=stream)
+        with p:
+            dda.dda_build_Dmatrix(p.h, prec)
+            P = torch.zeros((len(prop), 3, p.n_occ), dtype=torch.complex128, device="cuda")
+            torch.cuda.synchronize()
+            st, info = dda.dda_solve_batch(p.h, opts, prop, pol, P)
+            torch.cuda.synchronize()
+            assert st == dda.DDA_OK, info
+            out.append((P.cpu(), [i["iters"] for i in info]))
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]

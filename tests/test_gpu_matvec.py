@@ -122,14 +122,17 @@ def test_matvec_multi_rhs_and_adjoint():
         assert rel_l2(y, ref) <= 1e-12
 
 
+# Padded lengths under the default engine (compiled lengths within 1.35 times
+# the smallest 7-smooth one; the Stockham engine keeps the 7-smooth ones):
 ENGINE_CASES = [
     ("sphere16_M32", inputs.sphere(16)),
     ("sphere32_M64", inputs.sphere(32)),
     ("sphere64_M128", inputs.sphere(64)),
-    ("ellipsoid64x60x33", inputs.ellipsoid(64, 60, 33)),   # x fast (128), y and z Stockham
-    ("ellipsoid70x128x100", inputs.ellipsoid(70, 128, 100)),  # y fast (256), x and z Stockham
-    ("ellipsoid20x24x128", inputs.ellipsoid(20, 24, 128)),    # z fast (256)
-    ("ellipsoid134x12x134", inputs.ellipsoid(134, 12, 134)),  # x and z fast (270)
+    ("ellipsoid64x60x33", inputs.ellipsoid(64, 60, 33)),   # 128, 128, 80
+    ("ellipsoid70x128x100", inputs.ellipsoid(70, 128, 100)),  # 140 (Stockham), 256, 256
+    ("ellipsoid20x24x128", inputs.ellipsoid(20, 24, 128)),    # 40, 48, 256
+    ("ellipsoid134x12x134", inputs.ellipsoid(134, 12, 134)),  # 270, 32, 270
+    ("ellipsoid37x23x45", inputs.ellipsoid(37, 23, 45)),      # 80, 48, 96: the added lengths
     # complex64 register-resident passes of the large grids (512 and 1080) on
     # each axis, the other axes Stockham
     ("ellipsoid256x6x5", inputs.ellipsoid(256, 6, 5)),
