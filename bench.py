@@ -84,7 +84,9 @@ def parse():
     ap.add_argument("--batch-threads", type=int, default=16,
                     help="host threads (particles in flight) of the batch workload")
     ap.add_argument("--batch-maxiter", type=int, default=20000)
-    ap.add_argument("--batch-c64-only", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--batch-c64-only", type=int, default=0,
+                    help="batch workload: 1 keeps the inner solves complex64 for the whole budget "
+                         "(0, the default: the library's default switch after 1000 steps)")
     return ap.parse_args()
 
 
