@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df"],
                     help="products workload: complex64, complex128 or double-float product")
     ap.add_argument("--products", type=int, default=3, help="products workload: count")
+    ap.add_argument("--engine", default="auto", choices=["auto", "stockham"],
+                    help="products workload: FFT engine (register-resident passes where compiled, "
+                         "or the shared-memory Stockham passes for every length)")
     ap.add_argument("--x", type=float, default=X_SIZE, help="sphere workload: size parameter")
     ap.add_argument("--m", type=float, default=M_INDEX, help="sphere workload: refractive index")
     ap.add_argument("--maxiter", type=int, default=100000, help="sphere workload: iteration cap")
@@ -788,7 +791,8 @@ def run_products(args):
     from paper_0704_0037_gb300 import build, dda, inputs
     build.build()
     occ = inputs.sphere(args.n)
-    p = dda.Particle(occ, [args.m], args.x, volume_corrected=True)
+    engine = dda.DDA_ENGINE_STOCKHAM if args.engine == "stockham" else None
+    p = dda.Particle(occ, [args.m], args.x, volume_corrected=True, engine=engine)
     prec = {"fp32": dda.DDA_FP32_REFINED, "fp64": dda.DDA_FP64, "df": dda.DDA_FP64_PAIR}[args.prec]
     dda.dda_build_Dmatrix(p.h, dda.DDA_FP64 if prec == dda.DDA_FP64 else dda.DDA_FP32_REFINED)
     dda.dda_set_beta(p.h, dda.DDA_LDR, [(0.0, 0.0, 1.0)], [(1.0, 0.0, 0.0)])
@@ -815,6 +819,7 @@ def run_products(args):
     dda.dda_trace(p.h, False)
     p.close()
     return {"workload": "products", "n_box": args.n, "grid": list(p.grid), "prec": args.prec,
+            "engine": args.engine,
             "products": args.products, "ms_per_product": ms, "ms_per_pass": trace}
 
 

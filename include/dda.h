@@ -74,7 +74,8 @@ enum dda_solver { DDA_QMR_CS = 0, DDA_BICG_CS = 1, DDA_BICGSTAB = 2, DDA_CGNR = 
  * an FP64-class D-matrix build, FP64 Krylov scalars and inner products, and
  * an outer iterative refinement on the true residual computed from complex128
  * vectors.  On grids whose three padded lengths have register-resident passes
- * (32, 64, 128, 256, 270) the FP32_REFINED D-matrix build and its residual
+ * in every precision (32, 40, 48, 64, 80, 96, 128, 256, 270) the
+ * FP32_REFINED D-matrix build and its residual
  * products run in double-float arithmetic (pairs of floats, about 48
  * significant bits, on the FP32 pipe); elsewhere in FP64.
  * DDA_FP64_PAIR (dda_matvec only): that double-float product on complex128
@@ -96,8 +97,11 @@ enum dda_prec { DDA_FP64 = 0, DDA_FP32_REFINED = 1, DDA_FP64_PAIR = 2 };
  * Errors: DDA_ERR_ARG (bad sizes, no occupied cell, material index > n_mat),
  *   DDA_ERR_CUDA / DDA_ERR_OOM.  Copies what it needs from the host arrays.
  * The FFT passes use register-resident kernels for padded lengths with a
- * compiled split (32, 64, 128, 256, 270) and shared-memory Stockham kernels
- * otherwise; dda_set_fft_engine selects the latter for every length.
+ * compiled split (32, 40, 48, 64, 80, 96, 128, 256, 270; for complex64 also
+ * 512 and 1080) and shared-memory Stockham kernels otherwise;
+ * dda_set_fft_engine selects the latter for every length.  An axis is padded
+ * to the smallest compiled length >= 2n - 1 when that is within 1.35x of the
+ * smallest 7-smooth one, else to the 7-smooth one.
  */
 int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_t* occ_host,
                      int n_mat, const double* m_host, double kd, int volume_corrected,
