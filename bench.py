@@ -250,12 +250,7 @@ def load_peaks():
 # stored ncu capture of the kernel as it is now (not measured by this run),
 # with the capture it comes from.  Only valid for the 134^3 sphere on the
 # 270^3 grid; None elsewhere, and removed whenever the kernel changes.
-NCU_TRAFFIC_134 = {
-    "p3_zconv_c64": (450947328 + 196137728,
-                     "ncu --set full --clock-control none -k regex:fk_zconv -s 1 -c 1 of "
-                     "python bench.py --workload products --n 134 --prec fp32 --products 3 "
-                     "(fk_zconv<float, 15, 18, 16>, stored capture, not measured by this run)"),
-}
+NCU_TRAFFIC_134 = {}
 
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe's nominal 1.25 TFLOP/s)
 

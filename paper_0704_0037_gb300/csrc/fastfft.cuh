@@ -28,6 +28,12 @@ namespace dda {
 namespace fast {
 
 template <int M1, int M2> constexpr int kQ = M1 > M2 ? M1 : M2;
+// The product's padded lengths are M >= 2 n - 1, so its lines hold input (and
+// keep output) only at n < (M + 1) / 2: of the elements n = j + M2 i of a
+// line only i < kHalf can.  With this bound known at compile time the other
+// inputs are constant zeros and the arithmetic of the discarded outputs is
+// dead code (the zero input and partial output of Sec. 2).
+template <int M1, int M2> constexpr int kHalf = ((M1 * M2 + 1) / 2 + M2 - 1) / M2;
 // Blocks per SM a launch bound asks for: `want` for blocks of up to 288
 // threads, one for the larger blocks of the long lines (512 and 1080), and
 // never more than smem_bytes of shared memory per block lets reside
@@ -70,8 +76,9 @@ __device__ __forceinline__ void load_tw(cpx<R>* s_tw, const cpx<R>* __restrict__
 // msign != 0 (D-matrix build, whole lines): only elements y <= M/2 are read;
 // element y > M/2 is msign times element M - y (the line has that parity).
 // ostr != 0: line group blockIdx.y starts at element blockIdx.y * ostr of
-// both arrays (sub-blocks of whole lines, ny == M).
-template <typename R, int M1, int M2, int T>
+// both arrays (sub-blocks of whole lines, ny == M).  PRUNE: the product's
+// lines (ny <= (M + 1) / 2, inputs past kHalf known zero).
+template <typename R, int M1, int M2, int T, bool PRUNE>
 __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restrict__ in,
                                                           cpx<R>* __restrict__ out, int ny, int nz,
                                                           int Mx, const cpx<R>* __restrict__ tw,
@@ -96,7 +103,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
 #pragma unroll
       for (int i = 0; i < M1; ++i) {
         const int y = j + M2 * i;
-        v[i] = (y < ny && kx < Mx) ? in[ib + (long long)y * Mx + kx] : zero<R>();
+        v[i] = ((!PRUNE || i < kHalf<M1, M2>) && y < ny && kx < Mx) ? in[ib + (long long)y * Mx + kx]
+                                                                     : zero<R>();
       }
     } else {
 #pragma unroll
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yinv(const cpx<R>* __restri
 #pragma unroll
     for (int i = 0; i < M1; ++i) {
       const int y = j + M2 * i;
-      if (y < ny) out[ob + (long long)y * Mx + kx] = v[i];
+      if (i < kHalf<M1, M2> && y < ny) out[ob + (long long)y * Mx + kx] = v[i];
     }
   }
 }
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
                                                            int Mx, int My,
                                                            const cpx<R>* __restrict__ tw,
                                                            const int* __restrict__ skip) {
-  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, kZin = kHalf<M1, M2>;
   if (skip && skip[blockIdx.z]) return;
   B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
 #pragma unroll
       for (int i = 0; i < M1; ++i) {
         const int z = j + M2 * i;
-        v[i] = z < nz ? sc[z * T + t] : zero<R>();
+        v[i] = (i < kZin && z < nz) ? sc[z * T + t] : zero<R>();
       }
     }
     __syncthreads();           // every read of the tile before the region is rewritten
@@ -397,7 +405,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
 #pragma unroll
       for (int i = 0; i < M1; ++i) {
         const int z = j + M2 * i;
-        if (z < nz) B2[c * comp + z * plane + col] = v[i];
+        if (i < kZin && z < nz) B2[c * comp + z * plane + col] = v[i];
       }
     }
   }
@@ -484,7 +492,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) f
     const int j = q;
     cpx<R> v[M1];
 #pragma unroll
-    for (int i = 0; i < M1; ++i) v[i] = at[j + M2 * i];
+    for (int i = 0; i < M1; ++i) v[i] = i < kHalf<M1, M2> ? at[j + M2 * i] : zero<R>();
     cl::Dft<R, false, M1>::run(v);
 #pragma unroll
     for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
@@ -589,7 +597,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) f
     for (int k1 = 0; k1 < M1; ++k1) v[k1] = at[k1 * M2 + j];
     cl::Dft<R, true, M1>::run(v);
 #pragma unroll
-    for (int i = 0; i < M1; ++i) at[j + M2 * i] = v[i];
+    for (int i = 0; i < kHalf<M1, M2>; ++i) at[j + M2 * i] = v[i];   // x < n_x only
   }
   __syncthreads();
   constexpr int NW = (NT + 31) / 32;
@@ -748,9 +756,9 @@ struct Passes {
   static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
                           const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
-    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
+    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T, true>, sm);
     if (e != cudaSuccess) return e;
-    fk_yfwd<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3 * nrhs), NT, sm, st>>>(in, out, ny, nz,
+    fk_yfwd<R, M1, M2, T, true><<<dim3((Mx + T - 1) / T, nz, 3 * nrhs), NT, sm, st>>>(in, out, ny, nz,
                                                                                 Mx, tw, 0, skip, 0);
     count_launch();
     return cudaGetLastError();
@@ -815,9 +823,9 @@ struct Passes {
   static cudaError_t sfull(const cpx<R>* in, cpx<R>* out, int nlines, int n_outer, int stride,
                            int msign, const cpx<R>* tw, cudaStream_t st, long long ostride) {
     const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
-    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T>, sm);
+    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T, false>, sm);
     if (e != cudaSuccess) return e;
-    fk_yfwd<R, M1, M2, T><<<dim3((nlines + T - 1) / T, n_outer, 1), NT, sm, st>>>(in, out, M, n_outer,
+    fk_yfwd<R, M1, M2, T, false><<<dim3((nlines + T - 1) / T, n_outer, 1), NT, sm, st>>>(in, out, M, n_outer,
                                                                                  stride, tw, msign,
                                                                                  nullptr, ostride);
     count_launch();
