@@ -122,6 +122,29 @@ enum dda_engine { DDA_ENGINE_AUTO = 0, DDA_ENGINE_STOCKHAM = 1 };
 int dda_set_fft_engine(dda_t h, int engine);
 
 /*
+ * dda_set_pass_tiles / dda_get_pass_tiles -- tile variants of the
+ * register-resident product passes: lines per block of the y forward pass,
+ * the fused z pass and the y inverse pass (tiles[0..2]), for the products of
+ * one arithmetic (prec: DDA_FP32_REFINED the complex64 products, DDA_FP64 the
+ * complex128 ones, DDA_FP64_PAIR the double-float ones).
+ *   0  : the default lines per block (16 columns complex64, 8 wider; fewer
+ *        where the z pass's spectra would not fit in shared memory);
+ *   1  : half as many lines per block (twice the blocks);
+ *   -1 : chosen by dda_build_Dmatrix, which times both variants of each pass
+ *        on the handle's own buffers (CUDA events, three launches) and keeps
+ *        the faster (cached per device and grid shape).  The default.
+ * Every variant computes each line with the same arithmetic: the products
+ * agree bit for bit.  dda_set_pass_tiles with tiles == NULL sets -1 for all
+ * three; an entry set to 0 or 1 is kept by later builds.  dda_get_pass_tiles
+ * writes the current entries to tiles[0..2] (-1 before the first build).
+ * Errors: DDA_ERR_ARG (null handle, unknown precision, a value outside
+ * -1..1, null tiles for the get).  No counterpart in the paper (Sec. 2 names
+ * the FFT libraries ADDA can use; FFTW plans its transforms by timing).
+ */
+int dda_set_pass_tiles(dda_t h, int prec, const int* tiles);
+int dda_get_pass_tiles(dda_t h, int prec, int* tiles);
+
+/*
  * dda_build_Dmatrix -- FFT of the Green's tensor on the padded grid (Sec. 2:
  * the product is an FFT convolution and the symmetry of the interaction
  * matrix reduces the memory of its Fourier transform).

@@ -446,7 +446,43 @@ extern "C" int dda_build_Dmatrix(dda_t h, int prec) {
       if (rc != DDA_OK) return rc;
     }
   }
-  return dda_build_D_internal(h, prec == DDA_FP32_REFINED);
+  rc = dda_build_D_internal(h, prec == DDA_FP32_REFINED);
+  if (rc != DDA_OK) return rc;
+  // the tile variants of the product's y and z passes, picked by timing
+  // (cached per grid shape; entries pinned by dda_set_pass_tiles are kept)
+  cudaError_t e;
+  if (prec == DDA_FP32_REFINED) {
+    e = tune_tiles<float>(h->g, h->lat(), h->w32, h->stream);
+    if (e == cudaSuccess && dfok) e = tune_tiles<df>(h->g, h->lat(), h->wdf, h->stream);
+  } else {
+    e = tune_tiles<double>(h->g, h->lat(), h->w64, h->stream);
+  }
+  if (e != cudaSuccess) return dda_cuda_fail(h, e, "product pass tile autotuning");
+  return DDA_OK;
+}
+
+static int tile_kind(int prec) {
+  return prec == DDA_FP32_REFINED ? 0 : prec == DDA_FP64 ? 1 : prec == DDA_FP64_PAIR ? 2 : -1;
+}
+
+extern "C" int dda_set_pass_tiles(dda_t h, int prec, const int* tiles) {
+  if (!h) return DDA_ERR_ARG;
+  const int k = tile_kind(prec);
+  if (k < 0) return dda_fail(h, DDA_ERR_ARG, "unknown precision");
+  for (int i = 0; i < 3; ++i) {
+    const int v = tiles ? tiles[i] : -1;
+    if (v < -1 || v > 1) return dda_fail(h, DDA_ERR_ARG, "tile variant must be -1, 0 or 1");
+  }
+  for (int i = 0; i < 3; ++i) h->g.tiles[k][i] = tiles ? tiles[i] : -1;
+  return DDA_OK;
+}
+
+extern "C" int dda_get_pass_tiles(dda_t h, int prec, int* tiles) {
+  if (!h || !tiles) return DDA_ERR_ARG;
+  const int k = tile_kind(prec);
+  if (k < 0) return dda_fail(h, DDA_ERR_ARG, "unknown precision");
+  for (int i = 0; i < 3; ++i) tiles[i] = h->g.tiles[k][i];
+  return DDA_OK;
 }
 
 extern "C" int dda_set_beta(dda_t h, int presc, int nrhs, const double* prop, const double* pol) {

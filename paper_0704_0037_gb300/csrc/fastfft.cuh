@@ -224,6 +224,107 @@ __device__ __forceinline__ int fold_axis(int k, int M, int& neg) {
   return k;
 }
 
+// Pieces of the fused z pass shared by its two- and three-level forms.  A
+// block holds T adjacent columns (kx) of one ky and right-hand side; s is
+// [3][M][T] (component, row, column) in shared memory.
+//
+// Stage the nz x T input tile of every component in the first nz rows of
+// that component's own region of s: asynchronous 16-byte copies, all three
+// components in flight at once (three commit groups; the region is free until
+// the component's first phase overwrites it).  Chunks past the last column
+// are zero-filled without reading.  Rows of an odd number of complex64
+// elements (x padded to an odd length: this z pass runs whenever the z length
+// has a compiled split) do not start on 16-byte boundaries, so their elements
+// are copied one by one.
+template <typename R, int M, int T, int NT>
+__device__ __forceinline__ void zc_stage(cpx<R>* s, const cpx<R>* B2, int nz, int Mx, int My) {
+  constexpr int E = 16 / (int)sizeof(cpx<R>);   // elements per chunk
+  constexpr int CPR = T / E;                     // chunks per tile row
+  const long long plane = (long long)My * Mx;
+  const long long comp = (long long)nz * plane;
+  const int kx0 = blockIdx.x * T, ky = blockIdx.y;
+  const bool by_elem = E > 1 && (Mx % E) != 0;
+  for (int c = 0; c < 3; ++c) {
+    cpx<R>* tile = s + c * M * T;
+    const cpx<R>* src = B2 + c * comp + (long long)ky * Mx + kx0;
+    if (by_elem) {
+      for (int k = threadIdx.x; k < nz * T; k += NT) {
+        const int z = k / T, u = k - z * T;
+        const bool ok = kx0 + u < Mx;
+        cp_async_elem<sizeof(cpx<R>)>(tile + z * T + u,
+                                      ok ? (const void*)(src + z * plane + u) : (const void*)B2, ok);
+      }
+    } else {
+      for (int k = threadIdx.x; k < nz * CPR; k += NT) {
+        const int z = k / CPR, u = k - z * CPR;
+        const bool ok = kx0 + u * E < Mx;
+        cp_async16(tile + z * T + u * E, ok ? (const void*)(src + z * plane + u * E) : (const void*)B2,
+                   ok);
+      }
+    }
+    cp_async_commit();
+  }
+}
+
+// Warm L2 with the octant entries of the Fourier-space product (fy of this
+// block, its range of fx, every fz and component): they arrive from HBM while
+// the forward transforms run, so the product's loads hit L2.
+template <typename R, int M, int T, int NT>
+__device__ __forceinline__ void zc_prefetch(const cpx<R>* D, int Mx, int My) {
+  const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
+  const long long octs = (long long)hx * hy * hz;
+  int nys, na, nb;
+  const int fy = fold_axis(blockIdx.y, My, nys);
+  const int kxa = blockIdx.x * T, kxb = min(kxa + T, Mx) - 1;
+  const int fa = fold_axis(kxa, Mx, na), fb = fold_axis(kxb, Mx, nb);
+  const int fmin = min(fa, fb);
+  const int fmax = (2 * kxa <= Mx && 2 * kxb >= Mx) ? Mx / 2 : max(fa, fb);
+  for (int k = threadIdx.x; k < 6 * hz; k += NT) {
+    const int c6 = k / hz, fz = k - c6 * hz;
+    const cpx<R>* row = D + c6 * octs + ((long long)fz * hy + fy) * hx;
+    prefetch_l2(row + fmin);
+    if (((size_t)(row + fmax) >> 7) != ((size_t)(row + fmin) >> 7)) prefetch_l2(row + fmax);
+  }
+}
+
+// Fourier-space product with the octant of FFT(G).  Work item (t, fz): the
+// six octant values at (fx, fy, fz) are loaded once and applied to both
+// kz = fz and kz = M - fz (sign flips for the components odd in z); the
+// spectrum value kz of column t lives in row row_of(kz).
+template <typename R, int M, int T, int NT, typename RowOf>
+__device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__ D, int Mx, int My,
+                                           RowOf row_of) {
+  const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
+  const long long octs = (long long)hx * hy * hz;
+  int nys;
+  const int fy = fold_axis(blockIdx.y, My, nys);
+  const int kx0 = blockIdx.x * T;
+#pragma unroll 2
+  for (int it = threadIdx.x; it < T * hz; it += NT) {
+    const int t2 = it % T, fz = it / T;
+    const int kx2 = kx0 + t2;
+    if (kx2 >= Mx) continue;
+    int nxs;
+    const int fx = fold_axis(kx2, Mx, nxs);
+    const long long o = ((long long)fz * hy + fy) * hx + fx;
+    const cpx<R> dxx = D[o], dyy = D[3 * octs + o], dzz = D[5 * octs + o];
+    cpx<R> dxy = D[octs + o], dxz = D[2 * octs + o], dyz = D[4 * octs + o];
+    if (nxs ^ nys) dxy = mk<R>(-dxy.x, -dxy.y);
+    const int nkz = (fz == 0 || 2 * fz == M) ? 1 : 2;
+    for (int h = 0; h < nkz; ++h) {
+      const int kz = h ? M - fz : fz;
+      cpx<R> ez = dxz, fzz = dyz;
+      if (nxs ^ h) ez = mk<R>(-ez.x, -ez.y);
+      if (nys ^ h) fzz = mk<R>(-fzz.x, -fzz.y);
+      const int e = row_of(kz) * T + t2;
+      const cpx<R> vx = s[e], vy = s[M * T + e], vz = s[2 * M * T + e];
+      s[e] = dxx * vx + dxy * vy + ez * vz;
+      s[M * T + e] = dxy * vx + dyy * vy + fzz * vz;
+      s[2 * M * T + e] = ez * vx + fzz * vy + dzz * vz;
+    }
+  }
+}
+
 template <typename R, int M1, int M2, int T>
 __global__ void __launch_bounds__(T * kQ<M1, M2>,
                                   kMinB(T * kQ<M1, M2>, 2, (M1 * M2 + 3LL * M1 * M2 * T) * sizeof(cpx<R>)))
@@ -244,59 +345,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
   const long long plane = (long long)My * Mx;
   const long long comp = (long long)nz * plane;
   const long long col = (long long)ky * Mx + kx;
-  {
-    // Stage the nz x T input tile of every component in the first nz rows of
-    // that component's own region of s: asynchronous 16-byte copies, all
-    // three components in flight at once (the region is free until the
-    // component's phase 1 overwrites it).  Chunks past the last column are
-    // zero-filled without reading.  Rows of an odd number of complex64
-    // elements (x padded to an odd length: this z pass runs whenever the z
-    // length has a compiled split) do not start on 16-byte boundaries, so
-    // their elements are copied one by one.
-    constexpr int E = 16 / (int)sizeof(cpx<R>);   // elements per chunk
-    constexpr int CPR = T / E;                     // chunks per tile row
-    const int kx0 = blockIdx.x * T;
-    const bool by_elem = E > 1 && (Mx % E) != 0;
-    for (int c = 0; c < 3; ++c) {
-      cpx<R>* tile = s + c * M * T;
-      const cpx<R>* src = B2 + c * comp + (long long)ky * Mx + kx0;
-      if (by_elem) {
-        for (int k = threadIdx.x; k < nz * T; k += NT) {
-          const int z = k / T, u = k - z * T;
-          const bool ok = kx0 + u < Mx;
-          cp_async_elem<sizeof(cpx<R>)>(tile + z * T + u,
-                                        ok ? (const void*)(src + z * plane + u) : (const void*)B2, ok);
-        }
-      } else {
-        for (int k = threadIdx.x; k < nz * CPR; k += NT) {
-          const int z = k / CPR, u = k - z * CPR;
-          const bool ok = kx0 + u * E < Mx;
-          cp_async16(tile + z * T + u * E, ok ? (const void*)(src + z * plane + u * E) : (const void*)B2,
-                     ok);
-        }
-      }
-      cp_async_commit();
-    }
-  }
-  {
-    // Warm L2 with the octant entries of the Fourier-space product (fy of
-    // this block, its range of fx, every fz and component): they arrive from
-    // HBM while the forward transforms run, so the product's loads hit L2.
-    const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
-    const long long octs = (long long)hx * hy * hz;
-    int nys, na, nb;
-    const int fy = fold_axis(ky, My, nys);
-    const int kxa = blockIdx.x * T, kxb = min(kxa + T, Mx) - 1;
-    const int fa = fold_axis(kxa, Mx, na), fb = fold_axis(kxb, Mx, nb);
-    const int fmin = min(fa, fb);
-    const int fmax = (2 * kxa <= Mx && 2 * kxb >= Mx) ? Mx / 2 : max(fa, fb);
-    for (int k = threadIdx.x; k < 6 * hz; k += NT) {
-      const int c6 = k / hz, fz = k - c6 * hz;
-      const cpx<R>* row = D + c6 * octs + ((long long)fz * hy + fy) * hx;
-      prefetch_l2(row + fmin);
-      if (((size_t)(row + fmax) >> 7) != ((size_t)(row + fmin) >> 7)) prefetch_l2(row + fmax);
-    }
-  }
+  zc_stage<R, M, T, NT>(s, B2, nz, Mx, My);
+  zc_prefetch<R, M, T, NT>(D, Mx, My);
   load_tw(s_tw, tw, M, NT);
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
@@ -340,41 +390,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
     }
   }
   __syncthreads();
-  {
-    // Fourier-space product with the octant of FFT(G).  Work item (t, fz):
-    // the six octant values at (fx, fy, fz) are loaded once and applied to
-    // both kz = fz and kz = M - fz (sign flips for the components odd in z);
-    // kz = k1 + M1 k2 lives in row k1*M2 + k2.
-    const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
-    const long long octs = (long long)hx * hy * hz;
-    int nys;
-    const int fy = fold_axis(ky, My, nys);
-    const int kx0 = blockIdx.x * T;
-#pragma unroll 2
-    for (int it = threadIdx.x; it < T * hz; it += NT) {
-      const int t2 = it % T, fz = it / T;
-      const int kx2 = kx0 + t2;
-      if (kx2 >= Mx) continue;
-      int nxs;
-      const int fx = fold_axis(kx2, Mx, nxs);
-      const long long o = ((long long)fz * hy + fy) * hx + fx;
-      const cpx<R> dxx = D[o], dyy = D[3 * octs + o], dzz = D[5 * octs + o];
-      cpx<R> dxy = D[octs + o], dxz = D[2 * octs + o], dyz = D[4 * octs + o];
-      if (nxs ^ nys) dxy = mk<R>(-dxy.x, -dxy.y);
-      const int nkz = (fz == 0 || 2 * fz == M) ? 1 : 2;
-      for (int h = 0; h < nkz; ++h) {
-        const int kz = h ? M - fz : fz;
-        cpx<R> ez = dxz, fzz = dyz;
-        if (nxs ^ h) ez = mk<R>(-ez.x, -ez.y);
-        if (nys ^ h) fzz = mk<R>(-fzz.x, -fzz.y);
-        const int e = ((kz % M1) * M2 + kz / M1) * T + t2;
-        const cpx<R> vx = s[e], vy = s[M * T + e], vz = s[2 * M * T + e];
-        s[e] = dxx * vx + dxy * vy + ez * vz;
-        s[M * T + e] = dxy * vx + dyy * vy + fzz * vz;
-        s[2 * M * T + e] = ez * vx + fzz * vy + dzz * vz;
-      }
-    }
-  }
+  // kz = k1 + M1 k2 lives in row k1*M2 + k2
+  zc_product<R, M, T, NT>(s, D, Mx, My, [](int kz) { return (kz % M1) * M2 + kz / M1; });
   __syncthreads();
   if (q < M1 && kx < Mx) {
     const int k1 = q;
@@ -410,6 +427,169 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
     }
   }
 }
+
+// Three-level form of the fused z pass for the long lines (M = A B C; M1 = A,
+// M2 = B C): the M2-point transforms of the two-level form are themselves
+// split across threads, j = jc + C jb and k2 = kb + B kc:
+//   A : for each j, an A-point DFT over i (n = j + M2 i), twiddle w_M^(j k1);
+//   B1: for each (k1, jc), a B-point DFT over jb, twiddle w_M2^(jc kb);
+//   B2: for each (k1, kb), a C-point DFT over jc, giving kz = k1 + A (kb + B kc);
+// the inverse runs B2, B1, A backwards with conjugate twiddles.  A column then
+// has ~M / min(A, B, C) threads instead of max(M1, M2): at M = 1080 the three
+// spectra of 8 columns fill 211 KB of shared memory whichever form is used,
+// and this one keeps 30 warps per SM busy instead of 9.
+template <int A, int B, int C> constexpr int kQ3 =
+    (B * C > A * C ? (B * C > A * B ? B * C : A * B) : (A * C > A * B ? A * C : A * B));
+template <int A, int B, int C, int T, typename R>
+constexpr int kMinB3() {
+  const long long sm = ((long long)A * B * C * (1 + 3 * T)) * sizeof(cpx<R>);
+  const int by_smem = (int)((227LL * 1024) / sm);
+  return by_smem >= 2 ? 2 : 1;
+}
+
+template <typename R, int A, int B, int C, int T>
+__global__ void __launch_bounds__(T * kQ3<A, B, C>, (kMinB3<A, B, C, T, R>()))
+    fk_zconv3(cpx<R>* __restrict__ B2, const cpx<R>* __restrict__ D, int nz, int Mx, int My,
+              const cpx<R>* __restrict__ tw, const int* __restrict__ skip) {
+  constexpr int M1 = A, M2 = B * C, M = A * B * C, NT = T * kQ3<A, B, C>, kZin = kHalf<M1, M2>;
+  if (skip && skip[blockIdx.z]) return;
+  B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* s = s_tw + M;                      // [3][M][T]
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  const int kx = blockIdx.x * T + t;
+  const long long plane = (long long)My * Mx;
+  const long long comp = (long long)nz * plane;
+  const long long col = (long long)blockIdx.y * Mx + kx;
+  zc_stage<R, M, T, NT>(s, B2, nz, Mx, My);
+  zc_prefetch<R, M, T, NT>(D, Mx, My);
+  load_tw(s_tw, tw, M, NT);
+  // A: the staged input rows z = j + M2 i (i < kZin) -> rows k1 M2 + j
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    if (c == 0) cp_async_wait<2>();
+    else if (c == 1) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();           // this component's tile (and the twiddles) complete
+    cpx<R>* sc = s + c * M * T;
+    const int j = q;
+    cpx<R> v[M1];
+    if (q < M2) {
+#pragma unroll
+      for (int i = 0; i < M1; ++i) {
+        const int z = j + M2 * i;
+        v[i] = (i < kZin && z < nz) ? sc[z * T + t] : zero<R>();
+      }
+    }
+    __syncthreads();           // every read of the tile before the region is rewritten
+    if (q < M2) {
+      cl::Dft<R, false, M1>::run(v);
+#pragma unroll
+      for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) sc[(k1 * M2 + j) * T + t] = v[k1];
+    }
+  }
+  __syncthreads();
+  // B1: rows k1 M2 + jc + C jb -> the same rows indexed by kb
+  if (q < A * C && kx < Mx) {
+    const int k1 = q / C, jc = q - k1 * C;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cpx<R>* sc = s + c * M * T + (k1 * M2 + jc) * T + t;
+      cpx<R> u[B];
+#pragma unroll
+      for (int jb = 0; jb < B; ++jb) u[jb] = sc[C * jb * T];
+      cl::Dft<R, false, B>::run(u);
+#pragma unroll
+      for (int kb = 1; kb < B; ++kb) u[kb] = twiddle<R, false>(u[kb], s_tw[M1 * jc * kb]);
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) sc[C * kb * T] = u[kb];
+    }
+  }
+  __syncthreads();
+  // B2: rows k1 M2 + jc + C kb -> the same rows indexed by kc (kz = k1 + A (kb + B kc))
+  if (q < A * B && kx < Mx) {
+    const int k1 = q / B, kb = q - k1 * B;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cpx<R>* sc = s + c * M * T + (k1 * M2 + C * kb) * T + t;
+      cpx<R> w[C];
+#pragma unroll
+      for (int jc = 0; jc < C; ++jc) w[jc] = sc[jc * T];
+      cl::Dft<R, false, C>::run(w);
+#pragma unroll
+      for (int kc = 0; kc < C; ++kc) sc[kc * T] = w[kc];
+    }
+  }
+  __syncthreads();
+  zc_product<R, M, T, NT>(s, D, Mx, My, [](int kz) {
+    const int k1 = kz % A, k2 = kz / A, kb = k2 % B, kc = k2 / B;
+    return k1 * M2 + kc + C * kb;
+  });
+  __syncthreads();
+  // inverse B2: C-point inverse over kc, conjugate twiddle w_M2^(-jc kb)
+  if (q < A * B && kx < Mx) {
+    const int k1 = q / B, kb = q - k1 * B;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cpx<R>* sc = s + c * M * T + (k1 * M2 + C * kb) * T + t;
+      cpx<R> w[C];
+#pragma unroll
+      for (int kc = 0; kc < C; ++kc) w[kc] = sc[kc * T];
+      cl::Dft<R, true, C>::run(w);
+      if (kb > 0) {
+#pragma unroll
+        for (int jc = 1; jc < C; ++jc) w[jc] = twiddle<R, true>(w[jc], s_tw[M1 * jc * kb]);
+      }
+#pragma unroll
+      for (int jc = 0; jc < C; ++jc) sc[jc * T] = w[jc];
+    }
+  }
+  __syncthreads();
+  // inverse B1: B-point inverse over kb, conjugate twiddle w_M^(-j k1), j = jc + C jb
+  if (q < A * C && kx < Mx) {
+    const int k1 = q / C, jc = q - k1 * C;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      cpx<R>* sc = s + c * M * T + (k1 * M2 + jc) * T + t;
+      cpx<R> u[B];
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) u[kb] = sc[C * kb * T];
+      cl::Dft<R, true, B>::run(u);
+      if (k1 > 0) {
+#pragma unroll
+        for (int jb = 0; jb < B; ++jb) u[jb] = twiddle<R, true>(u[jb], s_tw[(jc + C * jb) * k1]);
+      }
+#pragma unroll
+      for (int jb = 0; jb < B; ++jb) sc[C * jb * T] = u[jb];
+    }
+  }
+  __syncthreads();
+  // inverse A: A-point inverse over k1, rows z = j + M2 i < nz stored
+  if (q < M2 && kx < Mx) {
+    const int j = q;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+      const cpx<R>* sc = s + c * M * T;
+      cpx<R> v[M1];
+#pragma unroll
+      for (int k1 = 0; k1 < M1; ++k1) v[k1] = sc[(k1 * M2 + j) * T + t];
+      cl::Dft<R, true, M1>::run(v);
+#pragma unroll
+      for (int i = 0; i < M1; ++i) {
+        const int z = j + M2 * i;
+        if (i < kZin && z < nz) B2[c * comp + z * plane + col] = v[i];
+      }
+    }
+  }
+}
+
+// Lengths whose fused z pass takes the three-level form (complex64)
+template <int M> struct Split3 { static constexpr bool on = false; static constexpr int A = 1, B = 1, C = 1; };
+template <> struct Split3<512> { static constexpr bool on = true; static constexpr int A = 8, B = 8, C = 8; };
+template <> struct Split3<1080> { static constexpr bool on = true; static constexpr int A = 12, B = 9, C = 10; };
 
 // ---------------------------------------------------------------- P1: x forward
 // gather beta*x of T rows into a [t][LD] tile, transform, store rows of
@@ -753,38 +933,72 @@ struct Passes {
   static constexpr int TZ = (size_t)(M + 3 * M * T) * sizeof(cpx<R>) <= 113 * 1024 ? T
                            : (size_t)(M + 3 * M * (T / 2)) * sizeof(cpx<R>) <= 226 * 1024 ? T / 2
                            : T / 4;
-  static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
-    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, T, true>, sm);
+  // Tile variants (lines per block) of the y passes and the z pass: 0 the
+  // default, 1 half as many lines per block.  Every variant computes each line
+  // with the same arithmetic, so the products agree bit for bit; the
+  // autotuner picks one by timing.
+  template <int TY>
+  static cudaError_t yfwd_t(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
+                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
+    const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_yfwd<R, M1, M2, TY, true>, sm);
     if (e != cudaSuccess) return e;
-    fk_yfwd<R, M1, M2, T, true><<<dim3((Mx + T - 1) / T, nz, 3 * nrhs), NT, sm, st>>>(in, out, ny, nz,
-                                                                                Mx, tw, 0, skip, 0);
+    fk_yfwd<R, M1, M2, TY, true><<<dim3((Mx + TY - 1) / TY, nz, 3 * nrhs), TY * kQ<M1, M2>, sm, st>>>(
+        in, out, ny, nz, Mx, tw, 0, skip, 0);
+    count_launch();
+    return cudaGetLastError();
+  }
+  static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
+                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var) {
+    return var == 1 ? yfwd_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st)
+                    : yfwd_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st);
+  }
+  template <int TY>
+  static cudaError_t yinv_t(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
+                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
+    const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
+    cudaError_t e = set_smem(fk_yinv<R, M1, M2, TY>, sm);
+    if (e != cudaSuccess) return e;
+    fk_yinv<R, M1, M2, TY><<<dim3((Mx + TY - 1) / TY, nz, 3 * nrhs), TY * kQ<M1, M2>, sm, st>>>(
+        in, out, ny, nz, Mx, tw, skip);
     count_launch();
     return cudaGetLastError();
   }
   static cudaError_t yinv(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + M * T) * sizeof(cpx<R>);
-    cudaError_t e = set_smem(fk_yinv<R, M1, M2, T>, sm);
-    if (e != cudaSuccess) return e;
-    fk_yinv<R, M1, M2, T><<<dim3((Mx + T - 1) / T, nz, 3 * nrhs), NT, sm, st>>>(in, out, ny, nz,
-                                                                                Mx, tw, skip);
-    count_launch();
-    return cudaGetLastError();
+                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var) {
+    return var == 1 ? yinv_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st)
+                    : yinv_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st);
+  }
+  template <int TC>
+  static cudaError_t zconv_t(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
+                             int nrhs, const int* skip, cudaStream_t st) {
+    const size_t sm = (size_t)(M + 3 * M * TC) * sizeof(cpx<R>);
+    if constexpr (std::is_same<R, float>::value && Split3<M>::on) {
+      using S3 = Split3<M>;
+      auto k = fk_zconv3<R, S3::A, S3::B, S3::C, TC>;
+      cudaError_t e = set_smem(k, sm);
+      if (e != cudaSuccess) return e;
+      if ((e = ensure_carveout_max((const void*)k)) != cudaSuccess) return e;
+      k<<<dim3((Mx + TC - 1) / TC, My, nrhs), TC * kQ3<S3::A, S3::B, S3::C>, sm, st>>>(B2, D, nz, Mx, My,
+                                                                                   tw, skip);
+      count_launch();
+      return cudaGetLastError();
+    } else {
+      cudaError_t e = set_smem(fk_zconv<R, M1, M2, TC>, sm);
+      if (e != cudaSuccess) return e;
+      // two ~106 KB blocks per SM need the largest shared-memory carveout
+      e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TC>);
+      if (e != cudaSuccess) return e;
+      fk_zconv<R, M1, M2, TC><<<dim3((Mx + TC - 1) / TC, My, nrhs), TC * kQ<M1, M2>, sm, st>>>(
+          B2, D, nz, Mx, My, tw, skip);
+      count_launch();
+      return cudaGetLastError();
+    }
   }
   static cudaError_t zconv(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
-                           int nrhs, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + 3 * M * TZ) * sizeof(cpx<R>);
-    cudaError_t e = set_smem(fk_zconv<R, M1, M2, TZ>, sm);
-    if (e != cudaSuccess) return e;
-    // two ~106 KB blocks per SM need the largest shared-memory carveout
-    e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TZ>);
-    if (e != cudaSuccess) return e;
-    fk_zconv<R, M1, M2, TZ><<<dim3((Mx + TZ - 1) / TZ, My, nrhs), TZ * kQ<M1, M2>, sm, st>>>(
-        B2, D, nz, Mx, My, tw, skip);
-    count_launch();
-    return cudaGetLastError();
+                           int nrhs, const int* skip, cudaStream_t st, int var) {
+    return var == 1 ? zconv_t<TZ / 2>(B2, D, nz, Mx, My, tw, nrhs, skip, st)
+                    : zconv_t<TZ>(B2, D, nz, Mx, My, tw, nrhs, skip, st);
   }
   using V = typename VecOf<R>::type;
   static cudaError_t xfwd(const V* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,

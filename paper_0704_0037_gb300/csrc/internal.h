@@ -47,6 +47,11 @@ struct Geom {
   FftPlan px, py, pz;      // plans for lengths Mx, My, Mz
   Tracer* tr = nullptr;    // per-kernel timing, owned by the handle
   int engine = 0;          // 0: register-resident passes where available; 1: Stockham only
+  // tile variants of the register-resident y forward, z and y inverse
+  // passes per arithmetic (0 complex64, 1 complex128, 2 double-float): -1
+  // not yet chosen (the autotuner picks at the D-matrix build), else the
+  // variant of FastArgs::var_*
+  int tiles[3][3] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
   long long oct() const { return (long long)(Mx / 2 + 1) * (My / 2 + 1) * (Mz / 2 + 1); }
   long long b1() const { return 3LL * nrows * Mx; }          // [3][nz][ny][Mx]
   long long b2() const { return 3LL * nz * My * Mx; }        // [3][nz][My][Mx]
@@ -115,6 +120,15 @@ cudaError_t launch_lines(const Geom& g, const cpx<R>* in, cpx<R>* out, const Fft
 cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, const c128* beta,
                              int n_mat, const c128* x, c128* y, int nrhs, cudaStream_t st,
                              const int* skip = nullptr);
+
+// Autotuner of the tile variants of the register-resident y forward, z and
+// y inverse passes (Geom::tiles[kind], kind 0 complex64 / 1 complex128 /
+// 2 double-float): each variant of each pass timed with CUDA events on the
+// handle's own buffers (one warm-up and three timed launches of one
+// right-hand side), the faster kept; entries already >= 0 are left alone.
+// Choices are cached per device and grid shape.  Needs w's buffers and D.
+template <typename R>
+cudaError_t tune_tiles(Geom& g, const LatticeDev& lat, Work<R>& w, cudaStream_t st);
 
 FftPlan make_plan(int M);
 int smooth_size(int lo);
@@ -260,6 +274,9 @@ struct FastArgs {
   // FP_SFULL: element offset between the outer groups of lines (0: M times
   // the element stride, i.e. whole line sets one after another)
   long long ostride = 0;
+  // tile variants of FP_YFWD, FP_ZCONV, FP_YINV (0: default lines per block,
+  // 1: half as many; the same product bit for bit)
+  int var_yf = 0, var_z = 0, var_yi = 0;
 };
 // number of (re, im) partials FP_XINV writes to dotp for nrows rows
 inline int fast_xinv_blocks(int nrows, bool fp32) { return 3 * ((nrows + (fp32 ? 16 : 8) - 1) / (fp32 ? 16 : 8)); }

@@ -14,6 +14,10 @@
 //       keep z < n_z; in place in B2
 //   P4  inverse y-FFT, keep y < n_y                          -> B1
 //   P5  inverse x-FFT, keep the occupied x, y = x - beta u   -> compact y
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 
 namespace dda {
@@ -342,6 +346,10 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
     fa.lat = lat; fa.beta = br; fa.D = w.D; fa.n_occ = g.n_occ; fa.nrows = g.nrows;
     fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = adjoint; fa.st = st;
     fa.nrhs = cnt; fa.bstride = bstride; fa.skip = sk;
+    {
+      const int* tl = g.tiles[std::is_same<R, float>::value ? 0 : 1];
+      fa.var_yf = tl[0] > 0 ? tl[0] : 0; fa.var_z = tl[1] > 0 ? tl[1] : 0; fa.var_yi = tl[2] > 0 ? tl[2] : 0;
+    }
     dim3 g1((g.nrows + (1 << lt1) - 1) >> lt1, 3 * cnt);
     const int tb = sizeof(R) == 4 ? TR_P1_C64 : TR_P1_C128;
     // P1: x lines of the occupied rows, gather and beta -> B1 [rhs][3][nz][ny][Mx]
@@ -443,6 +451,9 @@ cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, 
     fa.lat = lat; fa.beta = w.beta + (long long)r0 * bstride; fa.D = w.D; fa.n_occ = g.n_occ;
     fa.nrows = g.nrows; fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = false;
     fa.st = st; fa.nrhs = cnt; fa.bstride = bstride; fa.skip = skip ? skip + r0 : nullptr;
+    fa.var_yf = g.tiles[2][0] > 0 ? g.tiles[2][0] : 0;
+    fa.var_z = g.tiles[2][1] > 0 ? g.tiles[2][1] : 0;
+    fa.var_yi = g.tiles[2][2] > 0 ? g.tiles[2][2] : 0;
     tr_begin(g.tr, st);
     fa.in = x + r0 * nv; fa.out = w.B1; fa.tw = twx;
     if ((e = fast_pass<df>(g.Mx, FP_XFWD, fa)) != cudaSuccess) return e;
@@ -466,6 +477,73 @@ cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, 
   }
   return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t tune_tiles(Geom& g, const LatticeDev& lat, Work<R>& w, cudaStream_t st) {
+  const int kind = std::is_same<R, float>::value ? 0 : std::is_same<R, double>::value ? 1 : 2;
+  int* tl = g.tiles[kind];
+  if (tl[0] >= 0 && tl[1] >= 0 && tl[2] >= 0) return cudaSuccess;
+  auto has = [](int M) { return std::is_same<R, float>::value ? fast_supported_c64(M) : fast_supported(M); };
+  if (g.engine != 0 || !w.B1 || !w.B2 || !w.D || !w.tw) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::array<int, 8>, std::array<int, 3>> cache;
+  const std::array<int, 8> key{dev, kind, g.Mx, g.My, g.Mz, g.ny, g.nz, 0};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      for (int k = 0; k < 3; ++k)
+        if (tl[k] < 0) tl[k] = it->second[k];
+      return cudaSuccess;
+    }
+  }
+  FastArgs fa{};
+  fa.lat = lat; fa.D = w.D; fa.n_occ = g.n_occ; fa.nrows = g.nrows;
+  fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.st = st; fa.nrhs = 1;
+  const cpx<R>* twy = w.tw + g.Mx;
+  const cpx<R>* twz = w.tw + g.Mx + g.My;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  std::array<int, 3> best{0, 0, 0};
+  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass) {
+    if (!has(pass == 1 ? g.Mz : g.My)) continue;       // that axis runs the Stockham passes
+    float tbest = 0.f;
+    for (int var = 0; var < 2 && e == cudaSuccess; ++var) {
+      FastArgs a = fa;
+      int op, M;
+      if (pass == 0) { op = FP_YFWD; M = g.My; a.in = w.B1; a.out = w.B2; a.tw = twy; a.var_yf = var; }
+      else if (pass == 1) { op = FP_ZCONV; M = g.Mz; a.out = w.B2; a.tw = twz; a.var_z = var; }
+      else { op = FP_YINV; M = g.My; a.in = w.B2; a.out = w.B1; a.tw = twy; a.var_yi = var; }
+      if ((e = fast_pass<R>(M, op, a)) != cudaSuccess) break;   // warm-up (attributes, code)
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = fast_pass<R>(M, op, a);
+      if (e != cudaSuccess) break;
+      if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+      if (var == 0 || ms < tbest) { tbest = ms; best[pass] = var; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (tl[k] < 0) tl[k] = best[k];
+  return cudaSuccess;
+}
+
+template cudaError_t tune_tiles<float>(Geom&, const LatticeDev&, Work<float>&, cudaStream_t);
+template cudaError_t tune_tiles<double>(Geom&, const LatticeDev&, Work<double>&, cudaStream_t);
+template cudaError_t tune_tiles<df>(Geom&, const LatticeDev&, Work<df>&, cudaStream_t);
 
 template cudaError_t launch_matvec<float>(const Geom&, const LatticeDev&, Work<float>&,
                                           const c64*, int, const c64*, c64*, int, bool,

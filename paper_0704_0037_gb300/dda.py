@@ -39,7 +39,8 @@ EXPORTS = ("dda_init_lattice", "dda_build_Dmatrix", "dda_set_beta", "dda_matvec"
            "dda_orientation_average",
            "dda_farfield_noalloc", "dda_trace",
            "dda_trace_read", "dda_n_occ", "dda_kd", "dda_grid", "dda_positions", "dda_last_error",
-           "dda_free", "dda_release_cached_memory", "dda_set_fft_engine", "dda_set_memory_limit",
+           "dda_free", "dda_release_cached_memory", "dda_set_fft_engine", "dda_set_pass_tiles",
+           "dda_get_pass_tiles", "dda_set_memory_limit",
            "dda_memory_in_use", "dda_residual", "dda_checkpoint_bytes", "dda_pcnet_create",
            "dda_pcnet_free", "dda_pcnet_params", "dda_pcnet_last_error", "dda_pcnet_get_weights",
            "dda_pcnet_set_weights", "dda_pcnet_get_grads", "dda_pcnet_apply", "dda_pcnet_train_step",
@@ -92,6 +93,8 @@ def lib():
                               _dp, ctypes.c_double, _ip, _vp], _ip),
         "dda_build_Dmatrix": ([_vp, _ip], _ip),
         "dda_set_fft_engine": ([_vp, _ip], _ip),
+        "dda_set_pass_tiles": ([_vp, _ip, ctypes.POINTER(ctypes.c_int)], _ip),
+        "dda_get_pass_tiles": ([_vp, _ip, ctypes.POINTER(ctypes.c_int)], _ip),
         "dda_set_memory_limit": ([ctypes.c_ulonglong], _ip),
         "dda_memory_in_use": ([ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)], _ip),
         "dda_set_beta": ([_vp, _ip, _ip, _dp, _dp], _ip),
@@ -204,6 +207,19 @@ def dda_init_lattice(occ, m_list, kd, volume_corrected=False, stream=None):
 
 def dda_set_fft_engine(h, engine):
     return _check(h, lib().dda_set_fft_engine(h, int(engine)))
+
+
+def dda_set_pass_tiles(h, prec, tiles=None):
+    """Tile variants (y forward, z, y inverse) of one arithmetic's products:
+    0 default, 1 half the lines per block, -1 autotuned (None: all -1)."""
+    arr = None if tiles is None else (ctypes.c_int * 3)(*[int(t) for t in tiles])
+    return _check(h, lib().dda_set_pass_tiles(h, int(prec), arr))
+
+
+def dda_get_pass_tiles(h, prec):
+    arr = (ctypes.c_int * 3)()
+    _check(h, lib().dda_get_pass_tiles(h, int(prec), arr))
+    return tuple(arr)
 
 
 def dda_set_memory_limit(nbytes):
