@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "df"],
                     help="products workload: complex64, complex128 or double-float product")
     ap.add_argument("--products", type=int, default=3, help="products workload: count")
+    ap.add_argument("--box", default="",
+                    help="products workload: an ellipsoid inscribed in an nx,ny,nz box instead of "
+                         "the sphere (e.g. 100,100,540)")
     ap.add_argument("--engine", default="auto", choices=["auto", "stockham"],
                     help="products workload: FFT engine (register-resident passes where compiled, "
                          "or the shared-memory Stockham passes for every length)")
@@ -798,7 +801,11 @@ def run_products(args):
     import torch
     from paper_0704_0037_gb300 import build, dda, inputs
     build.build()
-    occ = inputs.sphere(args.n)
+    if args.box:
+        nx, ny, nz = (int(v) for v in args.box.split(","))
+        occ = inputs.ellipsoid(nx, ny, nz)
+    else:
+        occ = inputs.sphere(args.n)
     engine = dda.DDA_ENGINE_STOCKHAM if args.engine == "stockham" else None
     p = dda.Particle(occ, [args.m], args.x, volume_corrected=True, engine=engine)
     prec = {"fp32": dda.DDA_FP32_REFINED, "fp64": dda.DDA_FP64, "df": dda.DDA_FP64_PAIR}[args.prec]
@@ -826,7 +833,8 @@ def run_products(args):
              if k != "all_launches"}
     dda.dda_trace(p.h, False)
     p.close()
-    return {"workload": "products", "n_box": args.n, "grid": list(p.grid), "prec": args.prec,
+    return {"workload": "products", "n_box": args.n, "box": args.box or None, "grid": list(p.grid),
+            "prec": args.prec,
             "engine": args.engine,
             "products": args.products, "ms_per_product": ms, "ms_per_pass": trace}
 

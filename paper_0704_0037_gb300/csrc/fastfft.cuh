@@ -428,169 +428,6 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
   }
 }
 
-// Three-level form of the fused z pass for the long lines (M = A B C; M1 = A,
-// M2 = B C): the M2-point transforms of the two-level form are themselves
-// split across threads, j = jc + C jb and k2 = kb + B kc:
-//   A : for each j, an A-point DFT over i (n = j + M2 i), twiddle w_M^(j k1);
-//   B1: for each (k1, jc), a B-point DFT over jb, twiddle w_M2^(jc kb);
-//   B2: for each (k1, kb), a C-point DFT over jc, giving kz = k1 + A (kb + B kc);
-// the inverse runs B2, B1, A backwards with conjugate twiddles.  A column then
-// has ~M / min(A, B, C) threads instead of max(M1, M2): at M = 1080 the three
-// spectra of 8 columns fill 211 KB of shared memory whichever form is used,
-// and this one keeps 30 warps per SM busy instead of 9.
-template <int A, int B, int C> constexpr int kQ3 =
-    (B * C > A * C ? (B * C > A * B ? B * C : A * B) : (A * C > A * B ? A * C : A * B));
-template <int A, int B, int C, int T, typename R>
-constexpr int kMinB3() {
-  const long long sm = ((long long)A * B * C * (1 + 3 * T)) * sizeof(cpx<R>);
-  const int by_smem = (int)((227LL * 1024) / sm);
-  return by_smem >= 2 ? 2 : 1;
-}
-
-template <typename R, int A, int B, int C, int T>
-__global__ void __launch_bounds__(T * kQ3<A, B, C>, (kMinB3<A, B, C, T, R>()))
-    fk_zconv3(cpx<R>* __restrict__ B2, const cpx<R>* __restrict__ D, int nz, int Mx, int My,
-              const cpx<R>* __restrict__ tw, const int* __restrict__ skip) {
-  constexpr int M1 = A, M2 = B * C, M = A * B * C, NT = T * kQ3<A, B, C>, kZin = kHalf<M1, M2>;
-  if (skip && skip[blockIdx.z]) return;
-  B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* s = s_tw + M;                      // [3][M][T]
-  const int t = threadIdx.x % T, q = threadIdx.x / T;
-  const int kx = blockIdx.x * T + t;
-  const long long plane = (long long)My * Mx;
-  const long long comp = (long long)nz * plane;
-  const long long col = (long long)blockIdx.y * Mx + kx;
-  zc_stage<R, M, T, NT>(s, B2, nz, Mx, My);
-  zc_prefetch<R, M, T, NT>(D, Mx, My);
-  load_tw(s_tw, tw, M, NT);
-  // A: the staged input rows z = j + M2 i (i < kZin) -> rows k1 M2 + j
-#pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
-    if (c == 0) cp_async_wait<2>();
-    else if (c == 1) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    __syncthreads();           // this component's tile (and the twiddles) complete
-    cpx<R>* sc = s + c * M * T;
-    const int j = q;
-    cpx<R> v[M1];
-    if (q < M2) {
-#pragma unroll
-      for (int i = 0; i < M1; ++i) {
-        const int z = j + M2 * i;
-        v[i] = (i < kZin && z < nz) ? sc[z * T + t] : zero<R>();
-      }
-    }
-    __syncthreads();           // every read of the tile before the region is rewritten
-    if (q < M2) {
-      cl::Dft<R, false, M1>::run(v);
-#pragma unroll
-      for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
-#pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) sc[(k1 * M2 + j) * T + t] = v[k1];
-    }
-  }
-  __syncthreads();
-  // B1: rows k1 M2 + jc + C jb -> the same rows indexed by kb
-  if (q < A * C && kx < Mx) {
-    const int k1 = q / C, jc = q - k1 * C;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      cpx<R>* sc = s + c * M * T + (k1 * M2 + jc) * T + t;
-      cpx<R> u[B];
-#pragma unroll
-      for (int jb = 0; jb < B; ++jb) u[jb] = sc[C * jb * T];
-      cl::Dft<R, false, B>::run(u);
-#pragma unroll
-      for (int kb = 1; kb < B; ++kb) u[kb] = twiddle<R, false>(u[kb], s_tw[M1 * jc * kb]);
-#pragma unroll
-      for (int kb = 0; kb < B; ++kb) sc[C * kb * T] = u[kb];
-    }
-  }
-  __syncthreads();
-  // B2: rows k1 M2 + jc + C kb -> the same rows indexed by kc (kz = k1 + A (kb + B kc))
-  if (q < A * B && kx < Mx) {
-    const int k1 = q / B, kb = q - k1 * B;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      cpx<R>* sc = s + c * M * T + (k1 * M2 + C * kb) * T + t;
-      cpx<R> w[C];
-#pragma unroll
-      for (int jc = 0; jc < C; ++jc) w[jc] = sc[jc * T];
-      cl::Dft<R, false, C>::run(w);
-#pragma unroll
-      for (int kc = 0; kc < C; ++kc) sc[kc * T] = w[kc];
-    }
-  }
-  __syncthreads();
-  zc_product<R, M, T, NT>(s, D, Mx, My, [](int kz) {
-    const int k1 = kz % A, k2 = kz / A, kb = k2 % B, kc = k2 / B;
-    return k1 * M2 + kc + C * kb;
-  });
-  __syncthreads();
-  // inverse B2: C-point inverse over kc, conjugate twiddle w_M2^(-jc kb)
-  if (q < A * B && kx < Mx) {
-    const int k1 = q / B, kb = q - k1 * B;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      cpx<R>* sc = s + c * M * T + (k1 * M2 + C * kb) * T + t;
-      cpx<R> w[C];
-#pragma unroll
-      for (int kc = 0; kc < C; ++kc) w[kc] = sc[kc * T];
-      cl::Dft<R, true, C>::run(w);
-      if (kb > 0) {
-#pragma unroll
-        for (int jc = 1; jc < C; ++jc) w[jc] = twiddle<R, true>(w[jc], s_tw[M1 * jc * kb]);
-      }
-#pragma unroll
-      for (int jc = 0; jc < C; ++jc) sc[jc * T] = w[jc];
-    }
-  }
-  __syncthreads();
-  // inverse B1: B-point inverse over kb, conjugate twiddle w_M^(-j k1), j = jc + C jb
-  if (q < A * C && kx < Mx) {
-    const int k1 = q / C, jc = q - k1 * C;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      cpx<R>* sc = s + c * M * T + (k1 * M2 + jc) * T + t;
-      cpx<R> u[B];
-#pragma unroll
-      for (int kb = 0; kb < B; ++kb) u[kb] = sc[C * kb * T];
-      cl::Dft<R, true, B>::run(u);
-      if (k1 > 0) {
-#pragma unroll
-        for (int jb = 0; jb < B; ++jb) u[jb] = twiddle<R, true>(u[jb], s_tw[(jc + C * jb) * k1]);
-      }
-#pragma unroll
-      for (int jb = 0; jb < B; ++jb) sc[C * jb * T] = u[jb];
-    }
-  }
-  __syncthreads();
-  // inverse A: A-point inverse over k1, rows z = j + M2 i < nz stored
-  if (q < M2 && kx < Mx) {
-    const int j = q;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      const cpx<R>* sc = s + c * M * T;
-      cpx<R> v[M1];
-#pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) v[k1] = sc[(k1 * M2 + j) * T + t];
-      cl::Dft<R, true, M1>::run(v);
-#pragma unroll
-      for (int i = 0; i < M1; ++i) {
-        const int z = j + M2 * i;
-        if (i < kZin && z < nz) B2[c * comp + z * plane + col] = v[i];
-      }
-    }
-  }
-}
-
-// Lengths whose fused z pass takes the three-level form (complex64)
-template <int M> struct Split3 { static constexpr bool on = false; static constexpr int A = 1, B = 1, C = 1; };
-template <> struct Split3<512> { static constexpr bool on = true; static constexpr int A = 8, B = 8, C = 8; };
-template <> struct Split3<1080> { static constexpr bool on = true; static constexpr int A = 12, B = 9, C = 10; };
-
 // ---------------------------------------------------------------- P1: x forward
 // gather beta*x of T rows into a [t][LD] tile, transform, store rows of
 // B1 [3][nrows][M]; grid (ceil(nrows/T), 3)
@@ -973,27 +810,15 @@ struct Passes {
   static cudaError_t zconv_t(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
                              int nrhs, const int* skip, cudaStream_t st) {
     const size_t sm = (size_t)(M + 3 * M * TC) * sizeof(cpx<R>);
-    if constexpr (std::is_same<R, float>::value && Split3<M>::on) {
-      using S3 = Split3<M>;
-      auto k = fk_zconv3<R, S3::A, S3::B, S3::C, TC>;
-      cudaError_t e = set_smem(k, sm);
-      if (e != cudaSuccess) return e;
-      if ((e = ensure_carveout_max((const void*)k)) != cudaSuccess) return e;
-      k<<<dim3((Mx + TC - 1) / TC, My, nrhs), TC * kQ3<S3::A, S3::B, S3::C>, sm, st>>>(B2, D, nz, Mx, My,
-                                                                                   tw, skip);
-      count_launch();
-      return cudaGetLastError();
-    } else {
-      cudaError_t e = set_smem(fk_zconv<R, M1, M2, TC>, sm);
-      if (e != cudaSuccess) return e;
-      // two ~106 KB blocks per SM need the largest shared-memory carveout
-      e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TC>);
-      if (e != cudaSuccess) return e;
-      fk_zconv<R, M1, M2, TC><<<dim3((Mx + TC - 1) / TC, My, nrhs), TC * kQ<M1, M2>, sm, st>>>(
-          B2, D, nz, Mx, My, tw, skip);
-      count_launch();
-      return cudaGetLastError();
-    }
+    cudaError_t e = set_smem(fk_zconv<R, M1, M2, TC>, sm);
+    if (e != cudaSuccess) return e;
+    // two ~106 KB blocks per SM need the largest shared-memory carveout
+    e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TC>);
+    if (e != cudaSuccess) return e;
+    fk_zconv<R, M1, M2, TC><<<dim3((Mx + TC - 1) / TC, My, nrhs), TC * kQ<M1, M2>, sm, st>>>(
+        B2, D, nz, Mx, My, tw, skip);
+    count_launch();
+    return cudaGetLastError();
   }
   static cudaError_t zconv(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
                            int nrhs, const int* skip, cudaStream_t st, int var) {

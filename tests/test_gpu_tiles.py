@@ -53,6 +53,34 @@ def test_every_tile_variant_gives_the_same_product(name, occ, m, grid, form):
             assert torch.equal(y, ys[0]), v
 
 
+# the three-level z pass of the long complex64 lines (512 = 8 x 8 x 8,
+# 1080 = 12 x 9 x 10), the other axes Stockham
+LONG_Z = [("ellipsoid6x5x256", inputs.ellipsoid(6, 5, 256), 512),
+          ("ellipsoid4x3x540", inputs.ellipsoid(4, 3, 540), 1080)]
+
+
+@pytest.mark.parametrize("name,occ,mz", LONG_Z, ids=[c[0] for c in LONG_Z])
+@pytest.mark.parametrize("adjoint", [False, True], ids=["product", "adjoint"])
+def test_long_z_tile_variants_give_the_same_product(name, occ, mz, adjoint):
+    torch, dda = need_gpu()
+    p = dda.Particle(occ, [1.4 + 0.02j], 0.6)
+    with p:
+        assert p.grid[2] == mz
+        dda.dda_build_Dmatrix(p.h, dda.DDA_FP32_REFINED)
+        assert dda.dda_get_pass_tiles(p.h, dda.DDA_FP32_REFINED)[1] in (0, 1)
+        dda.dda_set_beta(p.h, dda.DDA_LDR, [(0.0, 0.0, 1.0)], [(1.0, 0.0, 0.0)])
+        x = torch.from_numpy(inputs.random_vectors(4, 1, p.n_occ)).to("cuda", torch.complex64)
+        f = dda.dda_matvec_adjoint if adjoint else dda.dda_matvec
+        ys = []
+        for v in ((0, 0, 0), (0, 1, 0)):
+            dda.dda_set_pass_tiles(p.h, dda.DDA_FP32_REFINED, v)
+            y = torch.empty_like(x)
+            f(p.h, dda.DDA_FP32_REFINED, x, y, 1)
+            torch.cuda.synchronize()
+            ys.append(y)
+        assert torch.equal(ys[0], ys[1])
+
+
 def test_pinned_tiles_survive_a_rebuild_and_bad_values_are_refused():
     torch, dda = need_gpu()
     p = dda.Particle(inputs.sphere(16), [1.5], 0.7)
