@@ -224,58 +224,66 @@ __device__ __forceinline__ int fold_axis(int k, int M, int& neg) {
   return k;
 }
 
-// Pieces of the fused z pass shared by its two- and three-level forms.  A
-// block holds T adjacent columns (kx) of one ky and right-hand side; s is
-// [3][M][T] (component, row, column) in shared memory.
+// Shared-memory rows of one component of the fused z pass: row k1 M2 + j of
+// the two-level split (j < M2) lives in physical row k1 (M2 + 1) + j when a
+// tile row is narrower than the 32 banks (T complex64 < 16 columns), so that
+// the rows M2 apart read together by the second phase fall in different
+// banks; otherwise in row k1 M2 + j.
+template <typename R, int M1, int M2, int T>
+struct ZRows {
+  static constexpr bool pad = T * (int)sizeof(cpx<R>) < 128;
+  static constexpr int rows = pad ? M1 * M2 + M1 : M1 * M2;
+  // physical row of row k1 M2 + j (j < M2)
+  static __device__ __forceinline__ int at(int k1, int j) { return k1 * (pad ? M2 + 1 : M2) + j; }
+};
+
+// Pieces of the fused z pass.  A tile is T adjacent columns (kx from bx T) of
+// one ky; s is [3][rows][T] (component, row, column) in shared memory.
 //
-// Stage the nz x T input tile of every component in the first nz rows of
-// that component's own region of s: asynchronous 16-byte copies, all three
-// components in flight at once (three commit groups; the region is free until
-// the component's first phase overwrites it).  Chunks past the last column
-// are zero-filled without reading.  Rows of an odd number of complex64
-// elements (x padded to an odd length: this z pass runs whenever the z length
-// has a compiled split) do not start on 16-byte boundaries, so their elements
-// are copied one by one.
-template <typename R, int M, int T, int NT>
-__device__ __forceinline__ void zc_stage(cpx<R>* s, const cpx<R>* B2, int nz, int Mx, int My) {
+// Stage the nz x T input tile of component c in the first nz rows of that
+// component's own region (its first transform phase reads it all before
+// overwriting the region): asynchronous 16-byte copies, one commit group per
+// call.  Chunks past the last column are zero-filled without reading.  Rows
+// of an odd number of complex64 elements (x padded to an odd length: this z
+// pass runs whenever the z length has a compiled split) do not start on
+// 16-byte boundaries, so their elements are copied one by one.
+template <typename R, int T, int NT>
+__device__ __forceinline__ void zc_stage(cpx<R>* tile, const cpx<R>* B2, int c, int nz, int Mx,
+                                         int My, int bx, int ky) {
   constexpr int E = 16 / (int)sizeof(cpx<R>);   // elements per chunk
   constexpr int CPR = T / E;                     // chunks per tile row
   const long long plane = (long long)My * Mx;
-  const long long comp = (long long)nz * plane;
-  const int kx0 = blockIdx.x * T, ky = blockIdx.y;
+  const int kx0 = bx * T;
   const bool by_elem = E > 1 && (Mx % E) != 0;
-  for (int c = 0; c < 3; ++c) {
-    cpx<R>* tile = s + c * M * T;
-    const cpx<R>* src = B2 + c * comp + (long long)ky * Mx + kx0;
-    if (by_elem) {
-      for (int k = threadIdx.x; k < nz * T; k += NT) {
-        const int z = k / T, u = k - z * T;
-        const bool ok = kx0 + u < Mx;
-        cp_async_elem<sizeof(cpx<R>)>(tile + z * T + u,
-                                      ok ? (const void*)(src + z * plane + u) : (const void*)B2, ok);
-      }
-    } else {
-      for (int k = threadIdx.x; k < nz * CPR; k += NT) {
-        const int z = k / CPR, u = k - z * CPR;
-        const bool ok = kx0 + u * E < Mx;
-        cp_async16(tile + z * T + u * E, ok ? (const void*)(src + z * plane + u * E) : (const void*)B2,
-                   ok);
-      }
+  const cpx<R>* src = B2 + c * (long long)nz * plane + (long long)ky * Mx + kx0;
+  if (by_elem) {
+    for (int k = threadIdx.x; k < nz * T; k += NT) {
+      const int z = k / T, u = k - z * T;
+      const bool ok = kx0 + u < Mx;
+      cp_async_elem<sizeof(cpx<R>)>(tile + z * T + u,
+                                    ok ? (const void*)(src + z * plane + u) : (const void*)B2, ok);
     }
-    cp_async_commit();
+  } else {
+    for (int k = threadIdx.x; k < nz * CPR; k += NT) {
+      const int z = k / CPR, u = k - z * CPR;
+      const bool ok = kx0 + u * E < Mx;
+      cp_async16(tile + z * T + u * E, ok ? (const void*)(src + z * plane + u * E) : (const void*)B2,
+                 ok);
+    }
   }
+  cp_async_commit();
 }
 
-// Warm L2 with the octant entries of the Fourier-space product (fy of this
-// block, its range of fx, every fz and component): they arrive from HBM while
-// the forward transforms run, so the product's loads hit L2.
+// Warm L2 with the octant entries of the Fourier-space product of a tile (fy
+// of its ky, its range of fx, every fz and component): they arrive from HBM
+// while the forward transforms run, so the product's loads hit L2.
 template <typename R, int M, int T, int NT>
-__device__ __forceinline__ void zc_prefetch(const cpx<R>* D, int Mx, int My) {
+__device__ __forceinline__ void zc_prefetch(const cpx<R>* D, int Mx, int My, int bx, int ky) {
   const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
   const long long octs = (long long)hx * hy * hz;
   int nys, na, nb;
-  const int fy = fold_axis(blockIdx.y, My, nys);
-  const int kxa = blockIdx.x * T, kxb = min(kxa + T, Mx) - 1;
+  const int fy = fold_axis(ky, My, nys);
+  const int kxa = bx * T, kxb = min(kxa + T, Mx) - 1;
   const int fa = fold_axis(kxa, Mx, na), fb = fold_axis(kxb, Mx, nb);
   const int fmin = min(fa, fb);
   const int fmax = (2 * kxa <= Mx && 2 * kxb >= Mx) ? Mx / 2 : max(fa, fb);
@@ -290,15 +298,16 @@ __device__ __forceinline__ void zc_prefetch(const cpx<R>* D, int Mx, int My) {
 // Fourier-space product with the octant of FFT(G).  Work item (t, fz): the
 // six octant values at (fx, fy, fz) are loaded once and applied to both
 // kz = fz and kz = M - fz (sign flips for the components odd in z); the
-// spectrum value kz of column t lives in row row_of(kz).
-template <typename R, int M, int T, int NT, typename RowOf>
+// spectrum value kz of column t lives in row row_of(kz); components are CS
+// elements apart.
+template <typename R, int M, int T, int NT, int CS, typename RowOf>
 __device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__ D, int Mx, int My,
-                                           RowOf row_of) {
+                                           int bx, int ky, RowOf row_of) {
   const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
   const long long octs = (long long)hx * hy * hz;
   int nys;
-  const int fy = fold_axis(blockIdx.y, My, nys);
-  const int kx0 = blockIdx.x * T;
+  const int fy = fold_axis(ky, My, nys);
+  const int kx0 = bx * T;
 #pragma unroll 2
   for (int it = threadIdx.x; it < T * hz; it += NT) {
     const int t2 = it % T, fz = it / T;
@@ -317,44 +326,33 @@ __device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__
       if (nxs ^ h) ez = mk<R>(-ez.x, -ez.y);
       if (nys ^ h) fzz = mk<R>(-fzz.x, -fzz.y);
       const int e = row_of(kz) * T + t2;
-      const cpx<R> vx = s[e], vy = s[M * T + e], vz = s[2 * M * T + e];
+      const cpx<R> vx = s[e], vy = s[CS + e], vz = s[2 * CS + e];
       s[e] = dxx * vx + dxy * vy + ez * vz;
-      s[M * T + e] = dxy * vx + dyy * vy + fzz * vz;
-      s[2 * M * T + e] = ez * vx + fzz * vy + dzz * vz;
+      s[CS + e] = dxy * vx + dyy * vy + fzz * vz;
+      s[2 * CS + e] = ez * vx + fzz * vy + dzz * vz;
     }
   }
 }
 
-template <typename R, int M1, int M2, int T>
-__global__ void __launch_bounds__(T * kQ<M1, M2>,
-                                  kMinB(T * kQ<M1, M2>, 2, (M1 * M2 + 3LL * M1 * M2 * T) * sizeof(cpx<R>)))
-    fk_zconv(cpx<R>* __restrict__ B2,
-                                                           const cpx<R>* __restrict__ D, int nz,
-                                                           int Mx, int My,
-                                                           const cpx<R>* __restrict__ tw,
-                                                           const int* __restrict__ skip) {
-  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, kZin = kHalf<M1, M2>;
-  if (skip && skip[blockIdx.z]) return;
-  B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* s = s_tw + M;                      // [3][M][T]
+// Forward z transforms of the three staged components of a tile (phase 1
+// waits for each component's copies), the product, and the inverse z
+// transforms up to the inverse phase A of every component; the caller runs
+// inverse phase B (zc_inverse_b) per component.
+template <typename R, int M1, int M2, int T, int NT>
+__device__ __forceinline__ void zc_forward_product_inva(cpx<R>* s, const cpx<R>* s_tw,
+                                                       const cpx<R>* __restrict__ D, int nz, int Mx,
+                                                       int My, int bx, int ky) {
+  using Z = ZRows<R, M1, M2, T>;
+  constexpr int M = M1 * M2, CS = Z::rows * T, kZin = kHalf<M1, M2>;
   const int t = threadIdx.x % T, q = threadIdx.x / T;
-  const int kx = blockIdx.x * T + t;
-  const int ky = blockIdx.y;
-  const long long plane = (long long)My * Mx;
-  const long long comp = (long long)nz * plane;
-  const long long col = (long long)ky * Mx + kx;
-  zc_stage<R, M, T, NT>(s, B2, nz, Mx, My);
-  zc_prefetch<R, M, T, NT>(D, Mx, My);
-  load_tw(s_tw, tw, M, NT);
+  const int kx = bx * T + t;
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
     if (c == 0) cp_async_wait<2>();
     else if (c == 1) cp_async_wait<1>();
     else cp_async_wait<0>();
     __syncthreads();           // this component's tile (and the twiddles) complete
-    cpx<R>* sc = s + c * M * T;
+    cpx<R>* sc = s + c * CS;
     const int j = q;
     cpx<R> v[M1];
     if (q < M2) {
@@ -370,7 +368,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
 #pragma unroll
       for (int k1 = 1; k1 < M1; ++k1) v[k1] = twiddle<R, false>(v[k1], s_tw[j * k1]);
 #pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) sc[(k1 * M2 + j) * T + t] = v[k1];
+      for (int k1 = 0; k1 < M1; ++k1) sc[Z::at(k1, j) * T + t] = v[k1];
     }
   }
   __syncthreads();
@@ -380,52 +378,82 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
     // (row k1*M2 + k2 holds kz = k1 + M1*k2)
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
-      cpx<R>* sc = s + c * M * T;
+      cpx<R>* sc = s + c * CS;
       cpx<R> u[M2];
 #pragma unroll
-      for (int j = 0; j < M2; ++j) u[j] = sc[(k1 * M2 + j) * T + t];
+      for (int j = 0; j < M2; ++j) u[j] = sc[Z::at(k1, j) * T + t];
       cl::Dft<R, false, M2>::run(u);
 #pragma unroll
-      for (int k2 = 0; k2 < M2; ++k2) sc[(k1 * M2 + k2) * T + t] = u[k2];
+      for (int k2 = 0; k2 < M2; ++k2) sc[Z::at(k1, k2) * T + t] = u[k2];
     }
   }
   __syncthreads();
   // kz = k1 + M1 k2 lives in row k1*M2 + k2
-  zc_product<R, M, T, NT>(s, D, Mx, My, [](int kz) { return (kz % M1) * M2 + kz / M1; });
+  zc_product<R, M, T, NT, CS>(s, D, Mx, My, bx, ky, [](int kz) { return Z::at(kz % M1, kz / M1); });
   __syncthreads();
   if (q < M1 && kx < Mx) {
     const int k1 = q;
     // inverse phase A of each component: M2-point inverse over k2, conjugate twiddle
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
-      cpx<R>* sc = s + c * M * T;
+      cpx<R>* sc = s + c * CS;
       cpx<R> u[M2];
 #pragma unroll
-      for (int k2 = 0; k2 < M2; ++k2) u[k2] = sc[(k1 * M2 + k2) * T + t];
+      for (int k2 = 0; k2 < M2; ++k2) u[k2] = sc[Z::at(k1, k2) * T + t];
       cl::Dft<R, true, M2>::run(u);
 #pragma unroll
       for (int j = 1; j < M2; ++j) u[j] = twiddle<R, true>(u[j], s_tw[j * k1]);
 #pragma unroll
-      for (int j = 0; j < M2; ++j) sc[(k1 * M2 + j) * T + t] = u[j];
+      for (int j = 0; j < M2; ++j) sc[Z::at(k1, j) * T + t] = u[j];
     }
   }
   __syncthreads();
+}
+
+// Inverse phase B of component c of a tile: M1-point inverse over k1, rows
+// z = j + M2 i < nz stored to B2.
+template <typename R, int M1, int M2, int T>
+__device__ __forceinline__ void zc_inverse_b(const cpx<R>* sc, cpx<R>* __restrict__ B2c, int nz,
+                                             int Mx, long long plane, long long col, int kx) {
+  using Z = ZRows<R, M1, M2, T>;
+  constexpr int kZin = kHalf<M1, M2>;
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
   if (q < M2 && kx < Mx) {
     const int j = q;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-      const cpx<R>* sc = s + c * M * T;
-      cpx<R> v[M1];
+    cpx<R> v[M1];
 #pragma unroll
-      for (int k1 = 0; k1 < M1; ++k1) v[k1] = sc[(k1 * M2 + j) * T + t];
-      cl::Dft<R, true, M1>::run(v);
+    for (int k1 = 0; k1 < M1; ++k1) v[k1] = sc[Z::at(k1, j) * T + t];
+    cl::Dft<R, true, M1>::run(v);
 #pragma unroll
-      for (int i = 0; i < M1; ++i) {
-        const int z = j + M2 * i;
-        if (i < kZin && z < nz) B2[c * comp + z * plane + col] = v[i];
-      }
+    for (int i = 0; i < M1; ++i) {
+      const int z = j + M2 * i;
+      if (i < kZin && z < nz) B2c[z * plane + col] = v[i];
     }
   }
+}
+
+template <typename R, int M1, int M2, int T>
+__global__ void __launch_bounds__(T * kQ<M1, M2>,
+                                  kMinB(T * kQ<M1, M2>, 2, (M1 * M2 + 3LL * ZRows<R, M1, M2, T>::rows * T) * sizeof(cpx<R>)))
+    fk_zconv(cpx<R>* __restrict__ B2, const cpx<R>* __restrict__ D, int nz, int Mx, int My,
+             const cpx<R>* __restrict__ tw, const int* __restrict__ skip) {
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, CS = ZRows<R, M1, M2, T>::rows * T;
+  if (skip && skip[blockIdx.z]) return;
+  B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* s = s_tw + M;                      // [3][rows][T]
+  const int bx = blockIdx.x, ky = blockIdx.y;
+  const int kx = bx * T + threadIdx.x % T;
+  const long long plane = (long long)My * Mx;
+  const long long comp = (long long)nz * plane;
+  const long long col = (long long)ky * Mx + kx;
+  for (int c = 0; c < 3; ++c) zc_stage<R, T, NT>(s + c * CS, B2, c, nz, Mx, My, bx, ky);
+  zc_prefetch<R, M, T, NT>(D, Mx, My, bx, ky);
+  load_tw(s_tw, tw, M, NT);
+  zc_forward_product_inva<R, M1, M2, T, NT>(s, s_tw, D, nz, Mx, My, bx, ky);
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) zc_inverse_b<R, M1, M2, T>(s + c * CS, B2 + c * comp, nz, Mx, plane, col, kx);
 }
 
 // ---------------------------------------------------------------- P1: x forward
@@ -809,7 +837,7 @@ struct Passes {
   template <int TC>
   static cudaError_t zconv_t(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
                              int nrhs, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + 3 * M * TC) * sizeof(cpx<R>);
+    const size_t sm = (size_t)(M + 3 * ZRows<R, M1, M2, TC>::rows * TC) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_zconv<R, M1, M2, TC>, sm);
     if (e != cudaSuccess) return e;
     // two ~106 KB blocks per SM need the largest shared-memory carveout
