@@ -120,6 +120,8 @@ __global__ void k_green_fill(T* __restrict__ grid, const T* __restrict__ table, 
 }
 
 // octant of the transformed FP64 grid, scaled by inv
+// D: component c of the (planar, complex128) octant, the caller passing its
+// base D + c * octant size
 __global__ void k_octant(const c128* __restrict__ grid, c128* __restrict__ D, int Mx, int My, int Mz,
                          double inv) {
   const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = Mz / 2 + 1;
@@ -147,8 +149,8 @@ __global__ void k_octant_df(const cdf* __restrict__ grid, cdf* __restrict__ Ddf,
       const cdf v = src[fx];
       const cdf sv = mk<df>(v.x * inv, v.y * inv);
       const long long i = (long long)row * hx + fx;
-      Ddf[i] = sv;
-      D32[i] = mk<float>(sv.x.hi, sv.y.hi);
+      Ddf[i] = sv;                                   // planar: Ddf = base + c * octant size
+      D32[6 * i] = mk<float>(sv.x.hi, sv.y.hi);      // interleaved: D32 = base + c
     }
   }
 }
@@ -160,10 +162,14 @@ __global__ void k_df_to128(const cdf* __restrict__ a, c128* __restrict__ b, long
     b[i] = to128(a[i]);
 }
 
-__global__ void k_to32(const c128* __restrict__ a, c64* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    b[i] = mk<float>((float)a[i].x, (float)a[i].y);
+// complex64 rounding of the planar complex128 octant a ([6][oct]) into the
+// interleaved complex64 octant b ([oct][6])
+__global__ void k_to32(const c128* __restrict__ a, c64* __restrict__ b, long long oct) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 6 * oct;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / oct, o = i - c * oct;
+    b[6 * o + c] = mk<float>((float)a[i].x, (float)a[i].y);
+  }
 }
 
 static int rows_grid(int rows) { return std::min(rows, num_sms() * 64); }
@@ -225,7 +231,7 @@ cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const cpx
   tr_begin(g.tr, st);
   const int orows = rows_grid((g.My / 2 + 1) * (g.Mz / 2 + 1));
   if constexpr (std::is_same<R, df>::value) {
-    k_octant_df<<<orows, 256, 0, st>>>(grid2, h->wdf.D + c * oct, h->w32.D + c * oct, g.Mx, g.My,
+    k_octant_df<<<orows, 256, 0, st>>>(grid2, h->wdf.D + c * oct, h->w32.D + c, g.Mx, g.My,
                                        g.Mz, df(inv)); count_launch();
   } else {
     k_octant<<<orows, 256, 0, st>>>(grid2, h->w64.D + c * oct, g.Mx, g.My, g.Mz, inv); count_launch();
@@ -368,7 +374,7 @@ int dda_build_D_internal(dda_t h, bool want32) {
     if (!use_df) {
       rc = alloc((void**)&h->w32.D, 6 * oct * sizeof(c64), "cannot allocate the FP32 D-matrix octant");
       if (rc != DDA_OK) return rc;
-      k_to32<<<grid_for(6 * oct), 256, 0, st>>>(h->w64.D, h->w32.D, 6 * oct); count_launch();
+      k_to32<<<grid_for(6 * oct), 256, 0, st>>>(h->w64.D, h->w32.D, oct); count_launch();
       e = cudaGetLastError();
       if (e != cudaSuccess) return dda_cuda_fail(h, e, "D-matrix FP32 copy");
     }

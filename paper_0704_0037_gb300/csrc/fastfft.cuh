@@ -274,24 +274,55 @@ __device__ __forceinline__ void zc_stage(cpx<R>* tile, const cpx<R>* B2, int c, 
   cp_async_commit();
 }
 
+// The six octant entries (xx, xy, xz, yy, yz, zz) of point o: of the
+// interleaved complex64 octant [Mz/2+1][My/2+1][Mx/2+1][6] with three 16-byte
+// loads, of the planar octant [6][octs] of the wider types with six.
+template <typename R>
+__device__ __forceinline__ void load_oct(const cpx<R>* __restrict__ D, long long o, long long octs,
+                                         cpx<R> (&d)[6]) {
+  if constexpr (kOctInterleaved<R>) {
+    const float4* q = reinterpret_cast<const float4*>(D + 6 * o);   // 48 bytes, 16-byte aligned
+    const float4 a = q[0], b = q[1], c = q[2];
+    d[0] = mk<float>(a.x, a.y); d[1] = mk<float>(a.z, a.w); d[2] = mk<float>(b.x, b.y);
+    d[3] = mk<float>(b.z, b.w); d[4] = mk<float>(c.x, c.y); d[5] = mk<float>(c.z, c.w);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[k] = D[k * octs + o];
+  }
+}
+
 // Warm L2 with the octant entries of the Fourier-space product of a tile (fy
 // of its ky, its range of fx, every fz and component): they arrive from HBM
-// while the forward transforms run, so the product's loads hit L2.
+// while the forward transforms run, so the product's loads hit L2.  Each fz
+// row of the tile is one contiguous run of the interleaved octant (every
+// 128-byte line it touches prefetched), or six runs of the planar one (their
+// first and last lines).
 template <typename R, int M, int T, int NT>
 __device__ __forceinline__ void zc_prefetch(const cpx<R>* D, int Mx, int My, int bx, int ky) {
   const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
-  const long long octs = (long long)hx * hy * hz;
   int nys, na, nb;
   const int fy = fold_axis(ky, My, nys);
   const int kxa = bx * T, kxb = min(kxa + T, Mx) - 1;
   const int fa = fold_axis(kxa, Mx, na), fb = fold_axis(kxb, Mx, nb);
   const int fmin = min(fa, fb);
   const int fmax = (2 * kxa <= Mx && 2 * kxb >= Mx) ? Mx / 2 : max(fa, fb);
-  for (int k = threadIdx.x; k < 6 * hz; k += NT) {
-    const int c6 = k / hz, fz = k - c6 * hz;
-    const cpx<R>* row = D + c6 * octs + ((long long)fz * hy + fy) * hx;
-    prefetch_l2(row + fmin);
-    if (((size_t)(row + fmax) >> 7) != ((size_t)(row + fmin) >> 7)) prefetch_l2(row + fmax);
+  if constexpr (kOctInterleaved<R>) {
+    const int nl = (int)(((size_t)(fmax - fmin + 1) * 6 * sizeof(cpx<R>) + 127) / 128) + 1;
+    for (int k = threadIdx.x; k < hz * nl; k += NT) {
+      const int fz = k / nl, l = k - fz * nl;
+      const long long o = ((long long)fz * hy + fy) * hx;
+      const size_t a0 = (size_t)(D + 6 * (o + fmin)) >> 7;
+      const size_t a1 = ((size_t)(D + 6 * (o + fmax + 1)) - 1) >> 7;
+      if (a0 + l <= a1) prefetch_l2((const void*)((a0 + l) << 7));
+    }
+  } else {
+    const long long octs = (long long)hx * hy * hz;
+    for (int k = threadIdx.x; k < 6 * hz; k += NT) {
+      const int c6 = k / hz, fz = k - c6 * hz;
+      const cpx<R>* row = D + c6 * octs + ((long long)fz * hy + fy) * hx;
+      prefetch_l2(row + fmin);
+      if (((size_t)(row + fmax) >> 7) != ((size_t)(row + fmin) >> 7)) prefetch_l2(row + fmax);
+    }
   }
 }
 
@@ -304,7 +335,6 @@ template <typename R, int M, int T, int NT, int CS, typename RowOf>
 __device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__ D, int Mx, int My,
                                            int bx, int ky, RowOf row_of) {
   const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
-  const long long octs = (long long)hx * hy * hz;
   int nys;
   const int fy = fold_axis(ky, My, nys);
   const int kx0 = bx * T;
@@ -315,9 +345,10 @@ __device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__
     if (kx2 >= Mx) continue;
     int nxs;
     const int fx = fold_axis(kx2, Mx, nxs);
-    const long long o = ((long long)fz * hy + fy) * hx + fx;
-    const cpx<R> dxx = D[o], dyy = D[3 * octs + o], dzz = D[5 * octs + o];
-    cpx<R> dxy = D[octs + o], dxz = D[2 * octs + o], dyz = D[4 * octs + o];
+    cpx<R> d6[6];
+    load_oct<R>(D, ((long long)fz * hy + fy) * hx + fx, (long long)hx * hy * hz, d6);
+    const cpx<R> dxx = d6[0], dyy = d6[3], dzz = d6[5];
+    cpx<R> dxy = d6[1], dxz = d6[2], dyz = d6[4];
     if (nxs ^ nys) dxy = mk<R>(-dxy.x, -dxy.y);
     const int nkz = (fz == 0 || 2 * fz == M) ? 1 : 2;
     for (int h = 0; h < nkz; ++h) {

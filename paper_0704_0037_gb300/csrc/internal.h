@@ -65,13 +65,20 @@ struct LatticeDev {
   const uint8_t* mat;
 };
 
+// Layout of the D-matrix octant: interleaved by point for complex64 (its six
+// 8-byte entries are three 16-byte loads), planar by component for the wider
+// types (six 16-byte loads either way; planar reads measured faster there).
+template <typename R> constexpr bool kOctInterleaved = sizeof(R) == 4;
+
 // Per-precision workspace of the FFT product.
 template <typename R>
 struct Work {
   cpx<R>* B1 = nullptr;     // after the x pass
   cpx<R>* B2 = nullptr;     // after the y pass (z pass in place)
   cpx<R>* tw = nullptr;     // twiddles: [Mx] then [My] then [Mz], exp(-2 pi i m / M)
-  cpx<R>* D = nullptr;      // octant of FFT(G)/(Mx My Mz): [6][Mz/2+1][My/2+1][Mx/2+1]
+  cpx<R>* D = nullptr;      // octant of FFT(G)/(Mx My Mz): complex64 interleaved
+                            // [Mz/2+1][My/2+1][Mx/2+1][6] (xx, xy, xz, yy, yz, zz of a point
+                            // together), the wider types [6][Mz/2+1][My/2+1][Mx/2+1]
   cpx<R>* beta = nullptr;   // [nrhs][n_mat][3]
   bool have_D = false;
   int cap = 0;              // right-hand sides B1 and B2 hold

@@ -228,9 +228,11 @@ __global__ void __launch_bounds__(256) k_p3(cpx<R>* __restrict__ B2, const cpx<R
     int nx_, nz_;
     const int fx = fold(kx, Mx, nx_);
     const int fz = fold(kz, Mz, nz_);
-    const long long o = ((long long)fz * hy + fy) * hx + fx;
-    cpx<R> dxx = D[o], dxy = D[octs + o], dxz = D[2 * octs + o];
-    cpx<R> dyy = D[3 * octs + o], dyz = D[4 * octs + o], dzz = D[5 * octs + o];
+    const long long p = ((long long)fz * hy + fy) * hx + fx;
+    // octant entry k of point p: interleaved (complex64) or planar
+    const long long o = kOctInterleaved<R> ? 6 * p : p, ks = kOctInterleaved<R> ? 1 : octs;
+    cpx<R> dxx = D[o], dxy = D[o + ks], dxz = D[o + 2 * ks];
+    cpx<R> dyy = D[o + 3 * ks], dyz = D[o + 4 * ks], dzz = D[o + 5 * ks];
     if (nx_ ^ ny_) dxy = mk<R>(-dxy.x, -dxy.y);
     if (nx_ ^ nz_) dxz = mk<R>(-dxz.x, -dxz.y);
     if (ny_ ^ nz_) dyz = mk<R>(-dyz.x, -dyz.y);
