@@ -237,6 +237,16 @@ struct ZRows {
   static __device__ __forceinline__ int at(int k1, int j) { return k1 * (pad ? M2 + 1 : M2) + j; }
 };
 
+// Row ky of the z pass taken by block row b: 0, 1, My - 1, 2, My - 2, ...
+// (a permutation of 0 .. My - 1), so that the rows ky and My - ky, whose
+// products read the same octant entries (fy = min(ky, My - ky)), run one
+// after the other and the second finds them in L2.
+__device__ __forceinline__ int ky_order(int b, int My) {
+  if (b == 0) return 0;
+  const int j = (b + 1) / 2;
+  return (b & 1) ? j : My - j;
+}
+
 // Pieces of the fused z pass.  A tile is T adjacent columns (kx from bx T) of
 // one ky; s is [3][rows][T] (component, row, column) in shared memory.
 //
@@ -474,7 +484,9 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* s = s_tw + M;                      // [3][rows][T]
-  const int bx = blockIdx.x, ky = blockIdx.y;
+  // complex64 (interleaved octant): mirrored rows together; the double-width
+  // passes measured faster in natural order
+  const int bx = blockIdx.x, ky = kOctInterleaved<R> ? ky_order(blockIdx.y, My) : (int)blockIdx.y;
   const int kx = bx * T + threadIdx.x % T;
   const long long plane = (long long)My * Mx;
   const long long comp = (long long)nz * plane;
@@ -510,7 +522,7 @@ __device__ __forceinline__ int row_of(const long long* off, long long i) {
 constexpr int kGU = 4;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) fk_xfwd(const typename VecOf<R>::type* __restrict__ x,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 * M2 + T * kLD<M1 * M2>) * sizeof(cpx<R>))) fk_xfwd(const typename VecOf<R>::type* __restrict__ x,
                                                           cpx<R>* __restrict__ B1, LatticeDev lat,
                                                           const cpx<R>* __restrict__ beta,
                                                           long long n_occ, int nrows,
@@ -610,7 +622,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) f
 template <int M> constexpr int kXRow = (M + 1) / 2;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) fk_xinv(const cpx<R>* __restrict__ B1,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 * M2 + T * kLD<M1 * M2>) * sizeof(cpx<R>) + T * kXRow<M1 * M2> * sizeof(typename VecOf<R>::type))) fk_xinv(const cpx<R>* __restrict__ B1,
                                                           const typename VecOf<R>::type* __restrict__ x,
                                                           typename VecOf<R>::type* __restrict__ y,
                                                           LatticeDev lat,
@@ -813,6 +825,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) f
 
 // ---------------------------------------------------------------- launchers
 template <typename R> constexpr int kT = sizeof(R) == 4 ? 16 : 8;
+template <typename R, int M> constexpr int kTX = (sizeof(R) == 4 && M >= 1000) ? 8 : kT<R>;
 
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
@@ -824,6 +837,9 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename R, int M1, int M2>
 struct Passes {
   static constexpr int M = M1 * M2, T = kT<R>, NT = T * kQ<M1, M2>;
+  // rows per block of the x passes: 8 for the complex64 lines of 1000 points
+  // and more (16 rows of 1080 points would take 147 KB, one block per SM)
+  static constexpr int TX = kTX<R, M>, NTX = TX * kQ<M1, M2>;
   // columns per block of the fused z pass: the three spectra of TZ columns
   // must fit in shared memory (two blocks per SM where they can)
   static constexpr int TZ = (size_t)(M + 3 * M * T) * sizeof(cpx<R>) <= 113 * 1024 ? T
@@ -888,16 +904,16 @@ struct Passes {
   static cudaError_t xfwd(const V* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,
                           long long n_occ, int nrows, const cpx<R>* tw, bool adj, int nrhs,
                           int bstride, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>);
-    const dim3 grid((nrows + T - 1) / T, 3 * nrhs);
+    const size_t sm = (size_t)(M + TX * kLD<M>) * sizeof(cpx<R>);
+    const dim3 grid((nrows + TX - 1) / TX, 3 * nrhs);
     cudaError_t e;
     if (adj) {
-      if ((e = set_smem(fk_xfwd<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
-      fk_xfwd<R, M1, M2, T, true><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
+      if ((e = set_smem(fk_xfwd<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
+      fk_xfwd<R, M1, M2, TX, true><<<grid, NTX, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
                                                         bstride, skip);
     } else {
-      if ((e = set_smem(fk_xfwd<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
-      fk_xfwd<R, M1, M2, T, false><<<grid, NT, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
+      if ((e = set_smem(fk_xfwd<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
+      fk_xfwd<R, M1, M2, TX, false><<<grid, NTX, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
                                                          bstride, skip);
     }
     count_launch();
@@ -932,19 +948,19 @@ struct Passes {
   static cudaError_t xinv(const cpx<R>* B1, const V* x, V* y, const LatticeDev& lat,
                           const cpx<R>* beta, long long n_occ, int nrows, const cpx<R>* tw, bool adj,
                           double* dotp, int nrhs, int bstride, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + T * kLD<M>) * sizeof(cpx<R>) + (size_t)T * kXRow<M> * sizeof(V);
-    const dim3 grid((nrows + T - 1) / T, 3 * nrhs);
+    const size_t sm = (size_t)(M + TX * kLD<M>) * sizeof(cpx<R>) + (size_t)TX * kXRow<M> * sizeof(V);
+    const dim3 grid((nrows + TX - 1) / TX, 3 * nrhs);
     cudaError_t e;
     // three blocks of up to ~56 KB per SM need a large shared-memory carveout
-    if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, T, true>)) != cudaSuccess) return e;
-    if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, T, false>)) != cudaSuccess) return e;
+    if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, TX, true>)) != cudaSuccess) return e;
+    if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, TX, false>)) != cudaSuccess) return e;
     if (adj) {
-      if ((e = set_smem(fk_xinv<R, M1, M2, T, true>, sm)) != cudaSuccess) return e;
-      fk_xinv<R, M1, M2, T, true><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
+      if ((e = set_smem(fk_xinv<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
+      fk_xinv<R, M1, M2, TX, true><<<grid, NTX, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
                                                         dotp, bstride, skip);
     } else {
-      if ((e = set_smem(fk_xinv<R, M1, M2, T, false>, sm)) != cudaSuccess) return e;
-      fk_xinv<R, M1, M2, T, false><<<grid, NT, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
+      if ((e = set_smem(fk_xinv<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
+      fk_xinv<R, M1, M2, TX, false><<<grid, NTX, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
                                                          dotp, bstride, skip);
     }
     count_launch();
@@ -952,7 +968,7 @@ struct Passes {
   }
   // number of blocks (partials written to dotp) of xinv for nrows rows, per
   // right-hand side (the partials of right-hand side r follow those of r - 1)
-  static int xinv_blocks(int nrows) { return 3 * ((nrows + T - 1) / T); }
+  static int xinv_blocks(int nrows) { return 3 * ((nrows + TX - 1) / TX); }
 };
 
 }  // namespace fast

@@ -286,7 +286,12 @@ struct FastArgs {
   int var_yf = 0, var_z = 0, var_yi = 0;
 };
 // number of (re, im) partials FP_XINV writes to dotp for nrows rows
-inline int fast_xinv_blocks(int nrows, bool fp32) { return 3 * ((nrows + (fp32 ? 16 : 8) - 1) / (fp32 ? 16 : 8)); }
+// (rows per block: 16 for complex64 lines shorter than 1000 points, else 8;
+// fp32 false gives the count of the double-width passes, the largest)
+inline int fast_xinv_blocks(int nrows, bool fp32, int Mx = 0) {
+  const int t = (fp32 && Mx < 1000) ? 16 : 8;
+  return 3 * ((nrows + t - 1) / t);
+}
 bool fast_supported(int M);          // complex64, complex128 and double-float passes
 bool fast_supported_c64(int M);      // complex64 passes (also 512 and 1080)
 cudaError_t fast_pass_512_c64(int pass, const FastArgs& a);

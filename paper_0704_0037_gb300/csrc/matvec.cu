@@ -333,7 +333,7 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
   const bool fx = g.engine == 0 && has_fast(g.Mx);
   const bool fy = g.engine == 0 && has_fast(g.My);
   const bool fz = g.engine == 0 && has_fast(g.Mz);
-  const int dnb = fast_xinv_blocks(g.nrows, sizeof(R) == 4);
+  const int dnb = fast_xinv_blocks(g.nrows, sizeof(R) == 4, g.Mx);
   if (dotp && dot_nb && fx) *dot_nb = dnb;
   // right-hand sides in chunks of the work buffers' capacity, each chunk in
   // one launch per pass
