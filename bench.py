@@ -254,7 +254,7 @@ def load_peaks():
 # with the capture it comes from.  Only valid for the 134^3 sphere on the
 # 270^3 grid; None elsewhere, and removed whenever the kernel changes.
 NCU_TRAFFIC_134 = {
-    "p3_zconv_c64": (450004736 + 195129856,
+    "p3_zconv_c64": (355293184 + 183375872,
                      "ncu --set full --clock-control none -k regex:fk_zconv -s 1 -c 1 of "
                      "python bench.py --workload products --n 134 --prec fp32 --products 3 "
                      "(fk_zconv<float, 15, 18, 16>, stored capture, not measured by this run)"),
@@ -832,8 +832,10 @@ def run_products(args):
     trace = {k: round(v[0] / max(1, v[1]), 4) for k, v in dda.dda_trace_read(p.h).items()
              if k != "all_launches"}
     dda.dda_trace(p.h, False)
+    tiles = list(dda.dda_get_pass_tiles(p.h, prec))
     p.close()
     return {"workload": "products", "n_box": args.n, "box": args.box or None, "grid": list(p.grid),
+            "pass_tiles": tiles,
             "prec": args.prec,
             "engine": args.engine,
             "products": args.products, "ms_per_product": ms, "ms_per_pass": trace}
