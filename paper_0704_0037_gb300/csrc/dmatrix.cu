@@ -172,6 +172,27 @@ __global__ void k_to32(const c128* __restrict__ a, c64* __restrict__ b, long lon
   }
 }
 
+// The remaining components of the octant of a cubic lattice (nx = ny = nz,
+// padded to Mx = My = Mz, octant side h) from xx and xy.  G_mn(r) =
+// A(|r|) d_mn - B(|r|) r_m r_n is then carried into itself by permuting the
+// axes, and the 3D DFT commutes with the permutation:
+//   D_yy(kx,ky,kz) = D_xx(ky,kx,kz),  D_zz(kx,ky,kz) = D_xx(kz,ky,kx),
+//   D_xz(kx,ky,kz) = D_xy(kx,kz,ky),  D_yz(kx,ky,kz) = D_xy(kz,ky,kx)
+// (the parity of each component in each axis permutes the same way).  The
+// octant is planar ([6][oct]) or interleaved by point ([oct][6]).
+template <typename T, bool INTERLEAVED>
+__global__ void k_oct_permute(T* __restrict__ D, int h, long long oct) {
+  auto at = [&](int c, long long q) -> T& { return INTERLEAVED ? D[6 * q + c] : D[c * oct + q]; };
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < oct;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int kx = (int)(p % h), ky = (int)((p / h) % h), kz = (int)(p / ((long long)h * h));
+    at(3, p) = at(0, ((long long)kz * h + kx) * h + ky);
+    at(5, p) = at(0, ((long long)kx * h + ky) * h + kz);
+    at(2, p) = at(1, ((long long)ky * h + kz) * h + kx);
+    at(4, p) = at(1, ((long long)kx * h + ky) * h + kz);
+  }
+}
+
 static int rows_grid(int rows) { return std::min(rows, num_sms() * 64); }
 
 static int grid_for(long long n) {
@@ -198,7 +219,6 @@ cudaError_t build_component_fast(dda_t h, cpx<R>* grid, cpx<R>* grid2, const cpx
                                  const int comp[2], int c, double inv) {
   const Geom& g = h->g;
   cudaStream_t st = h->stream;
-  const long long full = (long long)g.Mx * g.My * g.Mz;
   const long long oct = g.oct();
   const cpx<R>* twx = dwork<R>(h).tw;
   const cpx<R>* twy = twx + g.Mx;
@@ -245,7 +265,6 @@ cudaError_t build_component_generic(dda_t h, c128* grid, const c128* table, cons
                                     int c, double inv) {
   const Geom& g = h->g;
   cudaStream_t st = h->stream;
-  const long long full = (long long)g.Mx * g.My * g.Mz;
   const long long oct = g.oct();
   const c128* twx = h->w64.tw;
   const c128* twy = twx + g.Mx;
@@ -357,11 +376,26 @@ int dda_build_D_internal(dda_t h, bool want32) {
   tr_end(g.tr, st, TR_DB_GREEN);
   const int comps[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
   const double inv = 1.0 / (double)full;
+  // a cubic lattice on a cubic grid: xx and xy transformed, the other four
+  // components permuted from them
+  const bool cubic = g.nx == g.ny && g.ny == g.nz && g.Mx == g.My && g.My == g.Mz;
   cudaError_t e = cudaSuccess;
-  for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
+  for (int c = 0; c < (cubic ? 2 : 6) && e == cudaSuccess; ++c) {
     if (use_df) e = build_component_fast<df>(h, (cdf*)grid, (cdf*)grid2, (const cdf*)table, comps[c], c, inv);
     else if (fast) e = build_component_fast<double>(h, (c128*)grid, (c128*)grid2, (const c128*)table, comps[c], c, inv);
     else e = build_component_generic(h, (c128*)grid, (const c128*)table, comps[c], c, inv);
+  }
+  if (cubic && e == cudaSuccess) {
+    tr_begin(g.tr, st);
+    const int hh = g.Mx / 2 + 1;
+    if (use_df) {
+      k_oct_permute<cdf, false><<<grid_for(oct), 256, 0, st>>>(h->wdf.D, hh, oct); count_launch();
+      k_oct_permute<c64, true><<<grid_for(oct), 256, 0, st>>>(h->w32.D, hh, oct); count_launch();
+    } else {
+      k_oct_permute<c128, false><<<grid_for(oct), 256, 0, st>>>(h->w64.D, hh, oct); count_launch();
+    }
+    e = cudaGetLastError();
+    tr_end(g.tr, st, TR_DB_OCTANT);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   tr_flush(g.tr);
