@@ -131,8 +131,9 @@ int dda_set_fft_engine(dda_t h, int engine);
  *        where the z pass's spectra would not fit in shared memory);
  *   1  : half as many lines per block (twice the blocks);
  *   -1 : chosen by dda_build_Dmatrix, which times both variants of each pass
- *        on the handle's own buffers (CUDA events, three launches) and keeps
- *        the faster (cached per device and grid shape).  The default.
+ *        on the handle's own buffers (CUDA events, three launches) and takes
+ *        the half tiles when they are at least 3 % faster (cached per device
+ *        and grid shape).  The default.
  * Every variant computes each line with the same arithmetic: the products
  * agree bit for bit.  dda_set_pass_tiles with tiles == NULL sets -1 for all
  * three; an entry set to 0 or 1 is kept by later builds.  dda_get_pass_tiles
