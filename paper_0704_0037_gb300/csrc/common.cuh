@@ -6,6 +6,17 @@
 
 namespace dda {
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization (launch_pdl) may start before the kernel
+// ahead of it on its stream has finished; it calls pdl_wait() before touching
+// anything that kernel wrote (the wait returns once it has completed and its
+// writes are visible).  pdl_launch() lets the next such kernel be scheduled
+// as soon as every block of this one has called it.  Both are no-ops in an
+// ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+
 template <typename R> struct cpx;
 template <> struct __align__(8) cpx<float> { float x, y; };
 template <> struct __align__(16) cpx<double> { double x, y; };

@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
                                                           int msign, const int* __restrict__ skip,
                                                           long long ostr) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  pdl_wait();
+  pdl_launch();
   if (skip && skip[blockIdx.z / 3]) return;     // right-hand side already converged
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -143,6 +145,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yinv(const cpx<R>* __restri
                                                           int Mx, const cpx<R>* __restrict__ tw,
                                                           const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
+  pdl_wait();
+  pdl_launch();
   if (skip && skip[blockIdx.z / 3]) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -479,6 +483,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>,
     fk_zconv(cpx<R>* __restrict__ B2, const cpx<R>* __restrict__ D, int nz, int Mx, int My,
              const cpx<R>* __restrict__ tw, const int* __restrict__ skip) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, CS = ZRows<R, M1, M2, T>::rows * T;
+  pdl_wait();
+  pdl_launch();
   if (skip && skip[blockIdx.z]) return;
   B2 += (long long)blockIdx.z * 3 * nz * My * Mx;      // right-hand side blockIdx.z
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -535,6 +541,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 *
   cpx<R>* a = s_tw + M;                      // [T][LD]
   // blockIdx.y = 3 * (right-hand side) + component; vectors [rhs][3][n_occ]
   const int cc = blockIdx.y, c = cc % 3;
+  pdl_wait();
+  pdl_launch();
   if (skip && skip[cc / 3]) return;
   beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
@@ -639,6 +647,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 *
   cpx<R>* a = s_tw + M;                      // [T][LD]
   V* s_x = reinterpret_cast<V*>(a + T * LD); // [kXS]
   const int cc = blockIdx.y, c = cc % 3;     // 3 * (right-hand side) + component
+  pdl_wait();
+  pdl_launch();
   if (skip && skip[cc / 3]) return;
   beta += (long long)(cc / 3) * bstride;
   const int r0 = blockIdx.x * T;
@@ -855,10 +865,10 @@ struct Passes {
     const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, TY, true>, sm);
     if (e != cudaSuccess) return e;
-    fk_yfwd<R, M1, M2, TY, true><<<dim3((Mx + TY - 1) / TY, nz, 3 * nrhs), TY * kQ<M1, M2>, sm, st>>>(
-        in, out, ny, nz, Mx, tw, 0, skip, 0);
+    e = launch_pdl(sizeof(R) == 4, fk_yfwd<R, M1, M2, TY, true>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
+                   dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, 0, skip, 0LL);
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
                           const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var) {
@@ -871,10 +881,10 @@ struct Passes {
     const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yinv<R, M1, M2, TY>, sm);
     if (e != cudaSuccess) return e;
-    fk_yinv<R, M1, M2, TY><<<dim3((Mx + TY - 1) / TY, nz, 3 * nrhs), TY * kQ<M1, M2>, sm, st>>>(
-        in, out, ny, nz, Mx, tw, skip);
+    e = launch_pdl(sizeof(R) == 4, fk_yinv<R, M1, M2, TY>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
+                   dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, skip);
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   static cudaError_t yinv(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
                           const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var) {
@@ -890,10 +900,10 @@ struct Passes {
     // two ~106 KB blocks per SM need the largest shared-memory carveout
     e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TC>);
     if (e != cudaSuccess) return e;
-    fk_zconv<R, M1, M2, TC><<<dim3((Mx + TC - 1) / TC, My, nrhs), TC * kQ<M1, M2>, sm, st>>>(
-        B2, D, nz, Mx, My, tw, skip);
+    e = launch_pdl(sizeof(R) == 4, fk_zconv<R, M1, M2, TC>, dim3((Mx + TC - 1) / TC, My, nrhs), dim3(TC * kQ<M1, M2>),
+                   sm, st, B2, D, nz, Mx, My, tw, skip);
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   static cudaError_t zconv(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
                            int nrhs, const int* skip, cudaStream_t st, int var) {
@@ -909,15 +919,15 @@ struct Passes {
     cudaError_t e;
     if (adj) {
       if ((e = set_smem(fk_xfwd<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
-      fk_xfwd<R, M1, M2, TX, true><<<grid, NTX, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
-                                                        bstride, skip);
+      e = launch_pdl(sizeof(R) == 4, fk_xfwd<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
+                     nrows, tw, bstride, skip);
     } else {
       if ((e = set_smem(fk_xfwd<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
-      fk_xfwd<R, M1, M2, TX, false><<<grid, NTX, sm, st>>>(x, B1, lat, beta, n_occ, nrows, tw,
-                                                         bstride, skip);
+      e = launch_pdl(sizeof(R) == 4, fk_xfwd<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
+                     nrows, tw, bstride, skip);
     }
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   // whole contiguous lines (rows of length M): rows y < rows_y of each plane
   // of plane_rows rows, nrows rows in all
@@ -956,15 +966,15 @@ struct Passes {
     if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, TX, false>)) != cudaSuccess) return e;
     if (adj) {
       if ((e = set_smem(fk_xinv<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
-      fk_xinv<R, M1, M2, TX, true><<<grid, NTX, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
-                                                        dotp, bstride, skip);
+      e = launch_pdl(sizeof(R) == 4, fk_xinv<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta, n_occ,
+                     nrows, tw, dotp, bstride, skip);
     } else {
       if ((e = set_smem(fk_xinv<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
-      fk_xinv<R, M1, M2, TX, false><<<grid, NTX, sm, st>>>(B1, x, y, lat, beta, n_occ, nrows, tw,
-                                                         dotp, bstride, skip);
+      e = launch_pdl(sizeof(R) == 4, fk_xinv<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta,
+                     n_occ, nrows, tw, dotp, bstride, skip);
     }
     count_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
   // number of blocks (partials written to dotp) of xinv for nrows rows, per
   // right-hand side (the partials of right-hand side r follow those of r - 1)

@@ -348,6 +348,28 @@ int num_sms();
     return dda_cuda_fail(h, dda_dev_guard_.err, "cudaSetDevice(handle's device)")
 
 namespace dda {
+// Launch with programmatic stream serialization when pdl is set: the kernel
+// may be scheduled while the previous kernel on st finishes, so it must call
+// pdl_wait() (common.cuh) before reading what earlier work on st wrote.  The
+// complex64 passes and solver sweeps use it (a 16^3 sphere's FP32-refined
+// solve: 1.68 -> 1.26 ms); the complex128 ones measured slower with it (2.36
+// -> 3.37 ms) and launch plainly.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Kernel attributes set once per (kernel, device) instead of before every
 // launch: the dynamic shared-memory limit (raised when a larger size is
 // needed) and the maximum shared-memory carveout.

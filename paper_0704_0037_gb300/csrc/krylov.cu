@@ -397,6 +397,8 @@ __device__ __forceinline__ void qmr_stop(Scal* s, int status, int* mask, int rr)
 // right-hand side r's partials at part + r * rs); beta_i
 __global__ void k_qmr_a(Scal* s, const double* part, long long ks, long long is, long long rs,
                         int nb, int* mask) {
+  pdl_wait();
+  pdl_launch();
   const int rr = blockIdx.x;
   s += rr; part += rr * rs;
   if (s->done) return;
@@ -469,6 +471,8 @@ __device__ void qmr_c_fin(Scal* s, const double* part, int nb, int* mask, int rr
 template <typename R>
 __global__ void __launch_bounds__(kVT) k_qmr_k1(const cpx<R>* __restrict__ pt, cpx<R>* __restrict__ v,
                                                 long long n, Scal* s, double* part, int* mask) {
+  pdl_wait();
+  pdl_launch();
   pt += blockIdx.y * n; v += blockIdx.y * n; part += blockIdx.y * kPS; s += blockIdx.y;
   if (s->done) return;
   const cpx<R> be = cs<R>(s->q.beta);
@@ -513,6 +517,8 @@ __global__ void __launch_bounds__(kVT) k_qmr_k2(cpx<R>* __restrict__ v, cpx<R>* 
                                                 cpx<R>* __restrict__ sv, cpx<R>* __restrict__ x,
                                                 cpx<R>* __restrict__ r, long long n, Scal* s,
                                                 double* part, int* mask) {
+  pdl_wait();
+  pdl_launch();
   const long long o = blockIdx.y * n;
   v += o; p += o; pt += o; d += o; sv += o; x += o; r += o;
   part += blockIdx.y * kPS; s += blockIdx.y;
@@ -1503,13 +1509,13 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
           }
           if (e != cudaSuccess) { ok = false; break; }
           if (dnb > 0) {
-            k_qmr_a<<<nr, kVT, 0, st>>>(s, m->mvpart, 1, 2, 2LL * dnb, dnb, m->mask); count_launch();
+            launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)m->mvpart, 1LL, 2LL, 2LL * dnb, dnb, m->mask); count_launch();
           } else {
             k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
-            k_qmr_a<<<nr, kVT, 0, st>>>(s, part, kNB, 1, kPS, nb, m->mask); count_launch();
+            launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)part, (long long)kNB, 1LL, (long long)kPS, nb, m->mask); count_launch();
           }
-          k_qmr_k1<R><<<vg, kVT, 0, st>>>(pt, v, n, s, part, m->mask); count_launch();
-          k_qmr_k2<R><<<vg, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part, m->mask); count_launch();
+          launch_pdl(std::is_same<R, float>::value, k_qmr_k1<R>, vg, dim3(kVT), 0, st, (const cpx<R>*)pt, v, n, s, part, m->mask); count_launch();
+          launch_pdl(std::is_same<R, float>::value, k_qmr_k2<R>, vg, dim3(kVT), 0, st, v, p, (const cpx<R>*)pt, d, sv, x, r, n, s, part, m->mask); count_launch();
         }
         const cudaError_t ec = cudaStreamEndCapture(st, &graph);
         ok = ok && ec == cudaSuccess && graph &&
@@ -1554,17 +1560,17 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
       Tracer* tr = h->g.tr;
       tr_begin(tr, st);
       if (dnb > 0) {
-        k_qmr_a<<<nr, kVT, 0, st>>>(s, m->mvpart, 1, 2, 2LL * dnb, dnb, m->mask); count_launch();
+        launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)m->mvpart, 1LL, 2LL, 2LL * dnb, dnb, m->mask); count_launch();
       } else {
         k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
-        k_qmr_a<<<nr, kVT, 0, st>>>(s, part, kNB, 1, kPS, nb, m->mask); count_launch();
+        launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)part, (long long)kNB, 1LL, (long long)kPS, nb, m->mask); count_launch();
       }
       tr_end(tr, st, TR_QMR_SCALARS);
       tr_begin(tr, st);
-      k_qmr_k1<R><<<vg, kVT, 0, st>>>(pt, v, n, s, part, m->mask); count_launch();
+      launch_pdl(std::is_same<R, float>::value, k_qmr_k1<R>, vg, dim3(kVT), 0, st, (const cpx<R>*)pt, v, n, s, part, m->mask); count_launch();
       tr_end(tr, st, TR_QMR_K1);
       tr_begin(tr, st);
-      k_qmr_k2<R><<<vg, kVT, 0, st>>>(v, p, pt, d, sv, x, r, n, s, part, m->mask); count_launch();
+      launch_pdl(std::is_same<R, float>::value, k_qmr_k2<R>, vg, dim3(kVT), 0, st, v, p, (const cpx<R>*)pt, d, sv, x, r, n, s, part, m->mask); count_launch();
       tr_end(tr, st, TR_QMR_K2);
       LK(h);
     }
