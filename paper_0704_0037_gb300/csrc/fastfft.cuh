@@ -865,7 +865,7 @@ struct Passes {
     const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, TY, true>, sm);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(sizeof(R) == 4, fk_yfwd<R, M1, M2, TY, true>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
+    e = launch_pdl(!std::is_same<R, double>::value, fk_yfwd<R, M1, M2, TY, true>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
                    dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, 0, skip, 0LL);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -881,7 +881,7 @@ struct Passes {
     const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yinv<R, M1, M2, TY>, sm);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(sizeof(R) == 4, fk_yinv<R, M1, M2, TY>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
+    e = launch_pdl(!std::is_same<R, double>::value, fk_yinv<R, M1, M2, TY>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
                    dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, skip);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -900,7 +900,7 @@ struct Passes {
     // two ~106 KB blocks per SM need the largest shared-memory carveout
     e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TC>);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(sizeof(R) == 4, fk_zconv<R, M1, M2, TC>, dim3((Mx + TC - 1) / TC, My, nrhs), dim3(TC * kQ<M1, M2>),
+    e = launch_pdl(!std::is_same<R, double>::value, fk_zconv<R, M1, M2, TC>, dim3((Mx + TC - 1) / TC, My, nrhs), dim3(TC * kQ<M1, M2>),
                    sm, st, B2, D, nz, Mx, My, tw, skip);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -919,11 +919,11 @@ struct Passes {
     cudaError_t e;
     if (adj) {
       if ((e = set_smem(fk_xfwd<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(sizeof(R) == 4, fk_xfwd<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
+      e = launch_pdl(!std::is_same<R, double>::value, fk_xfwd<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
                      nrows, tw, bstride, skip);
     } else {
       if ((e = set_smem(fk_xfwd<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(sizeof(R) == 4, fk_xfwd<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
+      e = launch_pdl(!std::is_same<R, double>::value, fk_xfwd<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
                      nrows, tw, bstride, skip);
     }
     count_launch();
@@ -966,11 +966,11 @@ struct Passes {
     if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, TX, false>)) != cudaSuccess) return e;
     if (adj) {
       if ((e = set_smem(fk_xinv<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(sizeof(R) == 4, fk_xinv<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta, n_occ,
+      e = launch_pdl(!std::is_same<R, double>::value, fk_xinv<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta, n_occ,
                      nrows, tw, dotp, bstride, skip);
     } else {
       if ((e = set_smem(fk_xinv<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(sizeof(R) == 4, fk_xinv<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta,
+      e = launch_pdl(!std::is_same<R, double>::value, fk_xinv<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta,
                      n_occ, nrows, tw, dotp, bstride, skip);
     }
     count_launch();

@@ -351,9 +351,10 @@ namespace dda {
 // Launch with programmatic stream serialization when pdl is set: the kernel
 // may be scheduled while the previous kernel on st finishes, so it must call
 // pdl_wait() (common.cuh) before reading what earlier work on st wrote.  The
-// complex64 passes and solver sweeps use it (a 16^3 sphere's FP32-refined
-// solve: 1.68 -> 1.26 ms); the complex128 ones measured slower with it (2.36
-// -> 3.37 ms) and launch plainly.
+// complex64 and double-float product passes and the QMR sweeps use it (a
+// 16^3 sphere's FP32-refined solve 1.68 -> 1.24 ms, its FP64 solve 2.36 ->
+// 2.20 ms); the complex128 product passes measured slower with it (the FP64
+// solve 2.36 -> 3.37 ms) and launch plainly.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t st, Args... args) {

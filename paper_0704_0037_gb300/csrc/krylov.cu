@@ -1509,13 +1509,13 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
           }
           if (e != cudaSuccess) { ok = false; break; }
           if (dnb > 0) {
-            launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)m->mvpart, 1LL, 2LL, 2LL * dnb, dnb, m->mask); count_launch();
+            launch_pdl(true, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)m->mvpart, 1LL, 2LL, 2LL * dnb, dnb, m->mask); count_launch();
           } else {
             k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
-            launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)part, (long long)kNB, 1LL, (long long)kPS, nb, m->mask); count_launch();
+            launch_pdl(true, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)part, (long long)kNB, 1LL, (long long)kPS, nb, m->mask); count_launch();
           }
-          launch_pdl(std::is_same<R, float>::value, k_qmr_k1<R>, vg, dim3(kVT), 0, st, (const cpx<R>*)pt, v, n, s, part, m->mask); count_launch();
-          launch_pdl(std::is_same<R, float>::value, k_qmr_k2<R>, vg, dim3(kVT), 0, st, v, p, (const cpx<R>*)pt, d, sv, x, r, n, s, part, m->mask); count_launch();
+          launch_pdl(true, k_qmr_k1<R>, vg, dim3(kVT), 0, st, (const cpx<R>*)pt, v, n, s, part, m->mask); count_launch();
+          launch_pdl(true, k_qmr_k2<R>, vg, dim3(kVT), 0, st, v, p, (const cpx<R>*)pt, d, sv, x, r, n, s, part, m->mask); count_launch();
         }
         const cudaError_t ec = cudaStreamEndCapture(st, &graph);
         ok = ok && ec == cudaSuccess && graph &&
@@ -1560,17 +1560,17 @@ int run_qmr_batched(BRun& b, const cpx<R>* rhs, cpx<R>* x, cpx<R>** vec, double 
       Tracer* tr = h->g.tr;
       tr_begin(tr, st);
       if (dnb > 0) {
-        launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)m->mvpart, 1LL, 2LL, 2LL * dnb, dnb, m->mask); count_launch();
+        launch_pdl(true, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)m->mvpart, 1LL, 2LL, 2LL * dnb, dnb, m->mask); count_launch();
       } else {
         k_dot<R, false><<<vg, kVT, 0, st>>>(p, pt, n, part, 0, s); count_launch();
-        launch_pdl(std::is_same<R, float>::value, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)part, (long long)kNB, 1LL, (long long)kPS, nb, m->mask); count_launch();
+        launch_pdl(true, k_qmr_a, dim3(nr), dim3(kVT), 0, st, s, (const double*)part, (long long)kNB, 1LL, (long long)kPS, nb, m->mask); count_launch();
       }
       tr_end(tr, st, TR_QMR_SCALARS);
       tr_begin(tr, st);
-      launch_pdl(std::is_same<R, float>::value, k_qmr_k1<R>, vg, dim3(kVT), 0, st, (const cpx<R>*)pt, v, n, s, part, m->mask); count_launch();
+      launch_pdl(true, k_qmr_k1<R>, vg, dim3(kVT), 0, st, (const cpx<R>*)pt, v, n, s, part, m->mask); count_launch();
       tr_end(tr, st, TR_QMR_K1);
       tr_begin(tr, st);
-      launch_pdl(std::is_same<R, float>::value, k_qmr_k2<R>, vg, dim3(kVT), 0, st, v, p, (const cpx<R>*)pt, d, sv, x, r, n, s, part, m->mask); count_launch();
+      launch_pdl(true, k_qmr_k2<R>, vg, dim3(kVT), 0, st, v, p, (const cpx<R>*)pt, d, sv, x, r, n, s, part, m->mask); count_launch();
       tr_end(tr, st, TR_QMR_K2);
       LK(h);
     }
