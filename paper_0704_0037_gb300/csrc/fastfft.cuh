@@ -379,6 +379,62 @@ __device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__
   }
 }
 
+// The double-float z pass runs its forward phase 2 and its inverse phase A
+// through one M2-point codelet (zc_m2_one_codelet): its unrolled double-float
+// transforms are long enough that separate forward and inverse copies miss
+// the instruction cache (sharing the M1-point codelet too would give up the
+// compile-time pruning of the first and last phases, and measured slower)
+template <typename R> constexpr bool kZOneM2 = std::is_same<R, df>::value;
+// a.y times sg (+1 or -1): conjugation by a runtime sign
+__device__ __forceinline__ cpx<df> imag_sign(cpx<df> a, float sg) {
+  cpx<df> r;
+  r.x = a.x;
+  r.y = df(a.y.hi * sg, a.y.lo * sg);
+  return r;
+}
+
+// Forward phase 2 of every component, the product and inverse phase A of
+// every component with one M2-point codelet: the inverse transform is the
+// conjugate of the forward transform of the conjugate (pass 0 forward, then
+// the product, pass 1 inverse).  Starts after a barrier, ends with one.
+template <typename R, int M1, int M2, int T, int NT>
+__device__ __forceinline__ void zc_m2_one_codelet(cpx<R>* s, const cpx<R>* s_tw,
+                                                  const cpx<R>* __restrict__ D, int Mx, int My,
+                                                  int bx, int ky) {
+  using Z = ZRows<R, M1, M2, T>;
+  constexpr int M = M1 * M2, CS = Z::rows * T;
+  const int t = threadIdx.x % T, q = threadIdx.x / T;
+  const int kx = bx * T + t;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      zc_product<R, M, T, NT, CS>(s, D, Mx, My, bx, ky, [](int kz) { return Z::at(kz % M1, kz / M1); });
+      __syncthreads();
+    }
+    if (q < M1 && kx < Mx) {
+      const int k1 = q;
+      const float sg = pass ? -1.0f : 1.0f;
+#pragma unroll 1
+      for (int c = 0; c < 3; ++c) {
+        cpx<R>* sc = s + c * CS;
+        cpx<R> u[M2];
+#pragma unroll
+        for (int j = 0; j < M2; ++j) u[j] = imag_sign(sc[Z::at(k1, j) * T + t], sg);
+        cl::Dft<R, false, M2>::run(u);
+#pragma unroll
+        for (int j = 0; j < M2; ++j) u[j] = imag_sign(u[j], sg);
+        if (pass) {
+#pragma unroll
+          for (int j = 1; j < M2; ++j) u[j] = twiddle<R, true>(u[j], s_tw[j * k1]);
+        }
+#pragma unroll
+        for (int j = 0; j < M2; ++j) sc[Z::at(k1, j) * T + t] = u[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Forward z transforms of the three staged components of a tile (phase 1
 // waits for each component's copies), the product, and the inverse z
 // transforms up to the inverse phase A of every component; the caller runs
@@ -417,6 +473,10 @@ __device__ __forceinline__ void zc_forward_product_inva(cpx<R>* s, const cpx<R>*
     }
   }
   __syncthreads();
+  if constexpr (kZOneM2<R>) {
+    zc_m2_one_codelet<R, M1, M2, T, NT>(s, s_tw, D, Mx, My, bx, ky);
+    return;
+  }
   if (q < M1 && kx < Mx) {
     const int k1 = q;
     // forward phase 2 of each component, written back to this thread's rows
@@ -627,10 +687,16 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 *
 // transform, so their latency overlaps; the slice holds up to kXS elements
 // (a row has at most (M + 1) / 2 dipoles when M >= 2 n_x - 1; any excess is
 // read directly).
-template <int M> constexpr int kXRow = (M + 1) / 2;
+// staged elements of x per tile row: a row holds at most (M + 1) / 2
+// dipoles; the long lines stage up to 384 (about the mean of the 536^3
+// sphere's 4-row tiles) and read the rest directly
+template <int M> constexpr int kXRow = (M + 1) / 2 < 384 ? (M + 1) / 2 : 384;
+// blocks per SM the x inverse pass's launch bound asks for: four blocks of
+// 4.5 warps for the long complex64 lines, else three
+template <typename R, int M> constexpr int kXinvB = (sizeof(R) == 4 && M >= 1000) ? 4 : 3;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
-__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 * M2 + T * kLD<M1 * M2>) * sizeof(cpx<R>) + T * kXRow<M1 * M2> * sizeof(typename VecOf<R>::type))) fk_xinv(const cpx<R>* __restrict__ B1,
+__global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, kXinvB<R, M1 * M2>, (M1 * M2 + T * kLD<M1 * M2>) * sizeof(cpx<R>) + T * kXRow<M1 * M2> * sizeof(typename VecOf<R>::type))) fk_xinv(const cpx<R>* __restrict__ B1,
                                                           const typename VecOf<R>::type* __restrict__ x,
                                                           typename VecOf<R>::type* __restrict__ y,
                                                           LatticeDev lat,
@@ -835,7 +901,10 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) f
 
 // ---------------------------------------------------------------- launchers
 template <typename R> constexpr int kT = sizeof(R) == 4 ? 16 : 8;
-template <typename R, int M> constexpr int kTX = (sizeof(R) == 4 && M >= 1000) ? 8 : kT<R>;
+// rows per block of the x inverse pass (fast_x_rows gives the same on the
+// host) and of the x forward pass
+template <typename R, int M> constexpr int kTX = (sizeof(R) == 4 && M >= 1000) ? 4 : kT<R>;
+template <typename R, int M> constexpr int kTXF = kTX<R, M>;
 
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
@@ -847,9 +916,11 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename R, int M1, int M2>
 struct Passes {
   static constexpr int M = M1 * M2, T = kT<R>, NT = T * kQ<M1, M2>;
-  // rows per block of the x passes: 8 for the complex64 lines of 1000 points
-  // and more (16 rows of 1080 points would take 147 KB, one block per SM)
+  // rows per block of the x passes: for the complex64 lines of 1000 points
+  // and more 4 in the forward pass (four blocks of 4.5 warps per SM) and 8 in
+  // the inverse one (16 rows of 1080 points would take 147 KB, one block per SM)
   static constexpr int TX = kTX<R, M>, NTX = TX * kQ<M1, M2>;
+  static constexpr int TXF = kTXF<R, M>, NTXF = TXF * kQ<M1, M2>;
   // columns per block of the fused z pass: the three spectra of TZ columns
   // must fit in shared memory (two blocks per SM where they can)
   static constexpr int TZ = (size_t)(M + 3 * M * T) * sizeof(cpx<R>) <= 113 * 1024 ? T
@@ -861,69 +932,71 @@ struct Passes {
   // autotuner picks one by timing.
   template <int TY>
   static cudaError_t yfwd_t(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
+                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, bool pdl) {
     const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, TY, true>, sm);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(!std::is_same<R, double>::value, fk_yfwd<R, M1, M2, TY, true>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
+    e = launch_pdl(pdl, fk_yfwd<R, M1, M2, TY, true>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
                    dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, 0, skip, 0LL);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
   }
   static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var) {
-    return var == 1 ? yfwd_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st)
-                    : yfwd_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st);
+                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var,
+                          bool pdl) {
+    return var == 1 ? yfwd_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl)
+                    : yfwd_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl);
   }
   template <int TY>
   static cudaError_t yinv_t(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st) {
+                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, bool pdl) {
     const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yinv<R, M1, M2, TY>, sm);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(!std::is_same<R, double>::value, fk_yinv<R, M1, M2, TY>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
+    e = launch_pdl(pdl, fk_yinv<R, M1, M2, TY>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
                    dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, skip);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
   }
   static cudaError_t yinv(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var) {
-    return var == 1 ? yinv_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st)
-                    : yinv_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st);
+                          const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var,
+                          bool pdl) {
+    return var == 1 ? yinv_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl)
+                    : yinv_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl);
   }
   template <int TC>
   static cudaError_t zconv_t(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
-                             int nrhs, const int* skip, cudaStream_t st) {
+                             int nrhs, const int* skip, cudaStream_t st, bool pdl) {
     const size_t sm = (size_t)(M + 3 * ZRows<R, M1, M2, TC>::rows * TC) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_zconv<R, M1, M2, TC>, sm);
     if (e != cudaSuccess) return e;
     // two ~106 KB blocks per SM need the largest shared-memory carveout
     e = ensure_carveout_max((const void*)fk_zconv<R, M1, M2, TC>);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(!std::is_same<R, double>::value, fk_zconv<R, M1, M2, TC>, dim3((Mx + TC - 1) / TC, My, nrhs), dim3(TC * kQ<M1, M2>),
+    e = launch_pdl(pdl, fk_zconv<R, M1, M2, TC>, dim3((Mx + TC - 1) / TC, My, nrhs), dim3(TC * kQ<M1, M2>),
                    sm, st, B2, D, nz, Mx, My, tw, skip);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
   }
   static cudaError_t zconv(cpx<R>* B2, const cpx<R>* D, int nz, int Mx, int My, const cpx<R>* tw,
-                           int nrhs, const int* skip, cudaStream_t st, int var) {
-    return var == 1 ? zconv_t<TZ / 2>(B2, D, nz, Mx, My, tw, nrhs, skip, st)
-                    : zconv_t<TZ>(B2, D, nz, Mx, My, tw, nrhs, skip, st);
+                           int nrhs, const int* skip, cudaStream_t st, int var, bool pdl) {
+    return var == 1 ? zconv_t<TZ / 2>(B2, D, nz, Mx, My, tw, nrhs, skip, st, pdl)
+                    : zconv_t<TZ>(B2, D, nz, Mx, My, tw, nrhs, skip, st, pdl);
   }
   using V = typename VecOf<R>::type;
   static cudaError_t xfwd(const V* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,
                           long long n_occ, int nrows, const cpx<R>* tw, bool adj, int nrhs,
-                          int bstride, const int* skip, cudaStream_t st) {
-    const size_t sm = (size_t)(M + TX * kLD<M>) * sizeof(cpx<R>);
-    const dim3 grid((nrows + TX - 1) / TX, 3 * nrhs);
+                          int bstride, const int* skip, cudaStream_t st, bool pdl) {
+    const size_t sm = (size_t)(M + TXF * kLD<M>) * sizeof(cpx<R>);
+    const dim3 grid((nrows + TXF - 1) / TXF, 3 * nrhs);
     cudaError_t e;
     if (adj) {
-      if ((e = set_smem(fk_xfwd<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(!std::is_same<R, double>::value, fk_xfwd<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
+      if ((e = set_smem(fk_xfwd<R, M1, M2, TXF, true>, sm)) != cudaSuccess) return e;
+      e = launch_pdl(pdl, fk_xfwd<R, M1, M2, TXF, true>, grid, dim3(NTXF), sm, st, x, B1, lat, beta, n_occ,
                      nrows, tw, bstride, skip);
     } else {
-      if ((e = set_smem(fk_xfwd<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(!std::is_same<R, double>::value, fk_xfwd<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
+      if ((e = set_smem(fk_xfwd<R, M1, M2, TXF, false>, sm)) != cudaSuccess) return e;
+      e = launch_pdl(pdl, fk_xfwd<R, M1, M2, TXF, false>, grid, dim3(NTXF), sm, st, x, B1, lat, beta, n_occ,
                      nrows, tw, bstride, skip);
     }
     count_launch();
@@ -957,7 +1030,8 @@ struct Passes {
   }
   static cudaError_t xinv(const cpx<R>* B1, const V* x, V* y, const LatticeDev& lat,
                           const cpx<R>* beta, long long n_occ, int nrows, const cpx<R>* tw, bool adj,
-                          double* dotp, int nrhs, int bstride, const int* skip, cudaStream_t st) {
+                          double* dotp, int nrhs, int bstride, const int* skip, cudaStream_t st,
+                          bool pdl) {
     const size_t sm = (size_t)(M + TX * kLD<M>) * sizeof(cpx<R>) + (size_t)TX * kXRow<M> * sizeof(V);
     const dim3 grid((nrows + TX - 1) / TX, 3 * nrhs);
     cudaError_t e;
@@ -966,11 +1040,11 @@ struct Passes {
     if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, TX, false>)) != cudaSuccess) return e;
     if (adj) {
       if ((e = set_smem(fk_xinv<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(!std::is_same<R, double>::value, fk_xinv<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta, n_occ,
+      e = launch_pdl(pdl, fk_xinv<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta, n_occ,
                      nrows, tw, dotp, bstride, skip);
     } else {
       if ((e = set_smem(fk_xinv<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(!std::is_same<R, double>::value, fk_xinv<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta,
+      e = launch_pdl(pdl, fk_xinv<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, B1, x, y, lat, beta,
                      n_occ, nrows, tw, dotp, bstride, skip);
     }
     count_launch();

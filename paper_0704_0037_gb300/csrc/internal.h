@@ -284,14 +284,29 @@ struct FastArgs {
   // tile variants of FP_YFWD, FP_ZCONV, FP_YINV (0: default lines per block,
   // 1: half as many; the same product bit for bit)
   int var_yf = 0, var_z = 0, var_yi = 0;
+  // launch the passes as programmatic dependents (fast_pdl)
+  bool pdl = false;
 };
+// Whether the product passes launch as programmatic dependents: for the
+// complex64 and double-float arithmetic on grids of up to 2^23 points over
+// all right-hand sides, where a pass is a few microseconds and the launch
+// latency it hides is a large part of it.  On larger grids the attribute
+// measured slower for the memory-bound complex64 passes (a standalone
+// product 0.507 -> 0.542 ms at 270^3, 3.85 -> 4.13 ms at 512^3).
+inline bool fast_pdl(bool fp64, long long Mx, long long My, long long Mz, int nrhs) {
+  return !fp64 && Mx * My * Mz * nrhs <= (1LL << 23);
+}
+// rows per block of the x inverse pass: 16 for complex64 lines shorter than
+// 1000 points, 8 for the longer ones and for the double-width arithmetic
+inline int fast_x_rows(bool fp32, int Mx) { return fp32 ? (Mx < 1000 ? 16 : 4) : 8; }
 // number of (re, im) partials FP_XINV writes to dotp for nrows rows
-// (rows per block: 16 for complex64 lines shorter than 1000 points, else 8;
-// fp32 false gives the count of the double-width passes, the largest)
-inline int fast_xinv_blocks(int nrows, bool fp32, int Mx = 0) {
-  const int t = (fp32 && Mx < 1000) ? 16 : 8;
+inline int fast_xinv_blocks(int nrows, bool fp32, int Mx) {
+  const int t = fast_x_rows(fp32, Mx);
   return 3 * ((nrows + t - 1) / t);
 }
+// the most partials any arithmetic and length writes for nrows rows (the
+// size of the buffers that receive them)
+inline int fast_xinv_blocks_max(int nrows) { return 3 * ((nrows + 3) / 4); }
 bool fast_supported(int M);          // complex64, complex128 and double-float passes
 bool fast_supported_c64(int M);      // complex64 passes (also 512 and 1080)
 cudaError_t fast_pass_512_c64(int pass, const FastArgs& a);
@@ -351,10 +366,10 @@ namespace dda {
 // Launch with programmatic stream serialization when pdl is set: the kernel
 // may be scheduled while the previous kernel on st finishes, so it must call
 // pdl_wait() (common.cuh) before reading what earlier work on st wrote.  The
-// complex64 and double-float product passes and the QMR sweeps use it (a
-// 16^3 sphere's FP32-refined solve 1.68 -> 1.24 ms, its FP64 solve 2.36 ->
-// 2.20 ms); the complex128 product passes measured slower with it (the FP64
-// solve 2.36 -> 3.37 ms) and launch plainly.
+// QMR sweeps use it, and the complex64 and double-float product passes on the
+// grids fast_pdl selects (a 16^3 sphere's FP32-refined solve 1.68 -> 1.24 ms,
+// its FP64 solve 2.36 -> 2.20 ms); the complex128 product passes measured
+// slower with it (the FP64 solve 2.36 -> 3.37 ms) and launch plainly.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t st, Args... args) {

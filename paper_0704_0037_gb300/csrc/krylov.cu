@@ -1025,7 +1025,7 @@ int ensure_solver_mem(dda_t h, size_t bytes) {
   if (!h->d_part) {
     if (dev_malloc(&h->d_part, kSlots * kNB * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver partials"); }
     if (dev_malloc(&h->d_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "solver scalars"); }
-    const size_t mvp = 2 * (size_t)fast_xinv_blocks(h->g.nrows, false);
+    const size_t mvp = 2 * (size_t)fast_xinv_blocks_max(h->g.nrows);
     if (dev_malloc(&h->d_mvpart, mvp * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "product partials"); }
     if (cudaMallocHost(&h->h_scal, sizeof(Scal)) != cudaSuccess) { cudaGetLastError(); return dda_fail(h, DDA_ERR_OOM, "pinned scalars"); }
   }
@@ -1391,7 +1391,7 @@ int bm_ensure(dda_t h, int nrhs, size_t sv_bytes) {
     m->sv2 = nullptr; m->sv2_bytes = 0;
     bm_release(m, h->stream);
     *m = fresh;
-    const size_t mvp = 2 * (size_t)fast_xinv_blocks(h->g.nrows, false) * nrhs;
+    const size_t mvp = 2 * (size_t)fast_xinv_blocks_max(h->g.nrows) * nrhs;
     if (dev_malloc(&m->ds, nrhs * sizeof(Scal)) != cudaSuccess ||
         cudaMallocHost(&m->hs, nrhs * sizeof(Scal)) != cudaSuccess ||
         dev_malloc(&m->part, (size_t)nrhs * kPS * sizeof(double)) != cudaSuccess ||

@@ -348,6 +348,7 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
     fa.lat = lat; fa.beta = br; fa.D = w.D; fa.n_occ = g.n_occ; fa.nrows = g.nrows;
     fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = adjoint; fa.st = st;
     fa.nrhs = cnt; fa.bstride = bstride; fa.skip = sk;
+    fa.pdl = fast_pdl(std::is_same<R, double>::value, g.Mx, g.My, g.Mz, cnt);
     {
       const int* tl = g.tiles[std::is_same<R, float>::value ? 0 : 1];
       fa.var_yf = tl[0] > 0 ? tl[0] : 0; fa.var_z = tl[1] > 0 ? tl[1] : 0; fa.var_yi = tl[2] > 0 ? tl[2] : 0;
@@ -453,6 +454,7 @@ cudaError_t launch_matvec_df(const Geom& g, const LatticeDev& lat, Work<df>& w, 
     fa.lat = lat; fa.beta = w.beta + (long long)r0 * bstride; fa.D = w.D; fa.n_occ = g.n_occ;
     fa.nrows = g.nrows; fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = false;
     fa.st = st; fa.nrhs = cnt; fa.bstride = bstride; fa.skip = skip ? skip + r0 : nullptr;
+    fa.pdl = fast_pdl(false, g.Mx, g.My, g.Mz, cnt);
     fa.var_yf = g.tiles[2][0] > 0 ? g.tiles[2][0] : 0;
     fa.var_z = g.tiles[2][1] > 0 ? g.tiles[2][1] : 0;
     fa.var_yi = g.tiles[2][2] > 0 ? g.tiles[2][2] : 0;

@@ -53,8 +53,8 @@ def test_every_tile_variant_gives_the_same_product(name, occ, m, grid, form):
             assert torch.equal(y, ys[0]), v
 
 
-# the three-level z pass of the long complex64 lines (512 = 8 x 8 x 8,
-# 1080 = 12 x 9 x 10), the other axes Stockham
+# the z pass of the long complex64 lines (512 = 16 x 32, 1080 = 30 x 36:
+# fewer columns per block), the other axes Stockham
 LONG_Z = [("ellipsoid6x5x256", inputs.ellipsoid(6, 5, 256), 512),
           ("ellipsoid4x3x540", inputs.ellipsoid(4, 3, 540), 1080)]
 
