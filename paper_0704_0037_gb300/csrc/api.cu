@@ -365,6 +365,28 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
     });
   }
   g.n_occ = h->row_off_h[g.nrows];
+  // per z plane the span of its occupied rows, and the rows of all spans
+  std::vector<int> yr_h(2 * (size_t)nz), arow_h;
+  std::vector<long long> aoff_h;
+  for (int z = 0; z < nz; ++z) {
+    int lo = ny, hi = -1;
+    for (int y = 0; y < ny; ++y) {
+      const size_t r = (size_t)z * ny + y;
+      if (h->row_off_h[r + 1] > h->row_off_h[r]) {
+        lo = std::min(lo, y);
+        hi = y;
+      }
+    }
+    if (hi < 0) { lo = 1; hi = 0; }
+    yr_h[2 * z] = lo;
+    yr_h[2 * z + 1] = hi;
+    for (int y = lo; y <= hi; ++y) {
+      arow_h.push_back(z * ny + y);
+      aoff_h.push_back(h->row_off_h[(size_t)z * ny + y]);
+    }
+  }
+  aoff_h.push_back(g.n_occ);
+  h->nact = (int)arow_h.size();
   const std::vector<uint8_t>& mat = h->mat_h;
   g.Mx = padded_length(2 * nx - 1, DDA_ENGINE_AUTO);
   g.My = padded_length(2 * ny - 1, DDA_ENGINE_AUTO);
@@ -380,14 +402,23 @@ extern "C" int dda_init_lattice(dda_t* out, int nx, int ny, int nz, const uint8_
   int rc = DDA_OK;
   if (dev_malloc(&h->d_row_off, h->row_off_h.size() * sizeof(long long)) != cudaSuccess ||
       dev_malloc(&h->d_xi, h->xi_h.size() * sizeof(uint16_t)) != cudaSuccess ||
-      dev_malloc(&h->d_mat, mat.size()) != cudaSuccess) {
+      dev_malloc(&h->d_mat, mat.size()) != cudaSuccess ||
+      dev_malloc(&h->d_arow, arow_h.size() * sizeof(int)) != cudaSuccess ||
+      dev_malloc(&h->d_aoff, aoff_h.size() * sizeof(long long)) != cudaSuccess ||
+      dev_malloc(&h->d_yr, yr_h.size() * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     rc = DDA_ERR_OOM;
   } else if (cudaMemcpy(h->d_row_off, h->row_off_h.data(), h->row_off_h.size() * sizeof(long long),
                         cudaMemcpyHostToDevice) != cudaSuccess ||
              cudaMemcpy(h->d_xi, h->xi_h.data(), h->xi_h.size() * sizeof(uint16_t),
                         cudaMemcpyHostToDevice) != cudaSuccess ||
-             cudaMemcpy(h->d_mat, mat.data(), mat.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+             cudaMemcpy(h->d_mat, mat.data(), mat.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(h->d_arow, arow_h.data(), arow_h.size() * sizeof(int),
+                        cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(h->d_aoff, aoff_h.data(), aoff_h.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(h->d_yr, yr_h.data(), yr_h.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                 cudaSuccess) {
     cudaGetLastError();
     rc = DDA_ERR_CUDA;
   }
@@ -792,6 +823,7 @@ extern "C" int dda_free(dda_t h) {
   free_work(h->w32, h->stream);
   free_work(h->wdf, h->stream);
   dev_free(h->d_row_off, h->stream); dev_free(h->d_xi, h->stream); dev_free(h->d_mat, h->stream);
+  dev_free(h->d_arow, h->stream); dev_free(h->d_aoff, h->stream); dev_free(h->d_yr, h->stream);
   dev_free(h->sv, h->stream); dev_free(h->d_part, h->stream); dev_free(h->d_mvpart, h->stream); dev_free(h->d_scal, h->stream); cudaFreeHost(h->h_scal);
   batch_free(h);
   dev_free(h->d_tab, h->stream); dev_free(h->d_fpart, h->stream); dev_free(h->d_coll, h->stream); dev_free(h->d_dscratch, h->stream);

@@ -16,7 +16,7 @@ cudaError_t run_pass(int pass, const FastArgs& a) {
                      a.nrows, tw, a.adj, a.nrhs, a.bstride, a.skip, a.st, a.pdl);
     case FP_YFWD:
       return P::yfwd((const cpx<R>*)a.in, (cpx<R>*)a.out, a.ny, a.nz, a.Mx, tw, a.nrhs, a.skip, a.st,
-                     a.var_yf, a.pdl);
+                     a.var_yf, a.pdl, a.lat.yr);
     case FP_ZCONV:
       return P::zconv((cpx<R>*)a.out, (const cpx<R>*)a.D, a.nz, a.Mx, a.My, tw, a.nrhs, a.skip,
                       a.st, a.var_z, a.pdl);

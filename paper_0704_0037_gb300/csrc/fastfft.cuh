@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
                                                           cpx<R>* __restrict__ out, int ny, int nz,
                                                           int Mx, const cpx<R>* __restrict__ tw,
                                                           int msign, const int* __restrict__ skip,
-                                                          long long ostr) {
+                                                          long long ostr, const int* __restrict__ yr) {
   constexpr int M = M1 * M2, NT = T * kQ<M1, M2>;
   pdl_wait();
   pdl_launch();
@@ -96,8 +96,14 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
   const long long og = (long long)blockIdx.z * nz + blockIdx.y;
   const long long ib = ostr ? og * ostr : og * ny * Mx;
   const long long ob = ostr ? og * ostr : og * M * Mx;
+  // rows of plane blockIdx.y outside its span of occupied rows are not read
+  // (zero; the x pass does not write them) when the spans are given; the
+  // span is fetched with the twiddles
+  __shared__ int s_yr[2];
+  if (threadIdx.x < 2) s_yr[threadIdx.x] = yr ? yr[2 * blockIdx.y + threadIdx.x] : (threadIdx.x ? ny - 1 : 0);
   load_tw(s_tw, tw, M, NT);
   __syncthreads();
+  const int ylo = s_yr[0], yhi = s_yr[1];
   if (q < M2) {
     const int j = q;
     cpx<R> v[M1];
@@ -105,8 +111,9 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>) fk_yfwd(const cpx<R>* __restri
 #pragma unroll
       for (int i = 0; i < M1; ++i) {
         const int y = j + M2 * i;
-        v[i] = ((!PRUNE || i < kHalf<M1, M2>) && y < ny && kx < Mx) ? in[ib + (long long)y * Mx + kx]
-                                                                     : zero<R>();
+        v[i] = ((!PRUNE || i < kHalf<M1, M2>) && y >= ylo && y <= yhi && kx < Mx)
+                   ? in[ib + (long long)y * Mx + kx]
+                   : zero<R>();
       }
     } else {
 #pragma unroll
@@ -605,8 +612,16 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 *
   pdl_launch();
   if (skip && skip[cc / 3]) return;
   beta += (long long)(cc / 3) * bstride;
+  // the rows transformed: those within the planes' spans of occupied rows
+  // when the lattice lists them, else every row
+  __shared__ int s_row[T];
+  const int nr = lat.arow ? lat.nact : nrows;
   const int r0 = blockIdx.x * T;
-  if (threadIdx.x <= T) s_off[threadIdx.x] = lat.row_off[min(r0 + (int)threadIdx.x, nrows)];
+  if (threadIdx.x <= T) {
+    const int i = min(r0 + (int)threadIdx.x, nr);
+    s_off[threadIdx.x] = lat.arow ? lat.aoff[i] : lat.row_off[i];
+    if (threadIdx.x < T) s_row[threadIdx.x] = lat.arow ? lat.arow[min(i, nr - 1)] : i;
+  }
   load_tw(s_tw, tw, M, NT);
   for (int i = threadIdx.x; i < T * LD; i += NT) a[i] = zero<R>();
   __syncthreads();
@@ -670,12 +685,12 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 *
     for (int k2 = 0; k2 < M2; ++k2) at[k1 + M1 * k2] = u[k2];
   }
   __syncthreads();
-  // the block's rows are contiguous in B1
-  cpx<R>* out = B1 + ((long long)cc * nrows + r0) * M;
-  const int nel = min(T, nrows - r0) * M;
+  // row tt of the block is row s_row[tt] of B1
+  cpx<R>* out = B1 + (long long)cc * nrows * M;
+  const int nel = min(T, nr - r0) * M;
   for (int idx = threadIdx.x; idx < nel; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
-    out[idx] = a[tt * LD + m];
+    out[(long long)s_row[tt] * M + m] = a[tt * LD + m];
   }
 }
 
@@ -717,22 +732,35 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, kXinvB<R
   pdl_launch();
   if (skip && skip[cc / 3]) return;
   beta += (long long)(cc / 3) * bstride;
+  // the rows transformed: those within the planes' spans of occupied rows
+  // when the lattice lists them (the rows outside hold no dipole), else
+  // every row; a block's rows are consecutive in B1 unless they cross planes
+  const int nr = lat.arow ? lat.nact : nrows;
   const int r0 = blockIdx.x * T;
-  const int rows = min(T, nrows - r0);
-  const cpx<R>* in = B1 + ((long long)cc * nrows + r0) * M;
+  const int rows = min(T, nr - r0);
+  const long long* off = lat.arow ? lat.aoff : lat.row_off;
+  int rb = r0;
+  bool runs = false;
+  if (lat.arow) {
+    rb = lat.arow[r0];
+    runs = lat.arow[r0 + rows - 1] - rb != rows - 1;
+  }
+  const cpx<R>* in = B1 + (long long)cc * nrows * M;
   for (int idx = threadIdx.x; idx < T * M; idx += NT) {
     const int tt = idx / M, m = idx - tt * M;
     const bool ok = tt < rows;
-    cp_async_elem<sizeof(cpx<R>)>(a + tt * LD + m, ok ? (const void*)(in + idx) : (const void*)B1, ok);
+    const long long row = runs ? (ok ? lat.arow[r0 + tt] : 0) : rb + tt;
+    cp_async_elem<sizeof(cpx<R>)>(a + tt * LD + m, ok ? (const void*)(in + row * M + m) : (const void*)B1,
+                                  ok);
   }
   const V* xc = x + (long long)cc * n_occ;
   V* yc = y + (long long)cc * n_occ;
-  const long long S0 = lat.row_off[r0];
-  const int span = (int)(lat.row_off[r0 + rows] - S0);
+  const long long S0 = off[r0];
+  const int span = (int)(off[r0 + rows] - S0);
   const int staged = min(span, kXS);
   for (int k = threadIdx.x; k < staged; k += NT) cp_async_elem<sizeof(V)>(s_x + k, xc + S0 + k, true);
   cp_async_commit();
-  if (threadIdx.x <= T) s_off[threadIdx.x] = lat.row_off[min(r0 + (int)threadIdx.x, nrows)];
+  if (threadIdx.x <= T) s_off[threadIdx.x] = off[min(r0 + (int)threadIdx.x, nr)];
   load_tw(s_tw, tw, M, NT);
   cp_async_wait<0>();
   __syncthreads();
@@ -932,20 +960,21 @@ struct Passes {
   // autotuner picks one by timing.
   template <int TY>
   static cudaError_t yfwd_t(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
-                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, bool pdl) {
+                            const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, bool pdl,
+                            const int* yr) {
     const size_t sm = (size_t)(M + M * TY) * sizeof(cpx<R>);
     cudaError_t e = set_smem(fk_yfwd<R, M1, M2, TY, true>, sm);
     if (e != cudaSuccess) return e;
     e = launch_pdl(pdl, fk_yfwd<R, M1, M2, TY, true>, dim3((Mx + TY - 1) / TY, nz, 3 * nrhs),
-                   dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, 0, skip, 0LL);
+                   dim3(TY * kQ<M1, M2>), sm, st, in, out, ny, nz, Mx, tw, 0, skip, 0LL, yr);
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
   }
   static cudaError_t yfwd(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
                           const cpx<R>* tw, int nrhs, const int* skip, cudaStream_t st, int var,
-                          bool pdl) {
-    return var == 1 ? yfwd_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl)
-                    : yfwd_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl);
+                          bool pdl, const int* yr) {
+    return var == 1 ? yfwd_t<T / 2>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl, yr)
+                    : yfwd_t<T>(in, out, ny, nz, Mx, tw, nrhs, skip, st, pdl, yr);
   }
   template <int TY>
   static cudaError_t yinv_t(const cpx<R>* in, cpx<R>* out, int ny, int nz, int Mx,
@@ -988,7 +1017,8 @@ struct Passes {
                           long long n_occ, int nrows, const cpx<R>* tw, bool adj, int nrhs,
                           int bstride, const int* skip, cudaStream_t st, bool pdl) {
     const size_t sm = (size_t)(M + TXF * kLD<M>) * sizeof(cpx<R>);
-    const dim3 grid((nrows + TXF - 1) / TXF, 3 * nrhs);
+    const int nr = lat.arow ? lat.nact : nrows;
+    const dim3 grid((nr + TXF - 1) / TXF, 3 * nrhs);
     cudaError_t e;
     if (adj) {
       if ((e = set_smem(fk_xfwd<R, M1, M2, TXF, true>, sm)) != cudaSuccess) return e;
@@ -1024,7 +1054,7 @@ struct Passes {
     if (e != cudaSuccess) return e;
     fk_yfwd<R, M1, M2, T, false><<<dim3((nlines + T - 1) / T, n_outer, 1), NT, sm, st>>>(in, out, M, n_outer,
                                                                                  stride, tw, msign,
-                                                                                 nullptr, ostride);
+                                                                                 nullptr, ostride, nullptr);
     count_launch();
     return cudaGetLastError();
   }
@@ -1033,7 +1063,8 @@ struct Passes {
                           double* dotp, int nrhs, int bstride, const int* skip, cudaStream_t st,
                           bool pdl) {
     const size_t sm = (size_t)(M + TX * kLD<M>) * sizeof(cpx<R>) + (size_t)TX * kXRow<M> * sizeof(V);
-    const dim3 grid((nrows + TX - 1) / TX, 3 * nrhs);
+    const int nr = lat.arow ? lat.nact : nrows;
+    const dim3 grid((nr + TX - 1) / TX, 3 * nrhs);
     cudaError_t e;
     // three blocks of up to ~56 KB per SM need a large shared-memory carveout
     if ((e = ensure_carveout_max((const void*)fk_xinv<R, M1, M2, TX, true>)) != cudaSuccess) return e;

@@ -63,6 +63,16 @@ struct LatticeDev {
   const long long* row_off;
   const uint16_t* xi;
   const uint8_t* mat;
+  // The rows that hold dipoles lie, in each z plane, within the span
+  // yr[2 z] <= y <= yr[2 z + 1] of its occupied rows (an empty plane has
+  // yr = {1, 0}); arow lists the nact rows of all spans in increasing order
+  // and aoff[i] = row_off[arow[i]] (aoff[nact] = n_occ).  The register-resident
+  // x passes transform only these rows and the y forward pass reads only
+  // them (nullptr: every row).
+  const int* arow = nullptr;
+  const long long* aoff = nullptr;
+  const int* yr = nullptr;
+  int nact = 0;
 };
 
 // Layout of the D-matrix octant: interleaved by point for complex64 (its six
@@ -185,7 +195,11 @@ struct dda_ctx {
   void* d_dscratch = nullptr;     // D-matrix build scratch kept between builds (small grids)
   size_t dscratch_bytes = 0;
   void* d_ptab = nullptr;         // incident-wave phase per axis (right-hand sides), complex128
-  dda::LatticeDev lat() const { return {d_row_off, d_xi, d_mat}; }
+  int* d_arow = nullptr;          // rows within each plane's span of occupied rows
+  long long* d_aoff = nullptr;    // their dipole offsets (+ n_occ)
+  int* d_yr = nullptr;            // per z plane: first and last occupied row
+  int nact = 0;
+  dda::LatticeDev lat() const { return {d_row_off, d_xi, d_mat, d_arow, d_aoff, d_yr, nact}; }
 };
 
 int dda_fail(dda_t h, int code, const std::string& msg);

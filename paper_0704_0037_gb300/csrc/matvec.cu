@@ -333,7 +333,17 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
   const bool fx = g.engine == 0 && has_fast(g.Mx);
   const bool fy = g.engine == 0 && has_fast(g.My);
   const bool fz = g.engine == 0 && has_fast(g.Mz);
-  const int dnb = fast_xinv_blocks(g.nrows, sizeof(R) == 4, g.Mx);
+  // the register-resident x and y passes skip the rows outside the planes'
+  // spans of occupied rows when all four are register-resident (the
+  // Stockham passes transform every row)
+  LatticeDev la = lat;
+  if (!(fx && fy)) {
+    la.arow = nullptr;
+    la.aoff = nullptr;
+    la.yr = nullptr;
+    la.nact = 0;
+  }
+  const int dnb = fast_xinv_blocks(la.arow ? la.nact : g.nrows, sizeof(R) == 4, g.Mx);
   if (dotp && dot_nb && fx) *dot_nb = dnb;
   // right-hand sides in chunks of the work buffers' capacity, each chunk in
   // one launch per pass
@@ -345,7 +355,7 @@ cudaError_t launch_matvec(const Geom& g, const LatticeDev& lat, Work<R>& w, cons
     const cpx<R>* br = beta + (long long)r0 * bstride;
     const int* sk = skip ? skip + r0 : nullptr;
     FastArgs fa{};
-    fa.lat = lat; fa.beta = br; fa.D = w.D; fa.n_occ = g.n_occ; fa.nrows = g.nrows;
+    fa.lat = la; fa.beta = br; fa.D = w.D; fa.n_occ = g.n_occ; fa.nrows = g.nrows;
     fa.ny = g.ny; fa.nz = g.nz; fa.Mx = g.Mx; fa.My = g.My; fa.adj = adjoint; fa.st = st;
     fa.nrhs = cnt; fa.bstride = bstride; fa.skip = sk;
     fa.pdl = fast_pdl(std::is_same<R, double>::value, g.Mx, g.My, g.Mz, cnt);

@@ -258,6 +258,10 @@ int dda_scatter_internal(dda_t h, int presc, const void* P_dev, int nrhs, const 
     flat.row_off = roff;
     flat.xi = xis;
     flat.mat = nullptr;
+    flat.arow = nullptr;
+    flat.aoff = nullptr;
+    flat.yr = nullptr;
+    flat.nact = 0;
   }
   const int L = fnx + fny + fnz;
   const int qblocks = (int)std::min<long long>((g.nrows + 7) / 8, 1024);

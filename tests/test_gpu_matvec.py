@@ -13,6 +13,19 @@ from gpu_util import direct_sum_rows, need_gpu, rel_l2, sample_dipoles, twin
 
 pytestmark = pytest.mark.gpu
 
+def _gaps():
+    """A lattice whose occupied rows leave gaps: empty z planes, planes whose
+    span of occupied rows holds empty rows, planes of one dipole, and more
+    planes than one block of rows covers (16 x 20 x 18 box, grid 32 x 40 x 40)."""
+    occ = np.zeros((18, 20, 16), np.uint8)       # (z, y, x)
+    occ[2:6, 1:4, 3:9] = 1
+    occ[3, 12, :] = 2                            # plane 3: rows 1-3 and 12
+    occ[9, 10, 7] = 1                            # plane 9: one dipole
+    occ[12:16, 15:20, 5:12] = 2
+    occ[14, 0, 15] = 1                           # plane 14: rows 0 and 15-19
+    return occ
+
+
 CASES = [
     ("sphere1", inputs.sphere(1), [1.5]),
     ("sphere2", inputs.sphere(2), [1.5]),
@@ -25,6 +38,7 @@ CASES = [
     ("sphere16", inputs.sphere(16), [1.5]),
     ("ellipsoid33x20x17", inputs.ellipsoid(33, 20, 17), [1.33]),
     ("random40x9x23", inputs.random_occupancy(40, 9, 23, 0.3, seed=3, n_mat=3), [1.5, 1.05, 2.0 + 0.1j]),
+    ("gaps16x20x18", _gaps(), [1.5, 1.2 + 0.05j]),
 ]
 
 
@@ -73,6 +87,7 @@ DF_CASES = [
     ("random16x64x16", inputs.random_occupancy(16, 64, 16, 0.5, seed=4, n_mat=2),
      [1.5 + 0.1j, 2.0]),                                                        # 32 x 128 x 32
     ("ellipsoid64x16x16", inputs.ellipsoid(64, 16, 16), [1.33]),                 # 128 x 32 x 32
+    ("gaps16x20x18", _gaps(), [1.5, 1.2 + 0.05j]),                              # 32 x 40 x 40
 ]
 
 
