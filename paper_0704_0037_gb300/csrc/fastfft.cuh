@@ -706,9 +706,10 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 *
 // dipoles; the long lines stage up to 384 (about the mean of the 536^3
 // sphere's 4-row tiles) and read the rest directly
 template <int M> constexpr int kXRow = (M + 1) / 2 < 384 ? (M + 1) / 2 : 384;
-// blocks per SM the x inverse pass's launch bound asks for: four blocks of
-// 4.5 warps for the long complex64 lines, else three
-template <typename R, int M> constexpr int kXinvB = (sizeof(R) == 4 && M >= 1000) ? 4 : 3;
+// blocks per SM the x inverse pass's launch bound asks for: four in
+// complex64 (at 270 points 56 registers, no spill: P5 of the 134^3 sphere
+// 59 -> 55 us), three in the wider arithmetic
+template <typename R, int M> constexpr int kXinvB = (sizeof(R) == 4) ? 4 : 3;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
 __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, kXinvB<R, M1 * M2>, (M1 * M2 + T * kLD<M1 * M2>) * sizeof(cpx<R>) + T * kXRow<M1 * M2> * sizeof(typename VecOf<R>::type))) fk_xinv(const cpx<R>* __restrict__ B1,
