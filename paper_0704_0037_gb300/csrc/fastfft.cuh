@@ -350,39 +350,55 @@ __device__ __forceinline__ void zc_prefetch(const cpx<R>* D, int Mx, int My, int
 // Fourier-space product with the octant of FFT(G).  Work item (t, fz): the
 // six octant values at (fx, fy, fz) are loaded once and applied to both
 // kz = fz and kz = M - fz (sign flips for the components odd in z); the
-// spectrum value kz of column t lives in row row_of(kz); components are CS
-// elements apart.
-template <typename R, int M, int T, int NT, int CS, typename RowOf>
+// spectrum value kz = k1 + M1 k2 of column t lives in row Z::at(k1, k2);
+// components are CS elements apart.  A thread keeps its column t and steps
+// fz by NT / T, so its octant index and the (k1, k2) of both kz advance by
+// constants instead of being recomputed (no division per item).
+template <typename R, int M1, int M2, int T, int NT, int CS>
 __device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__ D, int Mx, int My,
-                                           int bx, int ky, RowOf row_of) {
-  const int hx = Mx / 2 + 1, hy = My / 2 + 1, hz = M / 2 + 1;
+                                           int bx, int ky) {
+  using Z = ZRows<R, M1, M2, T>;
+  constexpr int M = M1 * M2, hz = M / 2 + 1;
+  static_assert(NT % T == 0, "a thread's work items share its column");
+  constexpr int FS = NT / T, S1 = FS % M1, S2 = FS / M1;
+  const int hx = Mx / 2 + 1, hy = My / 2 + 1;
   int nys;
   const int fy = fold_axis(ky, My, nys);
-  const int kx0 = bx * T;
+  const int t2 = threadIdx.x % T;
+  const int kx2 = bx * T + t2;
+  if (kx2 >= Mx) return;
+  int nxs;
+  const int fx = fold_axis(kx2, Mx, nxs);
+  const long long octs = (long long)hx * hy * hz;
+  const long long ostep = (long long)FS * hy * hx;
+  int fz = threadIdx.x / T;
+  long long o = ((long long)fz * hy + fy) * hx + fx;
+  int a1 = fz % M1, a2 = fz / M1;                // kz = fz
+  int b1 = (M - fz) % M1, b2 = (M - fz) / M1;    // kz = M - fz
 #pragma unroll 2
-  for (int it = threadIdx.x; it < T * hz; it += NT) {
-    const int t2 = it % T, fz = it / T;
-    const int kx2 = kx0 + t2;
-    if (kx2 >= Mx) continue;
-    int nxs;
-    const int fx = fold_axis(kx2, Mx, nxs);
+  for (; fz < hz; fz += FS, o += ostep) {
     cpx<R> d6[6];
-    load_oct<R>(D, ((long long)fz * hy + fy) * hx + fx, (long long)hx * hy * hz, d6);
+    load_oct<R>(D, o, octs, d6);
     const cpx<R> dxx = d6[0], dyy = d6[3], dzz = d6[5];
     cpx<R> dxy = d6[1], dxz = d6[2], dyz = d6[4];
     if (nxs ^ nys) dxy = mk<R>(-dxy.x, -dxy.y);
     const int nkz = (fz == 0 || 2 * fz == M) ? 1 : 2;
     for (int h = 0; h < nkz; ++h) {
-      const int kz = h ? M - fz : fz;
       cpx<R> ez = dxz, fzz = dyz;
       if (nxs ^ h) ez = mk<R>(-ez.x, -ez.y);
       if (nys ^ h) fzz = mk<R>(-fzz.x, -fzz.y);
-      const int e = row_of(kz) * T + t2;
+      const int e = (h ? Z::at(b1, b2) : Z::at(a1, a2)) * T + t2;
       const cpx<R> vx = s[e], vy = s[CS + e], vz = s[2 * CS + e];
       s[e] = dxx * vx + dxy * vy + ez * vz;
       s[CS + e] = dxy * vx + dyy * vy + fzz * vz;
       s[2 * CS + e] = ez * vx + fzz * vy + dzz * vz;
     }
+    a1 += S1;
+    a2 += S2;
+    if (a1 >= M1) { a1 -= M1; ++a2; }
+    b1 -= S1;
+    b2 -= S2;
+    if (b1 < 0) { b1 += M1; --b2; }
   }
 }
 
@@ -415,7 +431,7 @@ __device__ __forceinline__ void zc_m2_one_codelet(cpx<R>* s, const cpx<R>* s_tw,
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) {
-      zc_product<R, M, T, NT, CS>(s, D, Mx, My, bx, ky, [](int kz) { return Z::at(kz % M1, kz / M1); });
+      zc_product<R, M1, M2, T, NT, CS>(s, D, Mx, My, bx, ky);
       __syncthreads();
     }
     if (q < M1 && kx < Mx) {
@@ -501,7 +517,7 @@ __device__ __forceinline__ void zc_forward_product_inva(cpx<R>* s, const cpx<R>*
   }
   __syncthreads();
   // kz = k1 + M1 k2 lives in row k1*M2 + k2
-  zc_product<R, M, T, NT, CS>(s, D, Mx, My, bx, ky, [](int kz) { return Z::at(kz % M1, kz / M1); });
+  zc_product<R, M1, M2, T, NT, CS>(s, D, Mx, My, bx, ky);
   __syncthreads();
   if (q < M1 && kx < Mx) {
     const int k1 = q;
