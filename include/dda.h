@@ -235,9 +235,12 @@ typedef struct {
   int status;           /* enum dda_status of this RHS                           */
   int iters;            /* solver iterations (all inner iterations for FP32)      */
   int matvecs;          /* products with A or A^H (any precision)                 */
-  int matvecs_fp64;     /* of which in FP64                                       */
+  int matvecs_fp64;     /* of which FP64-class (native FP64, or double-float)     */
   int outer;            /* FP32_REFINED: refinement steps; FP64: 0                */
-  double rel_res_true;  /* ||b - A x|| / ||b|| recomputed in FP64 at exit         */
+  double rel_res_true;  /* ||b - A x|| / ||b|| recomputed at exit with an FP64-class
+                           product: native FP64, or for FP32_REFINED on grids with
+                           register-resident passes double-float (about 48
+                           significant bits); dda_residual gives the native FP64 one */
   double rel_res_recur; /* the solver's own residual estimate at exit             */
   double seconds;       /* wall time of this RHS                                  */
 } dda_solve_info;
