@@ -380,18 +380,25 @@ __device__ __forceinline__ void zc_product(cpx<R>* s, const cpx<R>* __restrict__
     cpx<R> d6[6];
     load_oct<R>(D, o, octs, d6);
     const cpx<R> dxx = d6[0], dyy = d6[3], dzz = d6[5];
-    cpx<R> dxy = d6[1], dxz = d6[2], dyz = d6[4];
+    cpx<R> dxy = d6[1], ez = d6[2], fzz = d6[4];
     if (nxs ^ nys) dxy = mk<R>(-dxy.x, -dxy.y);
-    const int nkz = (fz == 0 || 2 * fz == M) ? 1 : 2;
-    for (int h = 0; h < nkz; ++h) {
-      cpx<R> ez = dxz, fzz = dyz;
-      if (nxs ^ h) ez = mk<R>(-ez.x, -ez.y);
-      if (nys ^ h) fzz = mk<R>(-fzz.x, -fzz.y);
-      const int e = (h ? Z::at(b1, b2) : Z::at(a1, a2)) * T + t2;
+    if (nxs) ez = mk<R>(-ez.x, -ez.y);           // xz and yz at kz = fz
+    if (nys) fzz = mk<R>(-fzz.x, -fzz.y);
+    {
+      const int e = Z::at(a1, a2) * T + t2;
       const cpx<R> vx = s[e], vy = s[CS + e], vz = s[2 * CS + e];
       s[e] = dxx * vx + dxy * vy + ez * vz;
       s[CS + e] = dxy * vx + dyy * vy + fzz * vz;
       s[2 * CS + e] = ez * vx + fzz * vy + dzz * vz;
+    }
+    if (fz != 0 && 2 * fz != M) {
+      // kz = M - fz: xz and yz change sign (odd in z); the negated terms are
+      // subtracted, which rounds exactly as adding the negated products
+      const int e = Z::at(b1, b2) * T + t2;
+      const cpx<R> vx = s[e], vy = s[CS + e], vz = s[2 * CS + e];
+      s[e] = dxx * vx + dxy * vy - ez * vz;
+      s[CS + e] = dxy * vx + dyy * vy - fzz * vz;
+      s[2 * CS + e] = dzz * vz - (ez * vx + fzz * vy);
     }
     a1 += S1;
     a2 += S2;
