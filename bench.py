@@ -254,7 +254,7 @@ def load_peaks():
 # with the capture it comes from.  Only valid for the 134^3 sphere on the
 # 270^3 grid; None elsewhere, and removed whenever the kernel changes.
 NCU_TRAFFIC_134 = {
-    "p3_zconv_c64": (355273472 + 183773184,
+    "p3_zconv_c64": (355240704 + 183284224,
                      "ncu --set full --clock-control none -k regex:fk_zconv -s 1 -c 1 of "
                      "python bench.py --workload products --n 134 --prec fp32 --products 3 "
                      "(fk_zconv<float, 15, 18, 16>, stored capture, not measured by this run)"),
