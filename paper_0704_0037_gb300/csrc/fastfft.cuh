@@ -615,7 +615,11 @@ __device__ __forceinline__ int row_of(const long long* off, long long i) {
 
 // Loads per thread issued together in the gather and scatter loops over a
 // block's dipoles
-constexpr int kGU = 4;
+// in the x forward and x inverse passes: more for the long lines, whose
+// blocks of few rows hold many dipoles, as far as the registers of the
+// blocks an SM holds allow
+template <int M> constexpr int kGUF = M >= 1000 ? 8 : 4;
+template <int M> constexpr int kGUI = M >= 1000 ? 16 : 4;
 
 template <typename R, int M1, int M2, int T, bool CONJ>
 __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 * M2 + T * kLD<M1 * M2>) * sizeof(cpx<R>))) fk_xfwd(const typename VecOf<R>::type* __restrict__ x,
@@ -624,7 +628,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, (M1 *
                                                           long long n_occ, int nrows,
                                                           const cpx<R>* __restrict__ tw,
                                                           int bstride, const int* __restrict__ skip) {
-  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>;
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>, kGU = kGUF<M1 * M2>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_off[T + 1];
   cpx<R>* s_tw = reinterpret_cast<cpx<R>*>(smem_raw);
@@ -744,7 +748,7 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, kXinvB<R
                                                           const cpx<R>* __restrict__ tw,
                                                           double* __restrict__ dotp, int bstride,
                                                           const int* __restrict__ skip) {
-  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>, kXS = T * kXRow<M>;
+  constexpr int M = M1 * M2, NT = T * kQ<M1, M2>, LD = kLD<M>, kXS = T * kXRow<M>, kGU = kGUI<M1 * M2>;
   using V = typename VecOf<R>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_off[T + 1];
