@@ -957,10 +957,8 @@ __global__ void __launch_bounds__(T * kQ<M1, M2>, kMinB(T * kQ<M1, M2>, 3, 1)) f
 
 // ---------------------------------------------------------------- launchers
 template <typename R> constexpr int kT = sizeof(R) == 4 ? 16 : 8;
-// rows per block of the x inverse pass (fast_x_rows gives the same on the
-// host) and of the x forward pass
+// rows per block of the x passes (fast_x_rows gives the same on the host)
 template <typename R, int M> constexpr int kTX = (sizeof(R) == 4 && M >= 1000) ? 4 : kT<R>;
-template <typename R, int M> constexpr int kTXF = kTX<R, M>;
 
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
@@ -972,11 +970,10 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 template <typename R, int M1, int M2>
 struct Passes {
   static constexpr int M = M1 * M2, T = kT<R>, NT = T * kQ<M1, M2>;
-  // rows per block of the x passes: for the complex64 lines of 1000 points
-  // and more 4 in the forward pass (four blocks of 4.5 warps per SM) and 8 in
-  // the inverse one (16 rows of 1080 points would take 147 KB, one block per SM)
+  // rows per block of the x passes: 4 for the complex64 lines of 1000 points
+  // and more (four blocks of 4.5 warps per SM; 16 rows of 1080 points would
+  // take 147 KB, one block per SM)
   static constexpr int TX = kTX<R, M>, NTX = TX * kQ<M1, M2>;
-  static constexpr int TXF = kTXF<R, M>, NTXF = TXF * kQ<M1, M2>;
   // columns per block of the fused z pass: the three spectra of TZ columns
   // must fit in shared memory (two blocks per SM where they can)
   static constexpr int TZ = (size_t)(M + 3 * M * T) * sizeof(cpx<R>) <= 113 * 1024 ? T
@@ -1044,17 +1041,17 @@ struct Passes {
   static cudaError_t xfwd(const V* x, cpx<R>* B1, const LatticeDev& lat, const cpx<R>* beta,
                           long long n_occ, int nrows, const cpx<R>* tw, bool adj, int nrhs,
                           int bstride, const int* skip, cudaStream_t st, bool pdl) {
-    const size_t sm = (size_t)(M + TXF * kLD<M>) * sizeof(cpx<R>);
+    const size_t sm = (size_t)(M + TX * kLD<M>) * sizeof(cpx<R>);
     const int nr = lat.arow ? lat.nact : nrows;
-    const dim3 grid((nr + TXF - 1) / TXF, 3 * nrhs);
+    const dim3 grid((nr + TX - 1) / TX, 3 * nrhs);
     cudaError_t e;
     if (adj) {
-      if ((e = set_smem(fk_xfwd<R, M1, M2, TXF, true>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(pdl, fk_xfwd<R, M1, M2, TXF, true>, grid, dim3(NTXF), sm, st, x, B1, lat, beta, n_occ,
+      if ((e = set_smem(fk_xfwd<R, M1, M2, TX, true>, sm)) != cudaSuccess) return e;
+      e = launch_pdl(pdl, fk_xfwd<R, M1, M2, TX, true>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
                      nrows, tw, bstride, skip);
     } else {
-      if ((e = set_smem(fk_xfwd<R, M1, M2, TXF, false>, sm)) != cudaSuccess) return e;
-      e = launch_pdl(pdl, fk_xfwd<R, M1, M2, TXF, false>, grid, dim3(NTXF), sm, st, x, B1, lat, beta, n_occ,
+      if ((e = set_smem(fk_xfwd<R, M1, M2, TX, false>, sm)) != cudaSuccess) return e;
+      e = launch_pdl(pdl, fk_xfwd<R, M1, M2, TX, false>, grid, dim3(NTX), sm, st, x, B1, lat, beta, n_occ,
                      nrows, tw, bstride, skip);
     }
     count_launch();

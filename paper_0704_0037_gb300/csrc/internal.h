@@ -310,8 +310,8 @@ struct FastArgs {
 inline bool fast_pdl(bool fp64, long long Mx, long long My, long long Mz, int nrhs) {
   return !fp64 && Mx * My * Mz * nrhs <= (1LL << 23);
 }
-// rows per block of the x inverse pass: 16 for complex64 lines shorter than
-// 1000 points, 8 for the longer ones and for the double-width arithmetic
+// rows per block of the x passes: 16 for complex64 lines shorter than 1000
+// points, 4 for the longer ones, 8 for the double-width arithmetic
 inline int fast_x_rows(bool fp32, int Mx) { return fp32 ? (Mx < 1000 ? 16 : 4) : 8; }
 // number of (re, im) partials FP_XINV writes to dotp for nrows rows
 inline int fast_xinv_blocks(int nrows, bool fp32, int Mx) {
