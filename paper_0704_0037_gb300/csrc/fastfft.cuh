@@ -1106,9 +1106,6 @@ struct Passes {
     count_launch();
     return e != cudaSuccess ? e : cudaGetLastError();
   }
-  // number of blocks (partials written to dotp) of xinv for nrows rows, per
-  // right-hand side (the partials of right-hand side r follow those of r - 1)
-  static int xinv_blocks(int nrows) { return 3 * ((nrows + TX - 1) / TX); }
 };
 
 }  // namespace fast
